@@ -1,0 +1,456 @@
+"""Plain FP64 CPU oracle: the paper's algorithms written out step by step.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  The scalar loops live
+in ``pssd_oracle.c``; this module strings them together in the paper's order
+and notation.  The only library primitive used as a step is the dense matrix
+product (``numpy.matmul``).
+
+Two layers (both FP64):
+
+* definition layer (``eig_def``, ``sign_def``): the exact result the method
+  converges to.  The eigenvalues of the definite pencil ``M v = lambda Sigma v``
+  (``M = Sigma H``) come from the Jacobi eigensolver applied to the symmetric
+  ``K = L^T Sigma L`` with ``M = L L^T``; the eigenvectors are
+  ``v = sqrt|lambda| L^{-T} u`` normalised to ``v^T Sigma v = +-1``
+  (Thm. EVRealSigmaOrth and its proof by simultaneous diagonalisation), and
+  ``sign(H) = V sign(Lambda) V^{-1}`` (Eq. signDef) with
+  ``V^{-1} = Sigma_hat V^T Sigma``.
+* algorithm layer (``sign_alg``, ``split_alg``, ``eig_alg``): Alg. 8 with the
+  inverse-form step Eq. (ZoloIt2), then Alg. 7, then the symmetric definite
+  subproblems by Jacobi (Thm. DefDivConq).
+
+Readings of the paper where it is garbled or silent (each also listed in the
+design notes):
+  R1  Eq. (Compcis): the argument is i*K'/(2r+1) with the integer index i.
+  R2  Eq. (ZPartialFrac2): the product between the two products is a quotient.
+  R3  r is the smallest value for which two steps map [l,1] into [1-tau,1].
+  R4  Alg. 8 step "X1 <- C(X_k + ...)" uses X_0; Alg. 4's Q_- uses P_-.
+  R5  bounds alpha, beta: alpha = lambda_max(Sigma A), beta = lambda_min(Sigma A)
+      (valid since |lambda(A)| lies in [lambda_min(M), lambda_max(M)]).
+  R6  restart of Alg. 8 (failed stopping test): A <- X_2 with the bounds
+      alpha = 1, beta = l_2, which bound |lambda(X_2)| because Zhat o Zhat maps
+      [l,1] monotonically into [l_2,1]; r by R3; at most ``max_restarts``
+      restarts.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import build as _build
+
+U_FP64 = 2.0 ** -53
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.or_cholesky.argtypes = [ctypes.c_int, dp, dp]
+        lib.or_lu_solve.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp]
+        lib.or_jacobi_eigh.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
+        lib.or_pivoted_lowrank_chol.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, ip]
+        lib.or_ellipk_from_comp.argtypes = [ctypes.c_double]
+        lib.or_ellipk_from_comp.restype = ctypes.c_double
+        lib.or_sncn.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.or_sc_comp.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.or_sc_comp.restype = ctypes.c_double
+        lib.or_zolo_coeffs.argtypes = [ctypes.c_double, ctypes.c_int, dp, dp, dp, dp]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class NotDefinite(ValueError):
+    """Sigma*H is not positive definite (a Cholesky pivot was not positive)."""
+
+
+# --------------------------------------------------------------------------
+# scalar Zolotarev machinery  (Sec. 5.3)
+# --------------------------------------------------------------------------
+
+def ellipk_from_comp(kc: float) -> float:
+    """K for the modulus whose complementary modulus is ``kc`` (AGM)."""
+    return _L().or_ellipk_from_comp(float(kc))
+
+
+def sncn(u: float, kc: float):
+    """Jacobi sn(u), cn(u) by descending Landen/AGM; modulus sqrt(1-kc^2)."""
+    s = ctypes.c_double(); c = ctypes.c_double()
+    _L().or_sncn(float(u), float(kc), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def sc_comp(u: float, kc: float) -> float:
+    """sn(u)/cn(u) for the modulus sqrt(1-kc^2) (imaginary transformation +
+    descending Landen on the small modulus kc)."""
+    return _L().or_sc_comp(float(u), float(kc))
+
+
+def zolo_coeffs(ell: float, r: int):
+    """Coefficients of the scaled Zolotarev function (Eqs. Compcis, hatZ,
+    ZPartialFrac2 and the l-update of Alg. 8; readings R1, R2).
+
+    Returns ``(c, a, chat, ell_next)`` with ``c[i-1] = c_i`` (i = 1..2r),
+    ``a[j-1] = a_j`` (j = 1..r).
+    Pinned by: equioscillation, Zhat(1)=1, the partial-fraction identity,
+    the composition law and the r=1 closed form (tests/test_oracle_zolo.py).
+    """
+    c = np.zeros(2 * r); a = np.zeros(r)
+    ch = ctypes.c_double(); l1 = ctypes.c_double()
+    st = _L().or_zolo_coeffs(float(ell), int(r), _p(c), _p(a), ctypes.byref(ch), ctypes.byref(l1))
+    if st:
+        raise ValueError("zolo_coeffs: invalid ell=%r r=%r" % (ell, r))
+    return c, a, ch.value, l1.value
+
+
+def zolo_eval(x, ell: float, r: int):
+    """Scaled Zolotarev function, product form (Eq. hatZ):
+    Zhat(x) = Chat x prod_j (x^2 + c_{2j}) / (x^2 + c_{2j-1})."""
+    c, _, chat, _ = zolo_coeffs(ell, r)
+    x = np.asarray(x, dtype=np.float64)
+    y = chat * x
+    for j in range(r):
+        y = y * (x * x + c[2 * j + 1]) / (x * x + c[2 * j])
+    return y
+
+
+def zolo_eval_partial_fractions(x, ell: float, r: int):
+    """Scaled Zolotarev function, partial-fraction form (Eq. ZPartialFrac):
+    Zhat(x) = Chat x (1 + sum_j a_j / (x^2 + c_{2j-1}))."""
+    c, a, chat, _ = zolo_coeffs(ell, r)
+    x = np.asarray(x, dtype=np.float64)
+    s = np.ones_like(x)
+    for j in range(r):
+        s = s + a[j] / (x * x + c[2 * j])
+    return chat * x * s
+
+
+def choose_r(ell: float, tau: float = 1e-15, r_max: int = 8) -> int:
+    """Reading R3 of the choice of r (the paper defers to a table that is not
+    reproduced): the smallest r <= r_max with 1 - l_2 <= tau, where
+    l_1 = Zhat(l; l) and l_2 = Zhat(l_1; l_1)."""
+    for r in range(1, r_max + 1):
+        l1 = min(zolo_coeffs(ell, r)[3], 1.0)
+        if 1.0 - l1 <= tau:
+            return r
+        l2 = zolo_coeffs(l1, r)[3]
+        if 1.0 - l2 <= tau:
+            return r
+    return r_max
+
+
+# --------------------------------------------------------------------------
+# dense scalar-loop kernels
+# --------------------------------------------------------------------------
+
+def cholesky(A):
+    """Lower Cholesky factor (scalar loops).  Raises NotDefinite."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    L = np.zeros((n, n))
+    st = _L().or_cholesky(n, _p(A), _p(L))
+    if st:
+        raise NotDefinite("non-positive pivot at index %d" % (st - 1))
+    return L
+
+
+def lu_solve(A, B):
+    """Solve A X = B by Gaussian elimination with partial pivoting."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    B = np.array(B, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    m = 1 if B.ndim == 1 else B.shape[1]
+    st = _L().or_lu_solve(n, _p(A), m, _p(B))
+    if st:
+        raise np.linalg.LinAlgError("singular at %d" % (st - 1))
+    return B
+
+
+def jacobi_eigh(A, max_sweeps: int = 60):
+    """Symmetric eigendecomposition by cyclic Jacobi; eigenvalues ascending."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    A = 0.5 * (A + A.T)
+    A = np.ascontiguousarray(A)
+    w = np.zeros(n); V = np.zeros((n, n))
+    sweeps = _L().or_jacobi_eigh(n, _p(A), _p(w), _p(V), int(max_sweeps))
+    if sweeps < 0:
+        raise RuntimeError("Jacobi did not converge")
+    idx = np.argsort(w, kind="stable")
+    return w[idx], np.ascontiguousarray(V[:, idx])
+
+
+def pivoted_lowrank_chol(A, rank: int):
+    """A ~= W W^T, W n-by-rank, diagonal pivoting (largest first, ties lowest)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    W = np.zeros((n, rank)); piv = np.zeros(rank, dtype=np.int32)
+    st = _L().or_pivoted_lowrank_chol(n, _p(A), int(rank), _p(W),
+                                      piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if st:
+        raise NotDefinite("pivoted low-rank Cholesky broke down at step %d" % (st - 1))
+    return W, piv
+
+
+# --------------------------------------------------------------------------
+# signature helpers (Def. pseudosym)
+# --------------------------------------------------------------------------
+
+def signature(n: int, sigma=None):
+    """Diagonal of Sigma as a float vector; None means diag(I_{n/2}, -I_{n/2})."""
+    if sigma is None:
+        if n % 2:
+            raise ValueError("default signature needs even n")
+        return np.r_[np.ones(n // 2), -np.ones(n // 2)]
+    s = np.asarray(sigma, dtype=np.float64).ravel()
+    if s.shape[0] != n or not np.all(np.abs(s) == 1.0):
+        raise ValueError("sigma must hold n entries in {+1,-1}")
+    return s
+
+
+def pseudosymmetry_defect(H, sigma=None):
+    """||Sigma H - (Sigma H)^T||_F / ||Sigma H||_F (Def. pseudosym)."""
+    s = signature(H.shape[0], sigma)
+    M = s[:, None] * H
+    return np.linalg.norm(M - M.T) / np.linalg.norm(M)
+
+
+# --------------------------------------------------------------------------
+# definition layer
+# --------------------------------------------------------------------------
+
+def _sign_fix_columns(V):
+    """Output convention: each column's largest-magnitude entry is positive
+    (ties: lowest index)."""
+    V = V.copy()
+    for j in range(V.shape[1]):
+        i = int(np.argmax(np.abs(V[:, j])))
+        if V[i, j] < 0:
+            V[:, j] = -V[:, j]
+    return V
+
+
+def _order(lam, V):
+    """Output convention: positive eigenvalues ascending, then negative ones by
+    ascending magnitude."""
+    pos = np.where(lam > 0)[0]; neg = np.where(lam < 0)[0]
+    pos = pos[np.argsort(lam[pos], kind="stable")]
+    neg = neg[np.argsort(-lam[neg], kind="stable")]
+    idx = np.r_[pos, neg]
+    return lam[idx], V[:, idx]
+
+
+def eig_def(H, sigma=None):
+    """Definition-level eigendecomposition of a definite pseudosymmetric H.
+
+    M = Sigma H = L L^T (scalar Cholesky), K = L^T Sigma L is symmetric and
+    similar to H (L^T H L^{-T} = K), so lambda(H) = lambda(K) (Jacobi).
+    Eigenvectors v = sqrt|lambda| L^{-T} u satisfy V^T Sigma V = Sigma_hat
+    (Eq. VSigmaOrth, up to the column order of the output convention).
+    Returns (lam, V) in the output convention.
+    """
+    n = H.shape[0]
+    s = signature(n, sigma)
+    M = s[:, None] * H
+    M = 0.5 * (M + M.T)
+    L = cholesky(M)
+    K = L.T @ (s[:, None] * L)
+    w, U = jacobi_eigh(K)
+    Y = lu_solve(L.T, U)                     # L^{-T} U
+    V = Y * np.sqrt(np.abs(w))[None, :]
+    lam, V = _order(w, V)
+    return lam, _sign_fix_columns(V)
+
+
+def sign_def(H, sigma=None):
+    """sign(H) = V sign(Lambda) V^{-1} (Eq. signDef) with
+    V^{-1} = Sigma_hat V^T Sigma; since Sigma_hat = sign(Lambda) here
+    (Thm. EVRealSigmaOrth), S = V V^T Sigma."""
+    n = H.shape[0]
+    s = signature(n, sigma)
+    lam, V = eig_def(H, sigma)
+    return (V @ V.T) * s[None, :]
+
+
+# --------------------------------------------------------------------------
+# algorithm layer: Alg. 8 (hyperbolic Zolo-PD), Alg. 7, Alg. 3
+# --------------------------------------------------------------------------
+
+def estimate_bounds(A, sigma=None):
+    """Alg. 8 first step, reading R5: alpha = lambda_max(Sigma A),
+    beta = lambda_min(Sigma A), from the Jacobi eigensolver."""
+    s = signature(A.shape[0], sigma)
+    M = s[:, None] * A
+    w, _ = jacobi_eigh(0.5 * (M + M.T))
+    if not w[0] > 0:
+        raise NotDefinite("Sigma*A is not positive definite")
+    return float(w[-1]), float(w[0])
+
+
+def zolo_step(X, sigma, c, a, chat, threads: int | None = None):
+    """One step of Eq. (ZoloIt2) with M = Sigma:
+    X_{k+1} = Chat (X + sum_j a_j X (X^T Sigma X + c_{2j-1} Sigma)^{-1} Sigma).
+
+    The r shifted systems are mutually independent and are solved in
+    parallel threads (Gaussian elimination with partial pivoting, which the
+    paper's pivoted LDL^T / hyperbolic QR forms equal in exact arithmetic,
+    Eqs. LDLZolo, HRZolo and Lemma HRnoInv)."""
+    n = X.shape[0]
+    s = signature(n, sigma)
+    XtSX = X.T @ (s[:, None] * X)
+    Sig = np.diag(s)
+    r = len(a)
+
+    def term(j):
+        Z = XtSX + c[2 * j] * Sig
+        Y = lu_solve(Z, Sig)                 # Z^{-1} Sigma
+        return a[j] * (X @ Y)
+
+    with ThreadPoolExecutor(max_workers=threads or r) as ex:
+        terms = list(ex.map(term, range(r)))
+    acc = X.copy()
+    for t in terms:
+        acc = acc + t
+    return chat * acc
+
+
+def sign_alg(H, sigma=None, r: int | None = None, alpha: float | None = None,
+             beta: float | None = None, max_restarts: int = 2, tau: float = 1e-15):
+    """Alg. 8 (hyperbolic Zolo-PD) for a definite pseudosymmetric H.
+
+    Returns (S, info) where info holds the per-step iterates X1, X2 of the
+    first pass, r per pass, the l values, the stopping quantity and the
+    number of restarts.  A failed stopping test restarts from A <- X_2
+    (reading R6); more than ``max_restarts`` restarts raises RuntimeError.
+    """
+    n = H.shape[0]
+    s = signature(n, sigma)
+    A = np.array(H, dtype=np.float64)
+    info = {"r": [], "ell": [], "stop": [], "restarts": 0, "X1": None, "X2": None}
+    ell_last = None
+    for attempt in range(max_restarts + 1):
+        if attempt > 0:
+            al, be = 1.0, ell_last                       # reading R6
+        elif alpha is not None and beta is not None:
+            al, be = float(alpha), float(beta)
+        else:
+            al, be = estimate_bounds(A, s)
+        X0 = A / al
+        ell = min(be / al, 1.0)
+        rr = r if (r is not None and attempt == 0) else choose_r(ell, tau)
+        info["r"].append(rr); info["ell"].append(ell)
+        c, a, chat, ell1 = zolo_coeffs(ell, rr)
+        X1 = zolo_step(X0, s, c, a, chat)               # first iteration
+        ell = min(ell1, 1.0)
+        info["ell"].append(ell)
+        c, a, chat, ell2 = zolo_coeffs(ell, rr)         # coefficient update
+        X2 = zolo_step(X1, s, c, a, chat)               # second iteration
+        info["ell"].append(min(ell2, 1.0))
+        ell_last = min(ell2, 1.0)
+        if attempt == 0:
+            info["X1"], info["X2"] = X1, X2
+        crit = np.linalg.norm(X2 - X1) / np.linalg.norm(X2)
+        info["stop"].append(crit)
+        if crit <= U_FP64 ** (1.0 / (2 * rr + 1)):
+            info["S"] = X2
+            return X2, info
+        info["restarts"] += 1
+        A = X2
+    raise RuntimeError("Zolo-PD: stopping test failed after %d restarts" % max_restarts)
+
+
+def split_alg(H, sigma=None, S=None):
+    """Alg. 7 (robust (Sigma, Sigma_hat)-orthogonal basis via pivoted,
+    truncated LDL^T) and the projections of Thm. DefDivConq.
+
+    P_+ = (I+S)/2 and P_- = (I-S)/2 (Lemma SignProj); Sigma P_+ and
+    -Sigma P_- are positive semidefinite of ranks p and n-p
+    (Thm. EVRealSigmaOrth); their pivoted low-rank Cholesky factors W_+-
+    give Q_+- = Sigma W_+-, with Q_+^T Sigma Q_+ = I_p and
+    Q_-^T Sigma Q_- = -I_{n-p} (Thm. HRisLDL).  Then
+    A11 = Q_+^T M Q_+ (SPD) and A22 = -Q_-^T M Q_- (SND), M = Sigma H.
+    Returns (Qp, Qm, A11, A22).
+    """
+    n = H.shape[0]
+    s = signature(n, sigma)
+    if S is None:
+        S, _ = sign_alg(H, s)
+    p = int(np.sum(s > 0))
+    I = np.eye(n)
+    Pp = 0.5 * (I + S)
+    Pm = 0.5 * (I - S)
+    SPp = s[:, None] * Pp
+    SPm = -(s[:, None] * Pm)
+    Wp, _ = pivoted_lowrank_chol(0.5 * (SPp + SPp.T), p)
+    Wm, _ = pivoted_lowrank_chol(0.5 * (SPm + SPm.T), n - p)
+    Qp = s[:, None] * Wp
+    Qm = s[:, None] * Wm
+    M = s[:, None] * H
+    A11 = Qp.T @ M @ Qp
+    A22 = -(Qm.T @ M @ Qm)
+    return Qp, Qm, A11, A22
+
+
+def split_backward_error(H, sigma, Qp, Qm):
+    """The paper's backward error ||Q_+^T Sigma A Q_-||_F / ||A||_F (Ex. 1)."""
+    s = signature(H.shape[0], sigma)
+    return np.linalg.norm(Qp.T @ (s[:, None] * H) @ Qm) / np.linalg.norm(H)
+
+
+def eig_alg(H, sigma=None, S=None):
+    """Alg. 3 for a definite H: one structure-preserving split (Alg. 8 +
+    Alg. 7), after which A11 is SPD and A22 SND (Thm. DefDivConq), so the
+    recursion ends in two symmetric eigenproblems solved by Jacobi.
+    V = [Q_+ V_1, Q_- V_2] satisfies V^T Sigma V = diag(I_p, -I_{n-p}).
+    Returns (lam, V) in the output convention."""
+    Qp, Qm, A11, A22 = split_alg(H, sigma, S)
+    w1, U1 = jacobi_eigh(A11)
+    w2, U2 = jacobi_eigh(A22)
+    lam = np.r_[w1, w2]
+    V = np.hstack([Qp @ U1, Qm @ U2])
+    lam, V = _order(lam, V)
+    return lam, _sign_fix_columns(V)
+
+
+# --------------------------------------------------------------------------
+# reference gradient: Newton sign iteration (Eq. NewtonSign)
+# --------------------------------------------------------------------------
+
+def newton_sign(X, tol: float = 1e-14, max_iter: int = 100):
+    """Unscaled Newton iteration X <- (X + X^{-1})/2 (Eq. NewtonSign), the
+    inverse by Gaussian elimination.  Stops when the relative change is
+    below ``tol`` (plus one more step)."""
+    X = np.array(X, dtype=np.float64)
+    n = X.shape[0]
+    I = np.eye(n)
+    for it in range(max_iter):
+        Xn = 0.5 * (X + lu_solve(X, I))
+        d = np.linalg.norm(Xn - X) / np.linalg.norm(Xn)
+        X = Xn
+        if d <= tol:
+            X = 0.5 * (X + lu_solve(X, I))
+            return X
+    raise RuntimeError("Newton sign iteration did not converge")
+
+
+def sign_vjp_block(H, G, tol: float = 1e-14):
+    """Reference cotangent of <G, sign(H)> with respect to H: the (1,2) block
+    of sign([[H^T, G], [0, H^T]]) (Frechet derivative of the sign function
+    applied to G, transposed into a gradient), computed by Newton because the
+    block matrix is not diagonalisable."""
+    n = H.shape[0]
+    B = np.zeros((2 * n, 2 * n))
+    B[:n, :n] = H.T; B[n:, n:] = H.T; B[:n, n:] = G
+    SB = newton_sign(B, tol=tol)
+    return SB[:n, n:]
