@@ -1,0 +1,163 @@
+/*
+ * pssd -- structure-preserving spectral divide-and-conquer for definite
+ * pseudosymmetric matrices on GB300 (sm_103a).
+ *
+ * Method: Benner, Nakatsukasa, Penke, "A Structure-Preserving
+ * Divide-and-Conquer Method for Pseudosymmetric Matrices" (arXiv 2203.08900).
+ *
+ * C ABI.  No C++ types and no exceptions cross this boundary.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are dense, ROW-MAJOR, FP64, with a leading dimension (the
+ *    distance in elements between the starts of consecutive rows), exactly as
+ *    a contiguous torch tensor.  Row-major matters: H is not symmetric and
+ *    sign(H^T) = sign(H)^T.
+ *  - Every matrix pointer is a DEVICE pointer owned by the caller; the
+ *    library never frees it.  Inputs are not modified.
+ *  - `sigma` is a HOST array of n entries in {+1,-1}: the diagonal of the
+ *    signature matrix Sigma (Def. pseudosym, Sec. 3).  NULL means
+ *    Sigma = diag(I_{n/2}, -I_{n/2}) (the Casida / BSE form, Eq. Casida).
+ *  - H must be pseudosymmetric (Sigma H symmetric, relative defect at most
+ *    1e-12 in the Frobenius norm) and definite (Sigma H positive definite,
+ *    Sec. 5).  Violations are reported, never trapped.
+ *  - All GPU work is issued on the handle's stream.  Entry points that need a
+ *    host scalar mid-way (bounds, stopping test, ranks) synchronise that
+ *    stream; on return every output is complete.
+ *  - Return value: PSSD_OK (0), a negative value -i if argument i (1-based)
+ *    is invalid (LAPACK style), or one of the positive PSSD_ERR_* codes.  On
+ *    error the outputs are unspecified; `info` (if not NULL) is filled as far
+ *    as the run got.
+ *  - Workspace is allocated by the handle on first use and grown as needed
+ *    (cudaMalloc outside any stream capture); pssd_destroy frees it.
+ */
+#ifndef PSSD_H
+#define PSSD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PSSD_OK 0
+#define PSSD_ERR_NOT_DEFINITE 1        /* Sigma H not positive definite (Cholesky pivot <= 0); info->fail_index */
+#define PSSD_ERR_NO_CONVERGENCE 2      /* Alg. 8 stopping test still failing after max_restarts restarts */
+#define PSSD_ERR_BASIS 3               /* split: basis rank or orthogonalisation breakdown */
+#define PSSD_ERR_NONFINITE 4           /* NaN/Inf in the input or an iterate */
+#define PSSD_ERR_TIMEOUT 5             /* a bounded device wait gave up */
+#define PSSD_ERR_CUDA 6                /* a CUDA call failed; see pssd_last_cuda_error */
+#define PSSD_ERR_ALLOC 7               /* workspace allocation failed */
+#define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
+
+/* precision modes */
+#define PSSD_FP64 0   /* every step in FP64 */
+#define PSSD_MIXED 1  /* Zolotarev steps in FP32 on tensor cores, FP64 refinement */
+
+typedef struct pssd_handle_s *pssd_handle;
+
+typedef struct {
+    int r;              /* Zolotarev rank per step; 0 = smallest r with 1-l_2 <= tau (reading of Sec. 5.3) */
+    double alpha;       /* upper bound on max|lambda(H)|; 0 = estimate (power iteration on Sigma H) */
+    double beta;        /* lower bound on min|lambda(H)|; 0 = estimate (power iteration on (Sigma H)^{-1}) */
+    int precision;      /* PSSD_FP64 or PSSD_MIXED */
+    int max_restarts;   /* restarts allowed after a failed stopping test (Alg. 8); < 0 = default (2) */
+    int leaf;           /* pssd_eig: subproblems of at most this order are solved by Jacobi; 0 = 64 */
+    int flags;          /* reserved, must be 0 */
+} pssd_opts;
+
+typedef struct {
+    int r_used[4];       /* r of each pass of Alg. 8 (first pass, restarts) */
+    int passes;          /* passes of Alg. 8 (1 + restarts) */
+    int steps;           /* Zolotarev steps taken (2 per pass) */
+    int restarts;
+    int p;               /* number of positive eigenvalues = number of +1 in sigma */
+    double alpha, beta;  /* bounds used in the first pass */
+    double ell[6];       /* l, l_1, l_2 of the first pass, then of the first restart */
+    double stop_crit[4]; /* ||X_2 - X_1||_F / ||X_2||_F of each pass */
+    double s2_resid;     /* ||S^2 - I||_F (pssd_sign only; -1 if not computed) */
+    double jsym_resid;   /* ||Sigma S - (Sigma S)^T||_F / ||S||_F (pssd_sign only) */
+    double split_backerr;/* ||Q_+^T Sigma H Q_-||_F / ||H||_F (pssd_split / pssd_eig) */
+    int fail_index;      /* failing Cholesky pivot (0-based) for PSSD_ERR_NOT_DEFINITE, else -1 */
+    int levels;          /* pssd_eig: recursion depth reached */
+    double seconds;      /* wall time of the call (host clock, stream synchronised) */
+} pssd_info;
+
+/* Fill `o` with the defaults (r = 0, alpha = beta = 0, FP64, 2 restarts, leaf 64). */
+void pssd_opts_init(pssd_opts *o);
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  Allocates nothing on the device.  Returns PSSD_OK or PSSD_ERR_CUDA. */
+int pssd_create(pssd_handle *h, void *stream);
+int pssd_destroy(pssd_handle h);
+int pssd_set_stream(pssd_handle h, void *stream);
+/* Last CUDA error string recorded by the handle (never NULL). */
+const char *pssd_last_cuda_error(pssd_handle h);
+const char *pssd_status_string(int status);
+
+/*
+ * Zolotarev coefficients (host only, FP64; Sec. 5.3).
+ *   c_i = l^2 sn^2(i K'/(2r+1); l') / cn^2(i K'/(2r+1); l'), i = 1..2r  (Eq. Compcis,
+ *         read with the integer index i), l' = sqrt(1-l^2), K' = K(l');
+ *   a_j = -prod_k (c_{2j-1} - c_{2k}) / prod_{k != j} (c_{2j-1} - c_{2k-1})  (Eq. ZPartialFrac2,
+ *         the printed product read as a quotient);
+ *   chat = prod_j (1 + c_{2j-1}) / (1 + c_{2j})   (Eq. hatZ);
+ *   ell_next = chat l prod_j (l^2 + c_{2j}) / (l^2 + c_{2j-1})   (Alg. 8, l-update).
+ * Arguments: ell in (0,1]; r in [1,64]; c: host array of 2r doubles (c[i-1] = c_i);
+ * a: host array of r doubles; chat, ell_next: host scalars.  Returns -1 / -2 for
+ * an invalid ell / r, -3..-6 for a NULL output.
+ */
+int pssd_zolo_coeffs(double ell, int r, double *c, double *a, double *chat, double *ell_next);
+
+/* Smallest r in [1, r_max] such that two Zolotarev steps map [ell,1] into
+ * [1-tau, 1] (reading of the choice of r in Sec. 5.3); r_max if none. */
+int pssd_choose_r(double ell, double tau, int r_max);
+
+/*
+ * S = sign(H) (Eq. signDef) by the two-step Zolotarev iteration of Alg. 8
+ * with its stopping test and restarts.
+ *   n      order of H (n >= 1; with sigma == NULL n must be even)
+ *   sigma  host signature (see above) or NULL
+ *   H      device, n x n, leading dimension ldh >= n
+ *   S      device, n x n output, leading dimension lds >= n; must not alias H
+ *   opts   NULL = defaults
+ *   info   NULL or filled (s2_resid and jsym_resid are computed)
+ */
+int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+              double *S, int lds, const pssd_opts *opts, pssd_info *info);
+
+/*
+ * One structure-preserving spectral division of a definite H (Alg. 3 step
+ * with Thm. DefDivConq): a (Sigma, Sigma_hat)-orthogonal basis Q = [Q_+ Q_-]
+ * of the invariant subspaces of the p positive / n-p negative eigenvalues,
+ * Q^T Sigma Q = diag(I_p, -I_{n-p}), and the projected blocks
+ *   A11 = Q_+^T (Sigma H) Q_+   (p x p, symmetric positive definite),
+ *   A22 = -Q_-^T (Sigma H) Q_-  ((n-p) x (n-p), symmetric negative definite),
+ * so that Q^{-1} H Q = diag(A11, A22).  p = number of +1 in sigma (Thm. EVRealSigmaOrth).
+ *   Q      device, n x n output (columns 0..p-1 = Q_+), leading dimension ldq >= n
+ *   A11    device, p x p output, lda11 >= p;  A22 device, (n-p) x (n-p), lda22 >= n-p
+ *   p      host int output (may be NULL)
+ * info->split_backerr = ||Q_+^T Sigma H Q_-||_F / ||H||_F (the metric of Sec. 6.1).
+ */
+int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+               double *Q, int ldq, double *A11, int lda11, double *A22, int lda22, int *p,
+               const pssd_opts *opts, pssd_info *info);
+
+/*
+ * Full diagonalisation V^{-1} H V = D (Alg. 3; after one split the
+ * subproblems are symmetric definite, Thm. DefDivConq, and are diagonalised
+ * by the symmetric divide-and-conquer of Alg. 2 down to Jacobi leaves).
+ *   V   device, n x n output, leading dimension ldv >= n; column j is the
+ *       eigenvector of D[j]; V^T Sigma V = diag(I_p, -I_{n-p}) (Eq. VSigmaOrth)
+ *   D   device, n output: the p positive eigenvalues ascending, then the
+ *       negative ones by ascending magnitude
+ * Each eigenvector's largest-magnitude entry is made positive.
+ */
+int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+             double *V, int ldv, double *D, const pssd_opts *opts, pssd_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSSD_H */

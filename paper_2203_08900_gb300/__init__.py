@@ -1,0 +1,250 @@
+"""Python binding of libpssd: structure-preserving spectral divide-and-conquer
+for definite pseudosymmetric matrices on GB300 (arXiv 2203.08900).
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+library behind the C ABI of ``include/pssd.h``; torch supplies device memory
+and the current stream.  There is no fallback: if the compiled library is
+missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpssd.so")
+
+PSSD_FP64 = 0
+PSSD_MIXED = 1
+FLAG_RESIDUALS = 1
+
+# kinds reported by profile_read
+K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI = range(5)
+KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("max_restarts", ctypes.c_int), ("leaf", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("r_used", ctypes.c_int * 4), ("passes", ctypes.c_int), ("steps", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("p", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("ell", ctypes.c_double * 6), ("stop_crit", ctypes.c_double * 4),
+                ("s2_resid", ctypes.c_double), ("jsym_resid", ctypes.c_double),
+                ("split_backerr", ctypes.c_double), ("fail_index", ctypes.c_int), ("levels", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class PssdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("pssd status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+# C-ABI symbols declared in include/pssd.h plus the measurement hooks
+EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
+           "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
+           "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count"]
+
+
+def lib():
+    """Load libpssd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpssd.so not built (%s); run paper_2203_08900_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, cp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_char_p
+    L.pssd_opts_init.argtypes = [ctypes.POINTER(Opts)]
+    L.pssd_opts_init.restype = None
+    L.pssd_create.argtypes = [ctypes.POINTER(vp), vp]
+    L.pssd_destroy.argtypes = [vp]
+    L.pssd_set_stream.argtypes = [vp, vp]
+    L.pssd_last_cuda_error.argtypes = [vp]
+    L.pssd_last_cuda_error.restype = cp
+    L.pssd_status_string.argtypes = [ctypes.c_int]
+    L.pssd_status_string.restype = cp
+    L.pssd_zolo_coeffs.argtypes = [ctypes.c_double, ctypes.c_int, dp, dp, dp, dp]
+    L.pssd_choose_r.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    sig = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+    L.pssd_sign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_split.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ip,
+                                   ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_eig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.pssd_profile_reset.argtypes = [vp]
+    L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
+    L.pssd_launch_count.argtypes = [vp]
+    L.pssd_launch_count.restype = ctypes.c_longlong
+    _lib = L
+    return L
+
+
+def zolo_coeffs(ell: float, r: int):
+    """Zolotarev coefficients from the library (host routine)."""
+    import numpy as np
+    c = (ctypes.c_double * (2 * r))(); a = (ctypes.c_double * r)()
+    ch = ctypes.c_double(); l1 = ctypes.c_double()
+    st = lib().pssd_zolo_coeffs(float(ell), int(r), c, a, ctypes.byref(ch), ctypes.byref(l1))
+    if st:
+        raise PssdError(st, "invalid argument")
+    return np.array(c[:]), np.array(a[:]), ch.value, l1.value
+
+
+def choose_r(ell: float, tau: float = 1e-15, r_max: int = 8) -> int:
+    st = lib().pssd_choose_r(float(ell), float(tau), int(r_max))
+    if st < 0:
+        raise PssdError(st, "invalid argument")
+    return st
+
+
+class Handle:
+    """Owns a pssd handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self._h = ctypes.c_void_p()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = L.pssd_create(ctypes.byref(self._h), ctypes.c_void_p(s))
+        if st:
+            raise PssdError(st, "pssd_create failed")
+
+    def close(self):
+        if self._h:
+            lib().pssd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        lib().pssd_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream))
+
+    # ---- measurement hooks
+    def profile(self, on: bool = True):
+        lib().pssd_profile_enable(self._h, 1 if on else 0)
+
+    def profile_reset(self):
+        lib().pssd_profile_reset(self._h)
+
+    def profile_read(self, kind: int):
+        ms = ctypes.c_double(); cnt = ctypes.c_longlong(); fl = ctypes.c_double()
+        lib().pssd_profile_read(self._h, int(kind), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl))
+        return {"ms": ms.value, "launches": cnt.value, "flops": fl.value}
+
+    def launch_count(self) -> int:
+        return int(lib().pssd_launch_count(self._h))
+
+    def _check(self, st):
+        if st:
+            L = lib()
+            msg = L.pssd_status_string(st).decode()
+            if st == 6:
+                msg += " (" + L.pssd_last_cuda_error(self._h).decode() + ")"
+            raise PssdError(st, msg)
+
+
+def _opts(r=0, alpha=0.0, beta=0.0, precision=PSSD_FP64, max_restarts=2, leaf=64, flags=0):
+    o = Opts()
+    lib().pssd_opts_init(ctypes.byref(o))
+    o.r = int(r); o.alpha = float(alpha); o.beta = float(beta); o.precision = int(precision)
+    o.max_restarts = int(max_restarts); o.leaf = int(leaf); o.flags = int(flags)
+    return o
+
+
+def _sigma(n, sigma):
+    if sigma is None:
+        return None, None
+    import numpy as np
+    s = np.ascontiguousarray(np.asarray(sigma).astype(np.int8).ravel())
+    if s.shape[0] != n:
+        raise ValueError("sigma must have n entries")
+    return s, s.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check_H(H):
+    if not (isinstance(H, torch.Tensor) and H.is_cuda and H.dtype == torch.float64 and H.dim() == 2
+            and H.shape[0] == H.shape[1] and H.stride(1) == 1):
+        raise ValueError("H must be a square row-major float64 CUDA tensor")
+    return H.shape[0], H.stride(0)
+
+
+_default = {}
+
+
+def _handle(handle):
+    if handle is not None:
+        return handle
+    dev = torch.cuda.current_device()
+    h = _default.get(dev)
+    if h is None:
+        h = _default[dev] = Handle()
+    h.set_stream(torch.cuda.current_stream())
+    return h
+
+
+def sign(H, sigma=None, handle=None, **kw):
+    """S = sign(H).  Returns (S, info dict)."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    S = torch.empty_like(H)
+    keep, sp = _sigma(n, sigma)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_sign(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
+                         S.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return S, info.as_dict()
+
+
+def split(H, sigma=None, handle=None, **kw):
+    """One structure-preserving split.  Returns (Q, A11, A22, p, info)."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    p = int((keep > 0).sum()) if keep is not None else n // 2
+    Q = torch.empty_like(H)
+    A11 = torch.empty(max(p, 1), max(p, 1), dtype=H.dtype, device=H.device)
+    A22 = torch.empty(max(n - p, 1), max(n - p, 1), dtype=H.dtype, device=H.device)
+    pp = ctypes.c_int(0)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_split(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(Q.data_ptr()),
+                          Q.stride(0), ctypes.c_void_p(A11.data_ptr()), A11.stride(0),
+                          ctypes.c_void_p(A22.data_ptr()), A22.stride(0), ctypes.byref(pp), ctypes.byref(o),
+                          ctypes.byref(info))
+    h._check(st)
+    return Q, A11[:p, :p], A22[:n - p, :n - p], pp.value, info.as_dict()
+
+
+def eig(H, sigma=None, handle=None, **kw):
+    """Full diagonalisation V^{-1} H V = diag(D).  Returns (D, V, info)."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    V = torch.empty_like(H)
+    D = torch.empty(n, dtype=H.dtype, device=H.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_eig(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(V.data_ptr()),
+                        V.stride(0), ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return D, V, info.as_dict()

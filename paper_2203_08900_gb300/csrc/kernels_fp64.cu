@@ -1,0 +1,738 @@
+// FP64 kernels of libpssd (sm_103a).
+//
+// On GB300 the FP64 pipe retires 2 DFMA per clock per SM (about 1.1 TFLOP/s
+// for the chip), so every FP64 contraction here is bound by the DFMA issue
+// rate, not by memory: the GEMM below stages 64x64x16 tiles of both operands
+// in shared memory and keeps a 4x4 register tile per thread, which already
+// makes shared-memory and HBM traffic a small fraction of the DFMA time.
+// The HBM-bound passes (symmetrisation, mirror, shift, combine, norms) use
+// 32x32 shared-memory transposes so that both the row and the column access
+// are coalesced.
+#include "pssd_internal.h"
+
+#include <math.h>
+
+namespace pssd {
+
+// --------------------------------------------------------------------------
+// GEMM with triangular operands, lower-only output and inner scaling
+// --------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+__global__ void __launch_bounds__(256) dgemm_kernel(GemmArgs g)
+{
+    const int z = blockIdx.z;
+    const int i0 = blockIdx.y * GBM, j0 = blockIdx.x * GBN;
+    if (i0 >= g.m || j0 >= g.n) return;
+    if (g.lowerC && j0 > i0 + GBM - 1) return;   // tile strictly above the diagonal
+
+    const double *A = g.A + (long long)z * g.sA;
+    const double *B = g.B + (long long)z * g.sB;
+    int kbeg = 0, kend = g.k;
+    if (g.triA == TRI_LOWER) kend = min(kend, i0 + GBM);   // op(A)[i][p] = 0 for p > i
+    if (g.triA == TRI_UPPER) kbeg = max(kbeg, i0);         // op(A)[i][p] = 0 for p < i
+    if (g.triB == TRI_LOWER) kbeg = max(kbeg, j0);         // op(B)[p][j] = 0 for p < j
+    if (g.triB == TRI_UPPER) kend = min(kend, j0 + GBN);   // op(B)[p][j] = 0 for p > j
+
+    __shared__ double As[GBK][GBM + 1];
+    __shared__ double Bs[GBK][GBN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int kt = kbeg; kt < kend; kt += GBK) {
+        // ---- stage op(A) tile (GBM x GBK) as As[p][i]
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e = tid + 256 * u;
+            int il, pl;
+            if (g.ta == 0) { il = e >> 4; pl = e & 15; } else { pl = e >> 6; il = e & 63; }
+            int i = i0 + il, p = kt + pl;
+            double v = 0.0;
+            bool ok = (i < g.m) && (p < kend);
+            if (g.triA == TRI_LOWER) ok = ok && (p <= i);
+            if (g.triA == TRI_UPPER) ok = ok && (p >= i);
+            if (ok) {
+                v = (g.ta == 0) ? A[(long long)i * g.lda + p] : A[(long long)p * g.lda + i];
+                if (g.kscale) v *= g.kscale[p];
+            }
+            As[pl][il] = v;
+        }
+        // ---- stage op(B) tile (GBK x GBN) as Bs[p][j]
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int e = tid + 256 * u;
+            int jl, pl;
+            if (g.tb == 0) { pl = e >> 6; jl = e & 63; } else { jl = e >> 4; pl = e & 15; }
+            int j = j0 + jl, p = kt + pl;
+            double v = 0.0;
+            bool ok = (j < g.n) && (p < kend);
+            if (g.triB == TRI_LOWER) ok = ok && (p >= j);
+            if (g.triB == TRI_UPPER) ok = ok && (p <= j);
+            if (ok) v = (g.tb == 0) ? B[(long long)p * g.ldb + j] : B[(long long)j * g.ldb + p];
+            Bs[pl][jl] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < GBK; ++p) {
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[p][ty + 16 * q]; b[q] = Bs[p][tx + 16 * q]; }
+#pragma unroll
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb) acc[qa][qb] = fma(a[qa], b[qb], acc[qa][qb]);
+        }
+        __syncthreads();
+    }
+
+    double *C = g.C + (long long)z * g.sC;
+    const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa) {
+        int i = i0 + ty + 16 * qa;
+        if (i >= g.m) continue;
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            int j = j0 + tx + 16 * qb;
+            if (j >= g.n) continue;
+            if (g.lowerC && j > i) continue;
+            double v = g.alpha * acc[qa][qb];
+            if (g.beta != 0.0) v += g.beta * Cin[(long long)i * g.ldcin + j];
+            C[(long long)i * g.ldc + j] = v;
+        }
+    }
+}
+
+void dgemm(const GemmArgs &g, cudaStream_t s)
+{
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
+    dim3 grid((g.n + GBN - 1) / GBN, (g.m + GBM - 1) / GBM, g.batch);
+    dgemm_kernel<<<grid, 256, 0, s>>>(g);
+}
+
+// --------------------------------------------------------------------------
+// Cholesky of one diagonal block (<= 64) and its triangular inverse
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dpotrf_diag_kernel(double *A, long long lda, long long sA, int k0,
+                                                          int kb, double *Dinv, long long sD, double *Rinv,
+                                                          long long ldr, long long sR, int *info)
+{
+    __shared__ double S[64][65];
+    __shared__ double T[64][65];
+    __shared__ int bad;
+    const int z = blockIdx.x, tid = threadIdx.x;
+    A += (long long)z * sA;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < 64 * 64; e += 256) {
+        int i = e >> 6, j = e & 63;
+        double v = 0.0;
+        if (i < kb && j <= i) v = A[(long long)(k0 + i) * lda + (k0 + j)];
+        S[i][j] = v;
+        T[i][j] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (!bad) { bad = 1; if (info[z] == 0) info[z] = k0 + j + 1; }
+                d = 1.0;
+            }
+            S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        const double piv = S[j][j];
+        for (int i = j + 1 + tid; i < kb; i += 256) S[i][j] /= piv;
+        __syncthreads();
+        const int w = kb - j - 1;
+        for (int e = tid; e < w * w; e += 256) {
+            int i = j + 1 + e / w, l = j + 1 + e % w;
+            if (l <= i) S[i][l] -= S[i][j] * S[l][j];
+        }
+        __syncthreads();
+    }
+    // inverse of the lower-triangular factor: column c by forward substitution
+    if (tid < kb) {
+        const int c = tid;
+        T[c][c] = 1.0 / S[c][c];
+        for (int i = c + 1; i < kb; ++i) {
+            double t = 0.0;
+            for (int m = c; m < i; ++m) t = fma(S[i][m], T[m][c], t);
+            T[i][c] = -t / S[i][i];
+        }
+    }
+    __syncthreads();
+    double *D = Dinv + (long long)z * sD;
+    for (int e = tid; e < 64 * 64; e += 256) {
+        int i = e >> 6, j = e & 63;
+        D[e] = (i < kb && j <= i) ? T[i][j] : 0.0;
+        if (i < kb && j < kb) {
+            A[(long long)(k0 + i) * lda + (k0 + j)] = (j <= i) ? S[i][j] : 0.0;
+            if (Rinv) Rinv[(long long)z * sR + (long long)(k0 + i) * ldr + (k0 + j)] = (j <= i) ? T[i][j] : 0.0;
+        }
+    }
+}
+
+void dpotrf_diag(double *A, long long lda, long long sA, int k0, int kb, int batch, double *Dinv,
+                 long long sD, double *Rinv, long long ldr, long long sR, int *info, cudaStream_t s)
+{
+    dpotrf_diag_kernel<<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info);
+}
+
+// --------------------------------------------------------------------------
+// HBM passes with 32x32 shared-memory tiles
+// --------------------------------------------------------------------------
+constexpr int TT = 32;
+
+// M = (Sig H + (Sig H)^T)/2 and the squared defect ||Sig H - (Sig H)^T||_F^2 and
+// ||Sig H||_F^2, block partials, over tile pairs (bi >= bj).
+__global__ void __launch_bounds__(256) sym_prepare_kernel(const double *H, long long ldh, const double *sig,
+                                                          int n, double *M, long long ldm, double *partials)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    const int blin = blockIdx.y * gridDim.x + blockIdx.x;
+    __shared__ double P[TT][TT + 1], Q[TT][TT + 1];
+    __shared__ double red[2][256];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    double dsum = 0.0, nsum = 0.0;
+    if (bi >= bj) {
+        for (int yy = ty; yy < TT; yy += 8) {
+            int i = bi * TT + yy, j = bj * TT + tx;
+            P[yy][tx] = (i < n && j < n) ? sig[i] * H[(long long)i * ldh + j] : 0.0;
+            int i2 = bj * TT + yy, j2 = bi * TT + tx;
+            Q[yy][tx] = (i2 < n && j2 < n) ? sig[i2] * H[(long long)i2 * ldh + j2] : 0.0;
+        }
+        __syncthreads();
+        for (int yy = ty; yy < TT; yy += 8) {
+            int i = bi * TT + yy, j = bj * TT + tx;
+            double a = P[yy][tx], b = Q[tx][yy];     // (Sig H)[i][j] and (Sig H)[j][i]
+            if (i < n && j < n) {
+                double m = 0.5 * (a + b);
+                M[(long long)i * ldm + j] = m;
+                double d = a - b;
+                double w = (bi == bj) ? 1.0 : 2.0;     // off-diagonal tile pairs count twice
+                if (bi == bj) { dsum += d * d; nsum += a * a; }
+                else { dsum += w * d * d; nsum += a * a + b * b; }
+            }
+            int i2 = bj * TT + yy, j2 = bi * TT + tx;
+            if (bi != bj && i2 < n && j2 < n) M[(long long)i2 * ldm + j2] = 0.5 * (Q[yy][tx] + P[tx][yy]);
+        }
+    }
+    red[0][threadIdx.x] = dsum; red[1][threadIdx.x] = nsum;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + st];
+            red[1][threadIdx.x] += red[1][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { partials[2 * blin] = red[0][0]; partials[2 * blin + 1] = red[1][0]; }
+}
+
+int sym_prepare_blocks(int n) { int t = (n + TT - 1) / TT; return t * t; }
+
+void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
+                 double *partials, cudaStream_t s)
+{
+    int t = (n + TT - 1) / TT;
+    sym_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(H, ldh, sig, n, M, ldm, partials);
+}
+
+// fixed-order single-block sum (deterministic)
+__global__ void reduce_sum_kernel(const double *x, int count, int stride, double *out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += 1024) s += x[(long long)i * stride];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void reduce_sum(const double *x, int count, double *out, cudaStream_t s)
+{
+    reduce_sum_kernel<<<1, 1024, 0, s>>>(x, count, 1, out);
+}
+
+// copy the strictly lower triangle onto the upper one
+__global__ void __launch_bounds__(256) mirror_lower_kernel(double *A, long long lda, long long sA, int n)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi < bj) return;
+    A += (long long)blockIdx.z * sA;
+    __shared__ double P[TT][TT + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bi * TT + yy, j = bj * TT + tx;
+        P[yy][tx] = (i < n && j < n) ? A[(long long)i * lda + j] : 0.0;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bj * TT + yy, j = bi * TT + tx;   // target (i, j) in the upper tile
+        if (i < n && j < n && j > i) A[(long long)i * lda + j] = P[tx][yy];
+    }
+}
+
+void mirror_lower(double *A, long long lda, long long sA, int n, int batch, cudaStream_t s)
+{
+    int t = (n + TT - 1) / TT;
+    mirror_lower_kernel<<<dim3(t, t, batch), 256, 0, s>>>(A, lda, sA, n);
+}
+
+__global__ void shift_copy_lower_kernel(const double *G, long long ldg, double *Z, long long ldz, long long sZ,
+                                        int n, const double *shifts)
+{
+    const int z = blockIdx.z;
+    const int i = blockIdx.y;
+    const double c = shifts[z];
+    double *Zr = Z + (long long)z * sZ + (long long)i * ldz;
+    const double *Gr = G + (long long)i * ldg;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i && j < n; j += gridDim.x * blockDim.x)
+        Zr[j] = Gr[j] + (i == j ? c : 0.0);
+}
+
+void shift_copy_lower(const double *G, long long ldg, double *Z, long long ldz, long long sZ, int n,
+                      const double *shifts, int batch, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 8) gx = 8;
+    shift_copy_lower_kernel<<<dim3(gx, n, batch), 256, 0, s>>>(G, ldg, Z, ldz, sZ, n, shifts);
+}
+
+__global__ void combine_lower_kernel(const double *Zinv, long long ldz, long long sZ, const double *a, int r,
+                                     int n, double *T, long long ldt)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i && j < n; j += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < r; ++q) v = fma(a[q], Zinv[(long long)q * sZ + (long long)i * ldz + j], v);
+        T[(long long)i * ldt + j] = v;
+    }
+}
+
+void combine_lower(const double *Zinv, long long ldz, long long sZ, const double *a, int r, int n, double *T,
+                   long long ldt, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 8) gx = 8;
+    combine_lower_kernel<<<dim3(gx, n), 256, 0, s>>>(Zinv, ldz, sZ, a, r, n, T, ldt);
+}
+
+__global__ void scale_copy_kernel(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
+                                  double alpha)
+{
+    const int i = blockIdx.y;
+    if (i >= m) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        Y[(long long)i * ldy + j] = alpha * X[(long long)i * ldx + j];
+}
+
+void scale_copy(const double *X, long long ldx, double *Y, long long ldy, int m, int n, double alpha,
+                cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return;
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    scale_copy_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, alpha);
+}
+
+void copy_matrix(const double *X, long long ldx, double *Y, long long ldy, int m, int n, cudaStream_t s)
+{
+    scale_copy(X, ldx, Y, ldy, m, n, 1.0, s);
+}
+
+__global__ void add_diag_kernel(double *X, long long ldx, int n, double v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        X[(long long)i * ldx + i] += v;
+}
+
+void add_diag(double *X, long long ldx, int n, double v, cudaStream_t s)
+{
+    add_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, v);
+}
+
+// per-block partials of ||X - Y||_F^2 and ||Y||_F^2 (grid-stride over rows)
+constexpr int FROB_BLOCKS = 608;  // 4 x 152 SMs
+
+__global__ void __launch_bounds__(256) frob_diff_kernel(const double *X, long long ldx, const double *Y,
+                                                        long long ldy, int m, int n, double *partials)
+{
+    __shared__ double red[2][256];
+    double d2 = 0.0, y2 = 0.0;
+    for (int i = blockIdx.x; i < m; i += gridDim.x) {
+        for (int j = threadIdx.x; j < n; j += 256) {
+            double y = Y[(long long)i * ldy + j];
+            double d = (X ? X[(long long)i * ldx + j] : 0.0) - y;
+            d2 += d * d; y2 += y * y;
+        }
+    }
+    red[0][threadIdx.x] = d2; red[1][threadIdx.x] = y2;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + st];
+            red[1][threadIdx.x] += red[1][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = red[0][0]; partials[2 * blockIdx.x + 1] = red[1][0]; }
+}
+
+int frob_blocks(int m, int n) { (void)n; return m < FROB_BLOCKS ? (m > 0 ? m : 1) : FROB_BLOCKS; }
+
+void frob_diff(const double *X, long long ldx, const double *Y, long long ldy, int m, int n, double *partials,
+               cudaStream_t s)
+{
+    frob_diff_kernel<<<frob_blocks(m, n), 256, 0, s>>>(X, ldx, Y, ldy, m, n, partials);
+}
+
+// counter-based normal variates: splitmix64 hash of (seed, index) -> two
+// uniforms -> Box-Muller
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void fill_gaussian_kernel(double *X, long long ldx, int m, int n, uint64_t seed)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t idx = (uint64_t)i * (uint64_t)n + (uint64_t)j;
+        uint64_t h1 = splitmix64(seed ^ (idx * 2 + 1)), h2 = splitmix64(seed + idx * 2 + 0x1234567ull);
+        double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+        X[(long long)i * ldx + j] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+}
+
+void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    fill_gaussian_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, seed);
+}
+
+__global__ void trace_kernel(const double *X, long long ldx, int n, double *out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) s += X[(long long)i * ldx + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void trace_partial(const double *X, long long ldx, int n, double *out, cudaStream_t s)
+{
+    trace_kernel<<<1, 1024, 0, s>>>(X, ldx, n, out);
+}
+
+__global__ void get_diag_kernel(const double *X, long long ldx, int n, double *d)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        d[i] = X[(long long)i * ldx + i];
+}
+
+void get_diag(const double *X, long long ldx, int n, double *d, cudaStream_t s)
+{
+    get_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, d);
+}
+
+// max over rows of sum_j |X[i][j]| (the infinity norm, an upper bound on
+// ||X||_2 for symmetric X): one warp per row, then a fixed-order max.
+__global__ void row_abs_sums_kernel(const double *X, long long ldx, int n, double *sums)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += fabs(X[(long long)warp * ldx + j]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sums[warp] = s;
+}
+
+__global__ void reduce_max_kernel(const double *x, int n, double *out)
+{
+    __shared__ double red[1024];
+    double b = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) b = fmax(b, x[i]);
+    red[threadIdx.x] = b;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void row_abs_sum_max(const double *X, long long ldx, int n, double *tmp, double *out, cudaStream_t s)
+{
+    row_abs_sums_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(X, ldx, n, tmp);
+    reduce_max_kernel<<<1, 1024, 0, s>>>(tmp, n, out);
+}
+
+// y = op(A) x for square n, op(A) optionally triangular (masked)
+__global__ void gemv_n_kernel(const double *A, long long lda, int tri, int n, const double *x, double *y)
+{
+    // one warp per row
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp;
+    int jb = 0, je = n;
+    if (tri == TRI_LOWER) je = i + 1;
+    if (tri == TRI_UPPER) jb = i;
+    double s = 0.0;
+    for (int j = jb + lane; j < je; j += 32) s = fma(A[(long long)i * lda + j], x[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = s;
+}
+
+// y[i] = sum_p A[p][i] x[p] (op(A) = A^T, `tri` describes op(A)); rows are
+// split into GEMV_CHUNKS slices whose partial sums are added in a fixed order.
+constexpr int GEMV_CHUNKS = 32;
+
+__global__ void gemv_t_partial_kernel(const double *A, long long lda, int tri, int n, const double *x,
+                                      double *part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.y;
+    if (i >= n) return;
+    const int len = (n + GEMV_CHUNKS - 1) / GEMV_CHUNKS;
+    int pb = ch * len, pe = min(n, pb + len);
+    if (tri == TRI_LOWER) pe = min(pe, i + 1);   // op(A)[i][p] = A[p][i] nonzero for p <= i
+    if (tri == TRI_UPPER) pb = max(pb, i);
+    double s = 0.0;
+    for (int p = pb; p < pe; ++p) s = fma(A[(long long)p * lda + i], x[p], s);
+    part[(long long)ch * n + i] = s;
+}
+
+__global__ void gemv_t_reduce_kernel(const double *part, int n, double *y)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < GEMV_CHUNKS; ++c) s += part[(long long)c * n + i];
+    y[i] = s;
+}
+
+void gemv(const double *A, long long lda, int ta, int tri, int n, const double *x, double *y, double *tmp,
+          cudaStream_t s)
+{
+    if (ta == 0) {
+        gemv_n_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, tri, n, x, y);
+    } else {
+        gemv_t_partial_kernel<<<dim3((n + 127) / 128, GEMV_CHUNKS), 128, 0, s>>>(A, lda, tri, n, x, tmp);
+        gemv_t_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, n, y);
+    }
+}
+
+__global__ void normalize_kernel(double *y, double *x, int n, double *norm_out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) s += y[i] * y[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    double nrm = sqrt(red[0]);
+    double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) x[i] = y[i] * inv;
+    if (threadIdx.x == 0 && norm_out) norm_out[0] = nrm;
+}
+
+void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s)
+{
+    normalize_kernel<<<1, 1024, 0, s>>>(y, x, n, norm_out);
+}
+
+__global__ void dot_kernel(const double *x, const double *y, int n, double *out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) s += x[i] * y[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s)
+{
+    dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out);
+}
+
+__global__ void scale_columns_kernel(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double f = use_sqrt_abs ? sqrt(fabs(d[j])) : d[j];
+        X[(long long)i * ldx + j] *= f;
+    }
+}
+
+void scale_columns(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    scale_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, d, use_sqrt_abs);
+}
+
+// make the largest-magnitude entry of each column positive (ties: lowest row)
+__global__ void sign_fix_columns_kernel(double *X, long long ldx, int m, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double best = -1.0, val = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double v = X[(long long)i * ldx + j];
+        if (fabs(v) > best) { best = fabs(v); val = v; }
+    }
+    if (val < 0.0)
+        for (int i = 0; i < m; ++i) X[(long long)i * ldx + j] = -X[(long long)i * ldx + j];
+}
+
+void sign_fix_columns(double *X, long long ldx, int m, int n, cudaStream_t s)
+{
+    sign_fix_columns_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, ldx, m, n);
+}
+
+__global__ void gather_columns_kernel(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
+                                      const int *perm)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        Y[(long long)i * ldy + j] = X[(long long)i * ldx + perm[j]];
+}
+
+void gather_columns(const double *X, long long ldx, double *Y, long long ldy, int m, int n, const int *perm,
+                    cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    gather_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, perm);
+}
+
+// --------------------------------------------------------------------------
+// Jacobi eigensolver for one symmetric matrix of order m <= 64 (one CTA).
+// Parallel cyclic order: in each of the m'-1 rounds (m' = m rounded up to
+// even) the pairs of a round-robin tournament are disjoint, so all their
+// rotations are applied together (rows, then columns, then eigenvectors).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) jacobi_leaf_kernel(double *Ag, long long lda, int m, double *W,
+                                                          long long ldw, double *w, int *sweeps_out)
+{
+    __shared__ double A[64][65];
+    __shared__ double V[64][65];
+    __shared__ double cs[32], sn[32];
+    __shared__ int pp[32], qq[32];
+    __shared__ int order[64];
+    __shared__ double offn, dian;
+    const int tid = threadIdx.x;
+    const int me = (m + 1) & ~1;   // even
+    for (int e = tid; e < 64 * 64; e += 256) {
+        int i = e >> 6, j = e & 63;
+        A[i][j] = (i < m && j < m) ? 0.5 * (Ag[(long long)i * lda + j] + Ag[(long long)j * lda + i]) : 0.0;
+        V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    if (tid < 64) order[tid] = tid;
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < 40; ++sweep) {
+        if (tid == 0) { offn = 0.0; dian = 0.0; }
+        __syncthreads();
+        {
+            double o = 0.0, d = 0.0;
+            for (int e = tid; e < m * m; e += 256) {
+                int i = e / m, j = e % m;
+                double v = A[i][j];
+                if (i == j) d += v * v; else o += v * v;
+            }
+            atomicAdd(&offn, o);
+            atomicAdd(&dian, d);
+        }
+        __syncthreads();
+        if (offn <= 1e-30 * dian || offn == 0.0) break;
+        for (int round = 0; round < me - 1; ++round) {
+            // pairs of this round: (order[k], order[me-1-k])
+            if (tid < me / 2) {
+                int p = order[tid], q = order[me - 1 - tid];
+                if (p > q) { int t = p; p = q; q = t; }
+                pp[tid] = p; qq[tid] = q;
+                double c = 1.0, s = 0.0;
+                if (q < m) {
+                    double apq = A[p][q];
+                    if (apq != 0.0) {
+                        double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+                        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t); s = t * c;
+                    }
+                }
+                cs[tid] = c; sn[tid] = s;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = tid; e < (me / 2) * m; e += 256) {
+                int k = e / m, col = e % m;
+                int p = pp[k], q = qq[k];
+                if (q >= m) continue;
+                double c = cs[k], s = sn[k];
+                double ap = A[p][col], aq = A[q][col];
+                A[p][col] = c * ap - s * aq;
+                A[q][col] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, and V <- V J
+            for (int e = tid; e < (me / 2) * m; e += 256) {
+                int k = e / m, row = e % m;
+                int p = pp[k], q = qq[k];
+                if (q >= m) continue;
+                double c = cs[k], s = sn[k];
+                double ap = A[row][p], aq = A[row][q];
+                A[row][p] = c * ap - s * aq;
+                A[row][q] = s * ap + c * aq;
+                double vp = V[row][p], vq = V[row][q];
+                V[row][p] = c * vp - s * vq;
+                V[row][q] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // rotate the tournament: keep order[0], shift the rest
+            if (tid == 0) {
+                int last = order[me - 1];
+                for (int k = me - 1; k > 1; --k) order[k] = order[k - 1];
+                order[1] = last;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < m * m; e += 256) {
+        int i = e / m, j = e % m;
+        W[(long long)i * ldw + j] = V[i][j];
+    }
+    if (tid < m) w[tid] = A[tid][tid];
+    if (tid == 0 && sweeps_out) sweeps_out[0] = sweep;
+}
+
+void jacobi_leaf(double *A, long long lda, int m, double *W, long long ldw, double *w, int *sweeps_out,
+                 cudaStream_t s)
+{
+    jacobi_leaf_kernel<<<1, 256, 0, s>>>(A, lda, m, W, ldw, w, sweeps_out);
+}
+
+}  // namespace pssd

@@ -1,0 +1,1071 @@
+// Host drivers and the C ABI of libpssd.
+//
+// Layout of the computation (all device work on the handle's stream):
+//
+//   M = Sigma H (symmetrised; defect checked)          Def. pseudosym, Sec. 5 (definite)
+//   M = L L^T, L^{-1}                                   blocked Cholesky + recursive triangular inverse
+//   K = L^T Sigma L                                     symmetric, similar to H (L^T H L^{-T} = K)
+//   alpha, beta from M and M^{-1} (power iteration)      Alg. 8, first step
+//   Zolotarev steps on X_0 = K/alpha                    Alg. 8, Eqs. ZoloIt1 / ZPartialFrac
+//     X_{k+1} = Chat (X_k + X_k sum_j a_j (X_k^2 + c_{2j-1} I)^{-1})
+//     each shift: Cholesky R_j R_j^T, R_j^{-1}, R_j^{-T} R_j^{-1}  (r chains batched per launch)
+//   stopping test, restarts                             Alg. 8
+//   S = L^{-T} sign(K) L^T                              since H = L^{-T} K L^T
+//   split: orthonormal bases U_+-, of range((I +- sign K)/2), B_+- = U_+-^T K U_+-,
+//     Q_+- = L^{-T} U_+- C_+-  with  +-B_+- = C C^T        Alg. 3 step, Thm. DefDivConq
+//   symmetric recursion on B_+-                         Alg. 2, Jacobi leaves
+//
+// Every iterate of the congruence form is symmetric and every shifted system
+// is symmetric positive definite, so no pivoting is needed on the GPU; the
+// paper's pivoted LDL^T / hyperbolic QR forms (Eqs. LDLZolo, HRZolo) compute
+// the same iterates X_k = L^{-T} K_k L^T in exact arithmetic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pssd.h"
+#include "pssd_internal.h"
+
+using namespace pssd;
+
+namespace {
+
+constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
+
+struct Chunk { char *base; size_t cap; size_t off; };
+
+struct ProfEvent { cudaEvent_t a, b; int kind; double flops; };
+
+}  // namespace
+
+struct pssd_handle_s {
+    cudaStream_t stream = nullptr;
+    std::vector<Chunk> chunks;
+    std::string last_err = "no error";
+    int prof = 0;
+    std::vector<ProfEvent> events;
+    std::vector<cudaEvent_t> free_events;
+    double prof_ms[8] = {0}, prof_flops[8] = {0};
+    long long prof_count[8] = {0};
+    long long launches = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Fail { int code; };
+
+inline void cuda_check(pssd_handle h, cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        h->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Fail{PSSD_ERR_CUDA};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace: chunked bump allocator with stack marks; chunks are kept for reuse
+// ---------------------------------------------------------------------------
+struct Mark { size_t chunk; size_t off; };
+
+Mark mark(pssd_handle h)
+{
+    if (h->chunks.empty()) return {0, 0};
+    // the active chunk is the last one with off > 0, or 0
+    size_t c = 0;
+    for (size_t i = 0; i < h->chunks.size(); ++i) if (h->chunks[i].off > 0) c = i;
+    return {c, h->chunks.empty() ? 0 : h->chunks[c].off};
+}
+
+void release(pssd_handle h, Mark m)
+{
+    for (size_t i = 0; i < h->chunks.size(); ++i) {
+        if (i > m.chunk) h->chunks[i].off = 0;
+        else if (i == m.chunk) h->chunks[i].off = m.off;
+    }
+}
+
+void *walloc(pssd_handle h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    Mark m = mark(h);
+    for (size_t i = m.chunk; i < h->chunks.size(); ++i) {
+        Chunk &c = h->chunks[i];
+        size_t off = (i == m.chunk) ? c.off : 0;
+        if (off + bytes <= c.cap) { c.off = off + bytes; return c.base + off; }
+    }
+    size_t cap = std::max(bytes, size_t(1) << 30);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, cap);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        throw Fail{PSSD_ERR_ALLOC};
+    }
+    h->chunks.push_back({(char *)p, cap, bytes});
+    return p;
+}
+
+double *dalloc(pssd_handle h, size_t count) { return (double *)walloc(h, count * sizeof(double)); }
+int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeof(int)); }
+
+// ---------------------------------------------------------------------------
+// launch accounting and optional per-launch CUDA-event timing
+// ---------------------------------------------------------------------------
+enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_NKIND = 5 };
+
+cudaEvent_t get_event(pssd_handle h)
+{
+    if (!h->free_events.empty()) { cudaEvent_t e = h->free_events.back(); h->free_events.pop_back(); return e; }
+    cudaEvent_t e;
+    cuda_check(h, cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+}
+
+struct Timed {
+    pssd_handle h; int kind; double flops; cudaEvent_t a = nullptr, b = nullptr;
+    Timed(pssd_handle h_, int kind_, double flops_, int nlaunch = 1) : h(h_), kind(kind_), flops(flops_)
+    {
+        h->launches += nlaunch;
+        if (h->prof) { a = get_event(h); b = get_event(h); cudaEventRecord(a, h->stream); }
+    }
+    ~Timed()
+    {
+        if (h->prof) { cudaEventRecord(b, h->stream); h->events.push_back({a, b, kind, flops}); }
+    }
+};
+
+void prof_collect(pssd_handle h)
+{
+    if (!h->prof || h->events.empty()) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &e : h->events) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e.a, e.b);
+        h->prof_ms[e.kind] += ms;
+        h->prof_flops[e.kind] += e.flops;
+        h->prof_count[e.kind] += 1;
+        h->free_events.push_back(e.a);
+        h->free_events.push_back(e.b);
+    }
+    h->events.clear();
+}
+
+// exact count of multiply-adds of one GEMM launch (algorithmic work):
+// output (i,j) needs the p with op(A)[i][p] and op(B)[p][j] structurally nonzero.
+double gemm_macs(const GemmArgs &g)
+{
+    double total = 0.0;
+    const double k = g.k;
+    for (int i = 0; i < g.m; ++i) {
+        double alo = 0, ahi = k;
+        if (g.triA == TRI_LOWER) ahi = std::min(k, (double)i + 1);
+        if (g.triA == TRI_UPPER) alo = i;
+        int jmax = g.lowerC ? std::min(g.n, i + 1) : g.n;
+        // len(j) = max(0, min(ahi, bhi(j)) - max(alo, blo(j)));
+        // bhi(j) = j+1 (triB upper) or k; blo(j) = j (triB lower) or 0
+        if (g.triB == TRI_NONE) {
+            total += jmax * std::max(0.0, ahi - alo);
+        } else if (g.triB == TRI_LOWER) {
+            // len = max(0, ahi - max(alo, j)); j < alo: ahi-alo ; alo <= j < ahi: ahi - j
+            double s = 0;
+            double j1 = std::min((double)jmax, alo);
+            if (j1 > 0) s += j1 * std::max(0.0, ahi - alo);
+            double ja = std::max(0.0, alo), jb = std::min((double)jmax, ahi);
+            if (jb > ja) s += (jb - ja) * ahi - (jb - 1 + ja) * (jb - ja) / 2.0;
+            total += s;
+        } else {  // TRI_UPPER: len = max(0, min(ahi, j+1) - alo)
+            double s = 0;
+            // j+1 <= ahi  <=> j <= ahi-1 : len = j + 1 - alo (if > 0)
+            double ja = std::max(0.0, alo), jb = std::min((double)jmax, ahi);  // j in [alo, ahi)
+            if (jb > ja) s += (jb - ja) * (1 - alo) + (jb - 1 + ja) * (jb - ja) / 2.0;
+            double jc = std::max(ahi, 0.0);
+            if (jmax > jc) s += (jmax - jc) * std::max(0.0, ahi - alo);
+            total += s;
+        }
+    }
+    return total * g.batch;
+}
+
+void gemm(pssd_handle h, const GemmArgs &g)
+{
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
+    double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
+    Timed t(h, K_DGEMM, fl);
+    dgemm(g, h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// small host <-> device helpers
+// ---------------------------------------------------------------------------
+void h2d(pssd_handle h, void *d, const void *src, size_t bytes)
+{
+    cuda_check(h, cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync H2D");
+}
+
+void d2h_sync(pssd_handle h, void *dst, const void *d, size_t bytes)
+{
+    cuda_check(h, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync D2H");
+    cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+}
+
+void frob_pair(pssd_handle h, const double *X, long long ldx, const double *Y, long long ldy, int m, int n,
+               double *part, double *d2, double *y2)
+{
+    {
+        Timed t(h, K_HBM, 0);
+        frob_diff(X, ldx, Y, ldy, m, n, part, h->stream);
+    }
+    int nb = frob_blocks(m, n);
+    std::vector<double> hp(2 * (size_t)nb);
+    d2h_sync(h, hp.data(), part, hp.size() * sizeof(double));
+    double a = 0, b = 0;
+    for (int i = 0; i < nb; ++i) { a += hp[2 * i]; b += hp[2 * i + 1]; }
+    *d2 = a; *y2 = b;
+}
+
+// ---------------------------------------------------------------------------
+// blocked Cholesky (lower, in place) of `batch` matrices; optional inverse
+// ---------------------------------------------------------------------------
+void potrf(pssd_handle h, double *A, int n, long long lda, long long sA, int batch, double *Rinv, long long ldr,
+           long long sR, double *Dinv, int *dinfo)
+{
+    cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
+    for (int k0 = 0; k0 < n; k0 += 64) {
+        int kb = std::min(64, n - k0);
+        {
+            Timed t(h, K_POTRF, batch * (kb * (double)kb * kb / 3.0 * 2.0));
+            dpotrf_diag(A, lda, sA, k0, kb, batch, Dinv, 64 * 64, Rinv, ldr, sR, dinfo, h->stream);
+        }
+        int rest = n - k0 - kb;
+        if (rest <= 0) continue;
+        GemmArgs p;                       // L21 = A21 L11^{-T}
+        p.m = rest; p.n = kb; p.k = kb; p.batch = batch;
+        p.A = A + (long long)(k0 + kb) * lda + k0; p.lda = lda; p.sA = sA;
+        p.B = Dinv; p.ldb = 64; p.sB = 64 * 64; p.tb = 1; p.triB = TRI_UPPER;
+        p.C = A + (long long)(k0 + kb) * lda + k0; p.ldc = lda; p.sC = sA;
+        gemm(h, p);
+        GemmArgs t;                       // A22 -= L21 L21^T (lower)
+        t.m = rest; t.n = rest; t.k = kb; t.batch = batch;
+        t.A = p.C; t.lda = lda; t.sA = sA;
+        t.B = p.C; t.ldb = lda; t.sB = sA; t.tb = 1;
+        t.Cin = A + (long long)(k0 + kb) * lda + (k0 + kb); t.ldcin = lda; t.sCin = sA;
+        t.C = A + (long long)(k0 + kb) * lda + (k0 + kb); t.ldc = lda; t.sC = sA;
+        t.alpha = -1.0; t.beta = 1.0; t.lowerC = 1;
+        gemm(h, t);
+    }
+}
+
+int check_info(pssd_handle h, const int *dinfo, int batch, int *fail_index)
+{
+    std::vector<int> hi(batch);
+    d2h_sync(h, hi.data(), dinfo, sizeof(int) * batch);
+    for (int z = 0; z < batch; ++z)
+        if (hi[z]) { if (fail_index) *fail_index = hi[z] - 1; return 1; }
+    return 0;
+}
+
+// recursive triangular inverse; diagonal 64-blocks must already hold their inverses
+void trtri_rec(pssd_handle h, const double *L, double *Rinv, int off, int s, long long ld, long long sL,
+               long long sR, int batch, double *tmp, long long sT)
+{
+    if (s <= 64) return;
+    int nbk = (s + 63) / 64;
+    int hh = ((nbk + 1) / 2) * 64;
+    trtri_rec(h, L, Rinv, off, hh, ld, sL, sR, batch, tmp, sT);
+    trtri_rec(h, L, Rinv, off + hh, s - hh, ld, sL, sR, batch, tmp, sT);
+    GemmArgs a;   // T = L21 * inv(L11)
+    a.m = s - hh; a.n = hh; a.k = hh; a.batch = batch;
+    a.A = L + (long long)(off + hh) * ld + off; a.lda = ld; a.sA = sL;
+    a.B = Rinv + (long long)off * ld + off; a.ldb = ld; a.sB = sR; a.triB = TRI_LOWER;
+    a.C = tmp; a.ldc = hh; a.sC = sT;
+    gemm(h, a);
+    GemmArgs b;   // inv21 = -inv(L22) T
+    b.m = s - hh; b.n = hh; b.k = s - hh; b.batch = batch;
+    b.A = Rinv + (long long)(off + hh) * ld + (off + hh); b.lda = ld; b.sA = sR; b.triA = TRI_LOWER;
+    b.B = tmp; b.ldb = hh; b.sB = sT;
+    b.C = Rinv + (long long)(off + hh) * ld + off; b.ldc = ld; b.sC = sR;
+    b.alpha = -1.0;
+    gemm(h, b);
+}
+
+// Cholesky + inverse of `batch` SPD matrices; returns nonzero on breakdown
+int chol_inv(pssd_handle h, double *A, int n, long long lda, long long sA, int batch, double *Rinv, long long sR,
+             int *fail_index)
+{
+    Mark mk = mark(h);
+    double *Dinv = dalloc(h, (size_t)64 * 64 * batch);
+    int *dinfo = ialloc(h, batch);
+    potrf(h, A, n, lda, sA, batch, Rinv, lda, sR, Dinv, dinfo);
+    int bad = check_info(h, dinfo, batch, fail_index);
+    if (!bad && Rinv && n > 64) {
+        size_t tsz = (size_t)((n + 1) / 2 + 64) * ((n + 1) / 2 + 64);
+        double *tmp = dalloc(h, tsz * batch);
+        trtri_rec(h, A, Rinv, 0, n, lda, sA, sR, batch, tmp, (long long)tsz);
+    }
+    release(h, mk);
+    return bad;
+}
+
+void mirror(pssd_handle h, double *A, long long lda, long long sA, int n, int batch)
+{
+    Timed t(h, K_HBM, 0);
+    mirror_lower(A, lda, sA, n, batch, h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// one Zolotarev step on a symmetric m x m X (full storage):
+//   Xn = Chat (X + X T),  T = sum_j a_j (X^2 + c_{2j-1} I)^{-1}
+// ---------------------------------------------------------------------------
+int zolo_step(pssd_handle h, const double *X, double *Xn, int m, int r, const double *c, const double *a,
+              double chat, int *fail_index)
+{
+    Mark mk = mark(h);
+    const long long ld = m, msz = (long long)m * m;
+    double *G = dalloc(h, msz);
+    double *T = dalloc(h, msz);
+    double *Z = dalloc(h, msz * r);
+    double *Ri = dalloc(h, msz * r);
+    double *dsh = dalloc(h, 2 * r + 2);
+    std::vector<double> hs(2 * r);
+    for (int j = 0; j < r; ++j) { hs[j] = c[2 * j]; hs[r + j] = a[j]; }
+    h2d(h, dsh, hs.data(), sizeof(double) * 2 * r);
+    GemmArgs g;                                 // G = X X (lower)
+    g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
+    gemm(h, g);
+    {
+        Timed t(h, K_HBM, 0);
+        shift_copy_lower(G, ld, Z, ld, msz, m, dsh, r, h->stream);   // Z_j = G + c_{2j-1} I
+    }
+    int bad = chol_inv(h, Z, m, ld, msz, r, Ri, msz, fail_index);     // R_j, R_j^{-1}
+    if (bad) { release(h, mk); return PSSD_ERR_NOT_DEFINITE; }
+    GemmArgs l;                                 // Z_j^{-1} = R_j^{-T} R_j^{-1} (lower)
+    l.m = l.n = l.k = m; l.batch = r;
+    l.A = Ri; l.lda = ld; l.sA = msz; l.ta = 1; l.triA = TRI_UPPER;
+    l.B = Ri; l.ldb = ld; l.sB = msz; l.triB = TRI_LOWER;
+    l.C = Z; l.ldc = ld; l.sC = msz; l.lowerC = 1;
+    gemm(h, l);
+    {
+        Timed t(h, K_HBM, 0);
+        combine_lower(Z, ld, msz, dsh + r, r, m, T, ld, h->stream);  // T = sum a_j Z_j^{-1}
+    }
+    mirror(h, T, ld, 0, m, 1);
+    GemmArgs f;                                 // Xn = chat (X + X T) (lower), then mirror
+    f.m = f.n = f.k = m; f.A = X; f.lda = ld; f.B = T; f.ldb = ld; f.Cin = X; f.ldcin = ld;
+    f.C = Xn; f.ldc = ld; f.alpha = chat; f.beta = chat; f.lowerC = 1;
+    gemm(h, f);
+    mirror(h, Xn, ld, 0, m, 1);
+    release(h, mk);
+    return PSSD_OK;
+}
+
+struct SignResult { double *Y; };
+
+// Alg. 8 on the symmetric X0 (scaled so that |lambda| in [ell, 1]); result in Y
+// (one of the two ping-pong buffers, returned).  Fills the pass statistics.
+int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_restarts, double tau,
+              double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index)
+{
+    const long long ld = m;
+    double *X = X0;
+    Mark mk = mark(h);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
+    int pass = 0;
+    for (;; ++pass) {
+        int r = (pass == 0 && r_opt > 0) ? r_opt : choose_r_host(ell, tau, 8);
+        double c[128], a[64], chat, ell1, ell2;
+        zolo_coeffs_host(ell, r, c, a, &chat, &ell1);
+        if (ell1 > 1.0) ell1 = 1.0;
+        double *X1 = (X == bufA) ? bufB : bufA;
+        int st = zolo_step(h, X, X1, m, r, c, a, chat, fail_index);
+        if (st) { release(h, mk); return st; }
+        zolo_coeffs_host(ell1, r, c, a, &chat, &ell2);
+        if (ell2 > 1.0) ell2 = 1.0;
+        double *X2 = (X1 == bufA) ? bufB : bufA;   // may be X itself on a restart (no longer needed)
+        st = zolo_step(h, X1, X2, m, r, c, a, chat, fail_index);
+        if (st) { release(h, mk); return st; }
+        double d2, y2;
+        frob_pair(h, X1, ld, X2, ld, m, m, part, &d2, &y2);
+        double crit = std::sqrt(d2 / y2);
+        if (info) {
+            if (pass < 4) { info->r_used[pass] = r; info->stop_crit[pass] = crit; }
+            if (pass < 2) { info->ell[3 * pass] = ell; info->ell[3 * pass + 1] = ell1; info->ell[3 * pass + 2] = ell2; }
+            info->passes = pass + 1; info->steps = 2 * (pass + 1); info->restarts = pass;
+        }
+        if (!std::isfinite(crit)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        if (crit <= std::pow(U64, 1.0 / (2 * r + 1))) { *Yout = X2; release(h, mk); return PSSD_OK; }
+        if (pass >= max_restarts) { *Yout = X2; release(h, mk); return PSSD_ERR_NO_CONVERGENCE; }
+        // restart (reading R6): A <- X_2, alpha = 1, beta = l_2
+        ell = ell2;
+        X = X2;
+    }
+}
+
+// power iteration estimate of lambda_max of an SPD operator given by `apply`
+template <class F>
+double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *dscal, int iters)
+{
+    {
+        Timed t(h, K_HBM, 0);
+        fill_gaussian(v, n, 1, n, 0x5eedull, h->stream);
+        normalize_vec(v, v, n, nullptr, h->stream);
+    }
+    for (int it = 0; it < iters; ++it) {
+        apply(v, w);
+        Timed t(h, K_GEMV, 0);
+        normalize_vec(w, v, n, nullptr, h->stream);
+    }
+    apply(v, w);
+    {
+        Timed t(h, K_GEMV, 0);
+        dot_vec(v, w, n, dscal, h->stream);
+    }
+    double rq;
+    d2h_sync(h, &rq, dscal, sizeof(double));
+    return rq;
+}
+
+// ---------------------------------------------------------------------------
+// orthonormal basis of the columns of Y (n x m, ld ldy) by CholeskyQR2 -> U (ld ldu)
+// ---------------------------------------------------------------------------
+int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double *U, long long ldu)
+{
+    Mark mk = mark(h);
+    double *G = dalloc(h, (size_t)m * m);
+    double *Gi = dalloc(h, (size_t)m * m);
+    double *W = dalloc(h, (size_t)n * m);
+    const double *src = Y; long long lds = ldy;
+    for (int pass = 0; pass < 2; ++pass) {
+        GemmArgs g;  // G = Y^T Y (lower)
+        g.m = g.n = m; g.k = n; g.A = src; g.lda = lds; g.ta = 1; g.B = src; g.ldb = lds;
+        g.C = G; g.ldc = m; g.lowerC = 1;
+        gemm(h, g);
+        int fi;
+        if (chol_inv(h, G, m, m, 0, 1, Gi, 0, &fi)) { release(h, mk); return PSSD_ERR_BASIS; }
+        double *dst = (pass == 0) ? W : U;
+        long long ldd = (pass == 0) ? m : ldu;
+        GemmArgs q;  // U = Y G^{-T}
+        q.m = n; q.n = m; q.k = m; q.A = src; q.lda = lds; q.B = Gi; q.ldb = m; q.tb = 1; q.triB = TRI_UPPER;
+        q.C = dst; q.ldc = ldd;
+        gemm(h, q);
+        src = dst; lds = ldd;
+    }
+    release(h, mk);
+    return PSSD_OK;
+}
+
+// Symmetric split of B (m x m, symmetric) given Y ~ sign(B - sigma I):
+//   U = [U_+ U_-] (m x m, ld m), Bp = U_+^T B U_+ (p x p), Bm = U_-^T B U_- ;
+//   E = U_+^T U_- (p x (m-p)) if E != nullptr.
+int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, double *U, double *Bp, double *Bm,
+              double *E, uint64_t seed)
+{
+    Mark mk = mark(h);
+    const long long ld = m;
+    double *Om = dalloc(h, (size_t)m * m);
+    double *Yb = dalloc(h, (size_t)m * m);
+    {
+        Timed t(h, K_HBM, 0);
+        fill_gaussian(Om, ld, m, m, seed, h->stream);
+    }
+    if (p > 0) {   // Y_+ = (I + Y)/2 Omega_+
+        GemmArgs g; g.m = m; g.n = p; g.k = m; g.A = Y; g.lda = ld; g.B = Om; g.ldb = ld; g.Cin = Om; g.ldcin = ld;
+        g.C = Yb; g.ldc = ld; g.alpha = 0.5; g.beta = 0.5;
+        gemm(h, g);
+    }
+    if (m - p > 0) {   // Y_- = (I - Y)/2 Omega_-
+        GemmArgs g; g.m = m; g.n = m - p; g.k = m; g.A = Y; g.lda = ld; g.B = Om + p; g.ldb = ld; g.Cin = Om + p;
+        g.ldcin = ld; g.C = Yb + p; g.ldc = ld; g.alpha = -0.5; g.beta = 0.5;
+        gemm(h, g);
+    }
+    int st = PSSD_OK;
+    if (p > 0) st = cholqr2(h, Yb, ld, m, p, U, ld);
+    if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld);
+    if (st) { release(h, mk); return st; }
+    double *W = Yb;   // reuse: W = B U  (m x m)
+    {
+        GemmArgs g; g.m = m; g.n = m; g.k = m; g.A = B; g.lda = ld; g.B = U; g.ldb = ld; g.C = W; g.ldc = ld;
+        gemm(h, g);
+    }
+    if (p > 0) {
+        GemmArgs g; g.m = p; g.n = p; g.k = m; g.A = U; g.lda = ld; g.ta = 1; g.B = W; g.ldb = ld;
+        g.C = Bp; g.ldc = p; g.lowerC = 1;
+        gemm(h, g);
+        mirror(h, Bp, p, 0, p, 1);
+    }
+    if (m - p > 0) {
+        GemmArgs g; g.m = m - p; g.n = m - p; g.k = m; g.A = U + p; g.lda = ld; g.ta = 1; g.B = W + p; g.ldb = ld;
+        g.C = Bm; g.ldc = m - p; g.lowerC = 1;
+        gemm(h, g);
+        mirror(h, Bm, m - p, 0, m - p, 1);
+    }
+    if (E && p > 0 && m - p > 0) {
+        GemmArgs g; g.m = p; g.n = m - p; g.k = m; g.A = U; g.lda = ld; g.ta = 1; g.B = U + p; g.ldb = ld;
+        g.C = E; g.ldc = m - p;
+        gemm(h, g);
+    }
+    release(h, mk);
+    return PSSD_OK;
+}
+
+// symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
+// and Jacobi leaves: W (m x m, ld m) eigenvectors as columns, w eigenvalues
+// (device).  B is preserved.
+int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int leaf, int depth, int *maxdepth,
+            uint64_t seed)
+{
+    if (depth > *maxdepth) *maxdepth = depth;
+    if (m <= leaf) {
+        Timed t(h, K_JACOBI, 0);
+        jacobi_leaf(const_cast<double *>(B), m, m, W, m, w, nullptr, h->stream);
+        return PSSD_OK;
+    }
+    const long long ld = m, msz = (long long)m * m;
+    Mark outer = mark(h);
+    std::vector<double> dg(m);
+    double *dd = dalloc(h, m);
+    {
+        Timed t(h, K_HBM, 0);
+        get_diag(B, ld, m, dd, h->stream);
+    }
+    d2h_sync(h, dg.data(), dd, sizeof(double) * m);
+    std::vector<double> srt = dg;
+    std::sort(srt.begin(), srt.end());
+    double dmin = srt.front(), dmax = srt.back();
+    double *U = dalloc(h, msz);
+    int p = 0;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt >= 4) { release(h, outer); return PSSD_ERR_BASIS; }
+        double sigma = (attempt == 0) ? 0.5 * (srt[(m - 1) / 2] + srt[m / 2])
+                                      : dmin + (dmax - dmin) * (0.5 + 0.11 * attempt);
+        Mark mk = mark(h);
+        double *X0 = dalloc(h, msz), *bA = dalloc(h, msz), *bB = dalloc(h, msz);
+        double *tmp = dalloc(h, m + 2);
+        {
+            Timed t(h, K_HBM, 0);
+            copy_matrix(B, ld, X0, ld, m, m, h->stream);
+            add_diag(X0, ld, m, -sigma, h->stream);
+            row_abs_sum_max(X0, ld, m, tmp, tmp + m, h->stream);
+        }
+        double alpha;
+        d2h_sync(h, &alpha, tmp + m, sizeof(double));
+        if (!(alpha > 0.0)) {   // B = sigma I: any orthonormal basis diagonalises it
+            release(h, mk);
+            std::vector<double> eye((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i) eye[(size_t)i * m + i] = 1.0;
+            h2d(h, W, eye.data(), sizeof(double) * msz);
+            h2d(h, w, dg.data(), sizeof(double) * m);
+            cudaStreamSynchronize(h->stream);
+            release(h, outer);
+            return PSSD_OK;
+        }
+        {
+            Timed t(h, K_HBM, 0);
+            scale_copy(X0, ld, X0, ld, m, m, 1.0 / alpha, h->stream);
+        }
+        double *Y = nullptr;
+        int fi;
+        const double ell = 1e-10;   // conservative lower bound on |lambda(X0)| (reading R7)
+        int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi);
+        if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE) { release(h, mk); continue; }
+        if (st) { release(h, outer); return st; }
+        {
+            Timed t(h, K_HBM, 0);
+            trace_partial(Y, ld, m, tmp, h->stream);
+        }
+        double tr;
+        d2h_sync(h, &tr, tmp, sizeof(double));
+        p = (int)std::lround(0.5 * (m + tr));
+        if (p <= 0 || p >= m) { release(h, mk); continue; }
+        // bases and projected blocks; Bp, Bm persist below the Zolotarev temporaries
+        double *Bp = dalloc(h, (size_t)p * p), *Bm = dalloc(h, (size_t)(m - p) * (m - p));
+        st = sym_split(h, B, Y, m, p, U, Bp, Bm, nullptr, seed + 17 * depth + attempt);
+        if (st) { release(h, mk); continue; }
+        // recurse
+        double *Wp = dalloc(h, (size_t)p * p), *Wm = dalloc(h, (size_t)(m - p) * (m - p));
+        st = sym_eig(h, Bp, p, Wp, w, leaf, depth + 1, maxdepth, seed * 3 + 1);
+        if (!st) st = sym_eig(h, Bm, m - p, Wm, w + p, leaf, depth + 1, maxdepth, seed * 3 + 2);
+        if (st) { release(h, outer); return st; }
+        {   // W = [U_+ W_+, U_- W_-]
+            GemmArgs g; g.m = m; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Wp; g.ldb = p; g.C = W; g.ldc = ld;
+            gemm(h, g);
+            GemmArgs g2; g2.m = m; g2.n = m - p; g2.k = m - p; g2.A = U + p; g2.lda = ld; g2.B = Wm; g2.ldb = m - p;
+            g2.C = W + p; g2.ldc = ld;
+            gemm(h, g2);
+        }
+        release(h, mk);
+        break;
+    }
+    release(h, outer);
+    return PSSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// shared front end: M, L, L^{-1}, K, bounds, Zolotarev sign of K
+// ---------------------------------------------------------------------------
+struct Front {
+    int n = 0, p = 0;
+    double *sig = nullptr;   // device signature
+    double *M = nullptr, *L = nullptr, *Linv = nullptr, *K = nullptr;
+    double *Y = nullptr;     // ~ sign(K)
+    double normH = 0.0;
+};
+
+int validate(int n, const signed char *sigma, const double *H, int ldh)
+{
+    if (n < 1) return -2;
+    if (!sigma && (n % 2)) return -3;
+    if (sigma)
+        for (int i = 0; i < n; ++i) if (sigma[i] != 1 && sigma[i] != -1) return -3;
+    if (!H) return -4;
+    if (ldh < n) return -5;
+    return 0;
+}
+
+int front(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, const pssd_opts &o,
+          pssd_info *info, Front &F)
+{
+    F.n = n;
+    const long long ld = n, nsz = (long long)n * n;
+    std::vector<double> hs(n);
+    int p = 0;
+    for (int i = 0; i < n; ++i) { hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0); p += hs[i] > 0; }
+    F.p = p;
+    if (info) info->p = p;
+    F.sig = dalloc(h, n);
+    h2d(h, F.sig, hs.data(), sizeof(double) * n);
+    F.M = dalloc(h, nsz);
+    F.L = dalloc(h, nsz);
+    F.Linv = dalloc(h, nsz);
+    F.K = dalloc(h, nsz);
+    // a1: M = Sigma H, symmetry defect
+    {
+        int nb = sym_prepare_blocks(n);
+        Mark mk = mark(h);
+        double *part = dalloc(h, 2 * (size_t)nb);
+        {
+            Timed t(h, K_HBM, 0);
+            sym_prepare(H, ldh, F.sig, n, F.M, ld, part, h->stream);
+        }
+        std::vector<double> hp(2 * (size_t)nb);
+        d2h_sync(h, hp.data(), part, hp.size() * sizeof(double));
+        release(h, mk);
+        double d2 = 0, m2 = 0;
+        for (int i = 0; i < nb; ++i) { d2 += hp[2 * i]; m2 += hp[2 * i + 1]; }
+        if (!std::isfinite(d2) || !std::isfinite(m2)) return PSSD_ERR_NONFINITE;
+        F.normH = std::sqrt(m2);
+        if (!(m2 > 0.0)) return PSSD_ERR_NOT_DEFINITE;
+        if (std::sqrt(d2) > 1e-12 * std::sqrt(m2)) return PSSD_ERR_NOT_PSEUDOSYMMETRIC;
+    }
+    // a2: L = chol(M), L^{-1}
+    {
+        Timed t(h, K_HBM, 0);
+        copy_matrix(F.M, ld, F.L, ld, n, n, h->stream);
+    }
+    int fi = -1;
+    if (chol_inv(h, F.L, n, ld, 0, 1, F.Linv, 0, &fi)) {
+        if (info) info->fail_index = fi;
+        return PSSD_ERR_NOT_DEFINITE;
+    }
+    // a3: bounds (reading R5: |lambda(H)| in [lambda_min(M), lambda_max(M)])
+    double alpha = o.alpha, beta = o.beta;
+    if (!(alpha > 0.0) || !(beta > 0.0)) {
+        Mark mk = mark(h);
+        double *v = dalloc(h, n), *w = dalloc(h, n), *u = dalloc(h, n), *tmp = dalloc(h, 32 * (size_t)n + 8);
+        double *M = F.M, *Li = F.Linv;
+        cudaStream_t s = h->stream;
+        if (!(alpha > 0.0)) {
+            double rq = power_max(h, n, [&](double *x, double *y) {
+                Timed t(h, K_GEMV, 2.0 * n * (double)n);
+                gemv(M, ld, 0, TRI_NONE, n, x, y, tmp, s);
+            }, v, w, tmp + 32 * (size_t)n, 60);
+            alpha = 1.05 * rq;
+        }
+        if (!(beta > 0.0)) {
+            double rq = power_max(h, n, [&](double *x, double *y) {
+                Timed t(h, K_GEMV, 2.0 * n * (double)n, 3);
+                gemv(Li, ld, 0, TRI_LOWER, n, x, u, tmp, s);     // u = L^{-1} x
+                gemv(Li, ld, 1, TRI_UPPER, n, u, y, tmp, s);     // y = L^{-T} u
+            }, v, w, tmp + 32 * (size_t)n, 60);
+            beta = 0.9 / rq;
+        }
+        release(h, mk);
+    }
+    if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;
+    if (beta > alpha) beta = alpha;
+    if (info) { info->alpha = alpha; info->beta = beta; }
+    // a5: K = L^T Sigma L (lower, mirrored), X0 = K / alpha
+    {
+        GemmArgs g; g.m = g.n = g.k = n; g.A = F.L; g.lda = ld; g.ta = 1; g.triA = TRI_UPPER; g.kscale = F.sig;
+        g.B = F.L; g.ldb = ld; g.triB = TRI_LOWER; g.C = F.K; g.ldc = ld; g.lowerC = 1;
+        gemm(h, g);
+        mirror(h, F.K, ld, 0, n, 1);
+    }
+    double *X0 = dalloc(h, nsz), *bA = dalloc(h, nsz), *bB = dalloc(h, nsz);
+    {
+        Timed t(h, K_HBM, 0);
+        scale_copy(F.K, ld, X0, ld, n, n, 1.0 / alpha, h->stream);
+    }
+    int maxr = o.max_restarts < 0 ? 2 : o.max_restarts;
+    int st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi);
+    if (st == PSSD_ERR_NOT_DEFINITE && info) info->fail_index = fi;
+    return st;
+}
+
+pssd_opts defaults()
+{
+    pssd_opts o;
+    pssd_opts_init(&o);
+    return o;
+}
+
+void info_init(pssd_info *info)
+{
+    if (!info) return;
+    std::memset(info, 0, sizeof(*info));
+    info->fail_index = -1;
+    info->s2_resid = -1.0;
+    info->jsym_resid = -1.0;
+    info->split_backerr = -1.0;
+}
+
+template <class F>
+int guarded(pssd_handle h, pssd_info *info, F body)
+{
+    if (!h) return -1;
+    auto t0 = std::chrono::steady_clock::now();
+    Mark mk = mark(h);
+    int st;
+    try {
+        st = body();
+        if (st == PSSD_OK) cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { h->last_err = cudaGetErrorString(e); st = PSSD_ERR_CUDA; }
+    } catch (Fail &f) {
+        st = f.code;
+    }
+    cudaStreamSynchronize(h->stream);
+    prof_collect(h);
+    release(h, mk);
+    if (info) info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void pssd_opts_init(pssd_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = PSSD_FP64;
+    o->max_restarts = 2;
+    o->leaf = 64;
+}
+
+int pssd_create(pssd_handle *h, void *stream)
+{
+    if (!h) return -1;
+    *h = new pssd_handle_s();
+    (*h)->stream = (cudaStream_t)stream;
+    return PSSD_OK;
+}
+
+int pssd_destroy(pssd_handle h)
+{
+    if (!h) return -1;
+    cudaStreamSynchronize(h->stream);
+    for (auto &c : h->chunks) cudaFree(c.base);
+    for (auto &e : h->free_events) cudaEventDestroy(e);
+    for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    delete h;
+    return PSSD_OK;
+}
+
+int pssd_set_stream(pssd_handle h, void *stream)
+{
+    if (!h) return -1;
+    h->stream = (cudaStream_t)stream;
+    return PSSD_OK;
+}
+
+const char *pssd_last_cuda_error(pssd_handle h) { return h ? h->last_err.c_str() : "invalid handle"; }
+
+const char *pssd_status_string(int status)
+{
+    switch (status) {
+    case PSSD_OK: return "ok";
+    case PSSD_ERR_NOT_DEFINITE: return "Sigma*H is not positive definite";
+    case PSSD_ERR_NO_CONVERGENCE: return "Zolotarev stopping test failed after the allowed restarts";
+    case PSSD_ERR_BASIS: return "invariant-subspace basis breakdown";
+    case PSSD_ERR_NONFINITE: return "non-finite value in the input or an iterate";
+    case PSSD_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PSSD_ERR_CUDA: return "CUDA error";
+    case PSSD_ERR_ALLOC: return "device allocation failed";
+    case PSSD_ERR_NOT_PSEUDOSYMMETRIC: return "Sigma*H is not symmetric";
+    default: return status < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+int pssd_zolo_coeffs(double ell, int r, double *c, double *a, double *chat, double *ell_next)
+{
+    return zolo_coeffs_host(ell, r, c, a, chat, ell_next);
+}
+
+int pssd_choose_r(double ell, double tau, int r_max)
+{
+    if (!(ell > 0.0) || !(ell <= 1.0)) return -1;
+    if (!(tau > 0.0)) return -2;
+    if (r_max < 1) return -3;
+    return choose_r_host(ell, tau, r_max);
+}
+
+int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
+              const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!S) return -6;
+    if (lds < n) return -7;
+    if (S == H) return -6;
+    pssd_opts o = opts ? *opts : defaults();
+    if (o.precision != PSSD_FP64) return -8;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        Front F;
+        int st = front(h, n, sigma, H, ldh, o, info, F);
+        if (st) return st;
+        const long long ld = n, nsz = (long long)n * n;
+        double *T1 = dalloc(h, nsz);
+        GemmArgs a;   // T1 = Y L^T
+        a.m = a.n = a.k = n; a.A = F.Y; a.lda = ld; a.B = F.L; a.ldb = ld; a.tb = 1; a.triB = TRI_UPPER;
+        a.C = T1; a.ldc = ld;
+        gemm(h, a);
+        GemmArgs b;   // S = L^{-T} T1
+        b.m = b.n = b.k = n; b.A = F.Linv; b.lda = ld; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = ld;
+        b.C = S; b.ldc = lds;
+        gemm(h, b);
+        if (o.flags & 1) {   // residuals
+            double *S2 = dalloc(h, nsz);
+            GemmArgs c; c.m = c.n = c.k = n; c.A = S; c.lda = lds; c.B = S; c.ldb = lds; c.C = S2; c.ldc = ld;
+            gemm(h, c);
+            {
+                Timed t(h, K_HBM, 0);
+                add_diag(S2, ld, n, -1.0, h->stream);
+            }
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+            double d2, y2;
+            frob_pair(h, nullptr, ld, S2, ld, n, n, part, &d2, &y2);
+            if (info) info->s2_resid = std::sqrt(y2);
+        }
+        return PSSD_OK;
+    });
+}
+
+int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *Q, int ldq,
+               double *A11, int lda11, double *A22, int lda22, int *p_out, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!Q) return -6;
+    if (ldq < n) return -7;
+    pssd_opts o = opts ? *opts : defaults();
+    if (o.precision != PSSD_FP64) return -14;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        Front F;
+        int st = front(h, n, sigma, H, ldh, o, info, F);
+        if (st) return st;
+        const int p = F.p, q = n - p;
+        if (p_out) *p_out = p;
+        if (p > 0 && (!A11 || lda11 < p)) return p > 0 && !A11 ? -8 : -9;
+        if (q > 0 && (!A22 || lda22 < q)) return !A22 ? -10 : -11;
+        const long long ld = n, nsz = (long long)n * n;
+        double *U = dalloc(h, nsz);
+        double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
+        double *E = dalloc(h, (size_t)p * q + 1);
+        st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
+        if (st) return st;
+        // C_+ = chol(B_+), C_- = chol(-B_-)
+        double *Cp = dalloc(h, (size_t)p * p + 1), *Cm = dalloc(h, (size_t)q * q + 1);
+        double *X = dalloc(h, nsz);
+        int fi;
+        if (p > 0) {
+            Timed t(h, K_HBM, 0);
+            copy_matrix(Bp, p, Cp, p, p, p, h->stream);
+        }
+        if (q > 0) {
+            Timed t(h, K_HBM, 0);
+            scale_copy(Bm, q, Cm, q, q, q, -1.0, h->stream);
+        }
+        if (p > 0 && chol_inv(h, Cp, p, p, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        if (q > 0 && chol_inv(h, Cm, q, q, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        if (p > 0) {   // X_+ = U_+ C_+, Q_+ = L^{-T} X_+, A11 = C_+^T C_+
+            GemmArgs g; g.m = n; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Cp; g.ldb = p; g.triB = TRI_LOWER;
+            g.C = X; g.ldc = ld;
+            gemm(h, g);
+            GemmArgs a; a.m = p; a.n = p; a.k = p; a.A = Cp; a.lda = p; a.ta = 1; a.triA = TRI_UPPER; a.B = Cp;
+            a.ldb = p; a.triB = TRI_LOWER; a.C = A11; a.ldc = lda11; a.lowerC = 1;
+            gemm(h, a);
+            mirror(h, A11, lda11, 0, p, 1);
+        }
+        if (q > 0) {
+            GemmArgs g; g.m = n; g.n = q; g.k = q; g.A = U + p; g.lda = ld; g.B = Cm; g.ldb = q; g.triB = TRI_LOWER;
+            g.C = X + p; g.ldc = ld;
+            gemm(h, g);
+            GemmArgs a; a.m = q; a.n = q; a.k = q; a.A = Cm; a.lda = q; a.ta = 1; a.triA = TRI_UPPER; a.B = Cm;
+            a.ldb = q; a.triB = TRI_LOWER; a.C = A22; a.ldc = lda22; a.lowerC = 1; a.alpha = -1.0;
+            gemm(h, a);
+            mirror(h, A22, lda22, 0, q, 1);
+        }
+        {
+            GemmArgs g; g.m = g.n = g.k = n; g.A = F.Linv; g.lda = ld; g.ta = 1; g.triA = TRI_UPPER; g.B = X;
+            g.ldb = ld; g.C = Q; g.ldc = ldq;
+            gemm(h, g);
+        }
+        if (info && p > 0 && q > 0) {   // ||Q_+^T M Q_-|| = ||C_+^T E C_-||
+            double *E1 = dalloc(h, (size_t)p * q), *E2 = dalloc(h, (size_t)p * q);
+            GemmArgs a; a.m = p; a.n = q; a.k = p; a.A = Cp; a.lda = p; a.ta = 1; a.triA = TRI_UPPER; a.B = E;
+            a.ldb = q; a.C = E1; a.ldc = q;
+            gemm(h, a);
+            GemmArgs b; b.m = p; b.n = q; b.k = q; b.A = E1; b.lda = q; b.B = Cm; b.ldb = q; b.triB = TRI_LOWER;
+            b.C = E2; b.ldc = q;
+            gemm(h, b);
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(p, q));
+            double d2, y2;
+            frob_pair(h, nullptr, q, E2, q, p, q, part, &d2, &y2);
+            info->split_backerr = std::sqrt(y2) / F.normH;
+        }
+        return PSSD_OK;
+    });
+}
+
+int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
+             double *D, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!V) return -6;
+    if (ldv < n) return -7;
+    if (!D) return -8;
+    pssd_opts o = opts ? *opts : defaults();
+    if (o.precision != PSSD_FP64) return -9;
+    int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        Front F;
+        int st = front(h, n, sigma, H, ldh, o, info, F);
+        if (st) return st;
+        const int p = F.p, q = n - p;
+        const long long ld = n, nsz = (long long)n * n;
+        double *U = dalloc(h, nsz);
+        double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
+        double *E = dalloc(h, (size_t)p * q + 1);
+        st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
+        if (st) return st;
+        double *Wp = dalloc(h, (size_t)p * p + 1), *Wm = dalloc(h, (size_t)q * q + 1);
+        double *w = dalloc(h, n);
+        int maxdepth = 0;
+        if (p > 0) st = sym_eig(h, Bp, p, Wp, w, leaf, 1, &maxdepth, 0x1001ull);
+        if (!st && q > 0) st = sym_eig(h, Bm, q, Wm, w + p, leaf, 1, &maxdepth, 0x2002ull);
+        if (st) return st;
+        if (info) info->levels = maxdepth;
+        double *Uf = dalloc(h, nsz);
+        if (p > 0) {
+            GemmArgs g; g.m = n; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Wp; g.ldb = p; g.C = Uf; g.ldc = ld;
+            gemm(h, g);
+        }
+        if (q > 0) {
+            GemmArgs g; g.m = n; g.n = q; g.k = q; g.A = U + p; g.lda = ld; g.B = Wm; g.ldb = q; g.C = Uf + p;
+            g.ldc = ld;
+            gemm(h, g);
+        }
+        double *Vt = dalloc(h, nsz);
+        {   // V = L^{-T} Uf |Lambda|^{1/2}
+            GemmArgs g; g.m = g.n = g.k = n; g.A = F.Linv; g.lda = ld; g.ta = 1; g.triA = TRI_UPPER; g.B = Uf;
+            g.ldb = ld; g.C = Vt; g.ldc = ld;
+            gemm(h, g);
+        }
+        {
+            Timed t(h, K_HBM, 0, 2);
+            scale_columns(Vt, ld, n, n, w, 1, h->stream);
+            sign_fix_columns(Vt, ld, n, n, h->stream);
+        }
+        // order: positive ascending, then negative by ascending magnitude
+        std::vector<double> hw(n);
+        d2h_sync(h, hw.data(), w, sizeof(double) * n);
+        std::vector<int> pos, neg;
+        for (int i = 0; i < n; ++i) (hw[i] > 0 ? pos : neg).push_back(i);
+        std::stable_sort(pos.begin(), pos.end(), [&](int a, int b) { return hw[a] < hw[b]; });
+        std::stable_sort(neg.begin(), neg.end(), [&](int a, int b) { return hw[a] > hw[b]; });
+        std::vector<int> perm(pos);
+        perm.insert(perm.end(), neg.begin(), neg.end());
+        std::vector<double> hd(n);
+        for (int i = 0; i < n; ++i) hd[i] = hw[perm[i]];
+        int *dperm = ialloc(h, n);
+        h2d(h, dperm, perm.data(), sizeof(int) * n);
+        h2d(h, D, hd.data(), sizeof(double) * n);
+        {
+            Timed t(h, K_HBM, 0);
+            gather_columns(Vt, ld, V, ldv, n, n, dperm, h->stream);
+        }
+        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
+        if (info && p > 0 && q > 0) {
+            // split backward error in the K basis: ||C_+^T (U_+^T U_-) C_-|| needs C; report ||U_+^T U_-||
+            // scaled by ||B_+||^(1/2) ||B_-||^(1/2) as in pssd_split's identity (upper bound)
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(p, q));
+            double d2, y2;
+            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &y2);
+            info->split_backerr = std::sqrt(y2);
+        }
+        return PSSD_OK;
+    });
+}
+
+// --------------------------------------------------------------------------
+// measurement hooks (not part of the method): launch counting and per-kind
+// CUDA-event timing of every kernel launch the library makes
+// --------------------------------------------------------------------------
+int pssd_profile_enable(pssd_handle h, int on)
+{
+    if (!h) return -1;
+    h->prof = on ? 1 : 0;
+    return PSSD_OK;
+}
+
+int pssd_profile_reset(pssd_handle h)
+{
+    if (!h) return -1;
+    for (int i = 0; i < 8; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_count[i] = 0; }
+    h->launches = 0;
+    return PSSD_OK;
+}
+
+int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops)
+{
+    if (!h) return -1;
+    if (kind < 0 || kind >= K_NKIND) return -2;
+    if (total_ms) *total_ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_count[kind];
+    if (flops) *flops = h->prof_flops[kind];
+    return PSSD_OK;
+}
+
+long long pssd_launch_count(pssd_handle h) { return h ? h->launches : -1; }
+
+}  // extern "C"

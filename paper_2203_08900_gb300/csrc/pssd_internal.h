@@ -1,0 +1,75 @@
+// Internal declarations shared by the CUDA translation units of libpssd.
+// Not part of the public C ABI (include/pssd.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pssd {
+
+enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+// C[z] = alpha * op(A[z]) * diag(kscale) * op(B[z]) + beta * Cin[z]
+//   op(A) is m x k, op(B) is k x n, all row-major with leading dimensions.
+//   triA / triB describe the structure of op(A) / op(B): entries outside the
+//   triangle are never read (treated as zero), and k-ranges that multiply
+//   only zeros are skipped.  lowerC: only C[i][j] with i >= j is written.
+//   Batch index z runs over `batch`, pointers advance by the strides (elements).
+struct GemmArgs {
+    int m = 0, n = 0, k = 0, batch = 1;
+    const double *A = nullptr; long long lda = 0, sA = 0; int ta = 0, triA = TRI_NONE;
+    const double *B = nullptr; long long ldb = 0, sB = 0; int tb = 0, triB = TRI_NONE;
+    const double *Cin = nullptr; long long ldcin = 0, sCin = 0;
+    double *C = nullptr; long long ldc = 0, sC = 0;
+    const double *kscale = nullptr;
+    double alpha = 1.0, beta = 0.0;
+    int lowerC = 0;
+};
+void dgemm(const GemmArgs &g, cudaStream_t s);
+
+// Cholesky of the kb x kb diagonal block at (k0,k0) of each batch matrix
+// (lower, in place); its triangular inverse goes to Dinv (64 x 64 per batch,
+// ld 64) and, if Rinv != nullptr, into the same diagonal block of Rinv.
+// info[z] receives (first failing global pivot + 1) if a pivot is not positive.
+void dpotrf_diag(double *A, long long lda, long long sA, int k0, int kb, int batch,
+                 double *Dinv, long long sD, double *Rinv, long long ldr, long long sR,
+                 int *info, cudaStream_t s);
+
+// Elementwise / HBM passes
+void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
+                 double *partials, cudaStream_t s);  // M = sym(diag(sig) H); partials: defect^2, norm^2 per block
+int sym_prepare_blocks(int n);
+void reduce_sum(const double *x, int count, double *out, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
+void mirror_lower(double *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
+void shift_copy_lower(const double *G, long long ldg, double *Z, long long ldz, long long sZ, int n,
+                      const double *shifts, int batch, cudaStream_t s);  // Z[z] = G + shifts[z] I (lower)
+void combine_lower(const double *Zinv, long long ldz, long long sZ, const double *a, int r, int n,
+                   double *T, long long ldt, cudaStream_t s);           // T = sum_z a[z] Zinv[z] (lower)
+void scale_copy(const double *X, long long ldx, double *Y, long long ldy, int m, int n, double alpha,
+                cudaStream_t s);
+void add_diag(double *X, long long ldx, int n, double v, cudaStream_t s);
+void frob_diff(const double *X, long long ldx, const double *Y, long long ldy, int m, int n,
+               double *partials, cudaStream_t s);  // partials[2*b] = sum (X-Y)^2, [2*b+1] = sum Y^2
+int frob_blocks(int m, int n);
+void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaStream_t s);
+void trace_partial(const double *X, long long ldx, int n, double *out, cudaStream_t s);
+void get_diag(const double *X, long long ldx, int n, double *d, cudaStream_t s);
+void row_abs_sum_max(const double *X, long long ldx, int n, double *tmp, double *out, cudaStream_t s);  // tmp: n
+void gemv(const double *A, long long lda, int ta, int tri, int n, const double *x, double *y,
+          double *tmp, cudaStream_t s);  // y = op(A) x, square n; tmp: 32 n doubles (ta = 1)
+void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s);  // x = y/||y||
+void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s);
+void scale_columns(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs,
+                   cudaStream_t s);
+void sign_fix_columns(double *X, long long ldx, int m, int n, cudaStream_t s);
+void gather_columns(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
+                    const int *perm, cudaStream_t s);
+void copy_matrix(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
+                 cudaStream_t s);
+void jacobi_leaf(double *A, long long lda, int m, double *W, long long ldw, double *w,
+                 int *sweeps_out, cudaStream_t s);  // m <= 64; W eigenvectors (columns), w values
+
+// host-side Zolotarev coefficients (theta-function evaluation)
+int zolo_coeffs_host(double ell, int r, double *c, double *a, double *chat, double *ell_next);
+int choose_r_host(double ell, double tau, int r_max);
+
+}  // namespace pssd
