@@ -137,6 +137,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp64e"],
+                    help="fp64: native FP64; mixed: FP32 Zolotarev + FP64-accurate refinement; "
+                         "fp64e: the FP64 algorithm with FP64 emulated on the FP32 pipe")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison solve")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -158,15 +162,21 @@ def main():
     n = args.n
     k = n // 2
     dist_d = ("loguniform", 1e-2, 1e2)
-    H, d1, d2 = G.casida_torch(k, dist_d, seed=1234 + rank, device=dev)
+    if n <= 4096:   # numpy generator (also keeps torch's GPU linear algebra out of profiler runs)
+        Hn, d1, d2 = G.casida(k, dist_d, seed=1234 + rank)
+        H = torch.from_numpy(Hn).to(dev)
+    else:
+        H, d1, d2 = G.casida_torch(k, dist_d, seed=1234 + rank, device=dev)
     H = H.contiguous()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     h = P.Handle(stream)
     p = n // 2
 
-    def step():
-        return P.split(H, handle=h)
+    prec = {"fp64": P.PSSD_FP64, "mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}[args.precision]
+
+    def step(pr=prec):
+        return P.split(H, handle=h, precision=pr)
 
     infos = []
     for _ in range(args.warmup):
@@ -197,12 +207,15 @@ def main():
         tt = torch.tensor([t], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    gemm = h.profile_read(P.K_DGEMM)
-    kinds = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(5)}
+    kinds = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
+    # dominant kernel of this precision mode
+    dom = max(["dgemm", "sgemm", "dfgemm"], key=lambda kk: kinds[kk]["ms"])
+    gemm = kinds[dom]
     last = infos[-1]
     rs = [x for x in last["r_used"][:last["passes"]]]
     # algorithmic FLOPs: the library's exact structural count of every contraction it launched
-    fl = (kinds["dgemm"]["flops"] + kinds["potrf_diag"]["flops"]) / args.steps
+    fl = (kinds["dgemm"]["flops"] + kinds["sgemm"]["flops"] + kinds["dfgemm"]["flops"]
+          + kinds["potrf_diag"]["flops"]) / args.steps
     solves = args.steps * ws
     s_per_solve = t / solves
     # accuracy of the split, measured outside the timed region: S = Q Q^T Sigma,
@@ -218,27 +231,38 @@ def main():
         comm = float(torch.linalg.norm(C) / 4.0 / torch.linalg.norm(H))
         QJQ = float(torch.linalg.norm(Q.T @ (J[:, None] * Q) - torch.diag(J)))
     peak_fp64 = 152 * 2 * 2 * 2.07e9 / 1e12        # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12      # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
     achieved = (gemm["flops"] / gemm["launches"]) / (gemm["ms"] / gemm["launches"] / 1e3) / 1e12 if gemm["launches"] else None
+    # the FP64-emulating kernel spends 13 FP32 instructions per multiply-add (see the design notes):
+    # its ALU roof is the FP32 issue rate / 6.5 in FP64-equivalent FLOP/s
+    peak_dom = {"dgemm": peak_fp64, "sgemm": peak_fp32, "dfgemm": peak_fp32 / 6.5}[dom]
     line = {
         "metric": METRIC, "value": s_per_solve, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "casida_n%d_log1e-2_1e2 split (sign+split), plain FP64 path" % n, "n": n,
-                   "k": k, "precision": "fp64", "l2": "inputs larger than L2 (2.1 GB per H), no flush",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp64e": "f64 (emulated on f32)"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "casida_n%d_log1e-2_1e2 split (sign+split), %s path" % (n, args.precision), "n": n,
+                   "k": k, "precision": args.precision, "l2": "inputs larger than L2 (2.1 GB per H), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "tflops": fl * solves / t / 1e12, "algorithmic_flops_per_solve": fl,
         "r_per_pass": rs, "restarts": last["restarts"], "alpha": last["alpha"], "beta": last["beta"],
         "accuracy": {"s2_resid_est": s2, "s2_bound": 1e-12 * n, "comm_rel_est": comm, "qjq_defect": QJQ,
                      "split_backerr": last["split_backerr"]},
-        "roofline": {"kernel": "dgemm_kernel (FP64 DFMA, 64x64x16 tiles)", "bound": "alu",
-                     "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                     "frac": (achieved / peak_fp64) if achieved else None, "traffic": None,
-                     "peak_note": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (cuBLAS DGEMM measured 1.09)",
+        "roofline": {"kernel": {"dgemm": "gemm_kernel<GM_F64> (FP64 DFMA, 64x64x16 tiles)",
+                                "sgemm": "gemm_kernel<GM_F32> (FP32 FFMA)",
+                                "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated on the FP32 pipe)"}[dom],
+                     "bound": "alu", "achieved": achieved, "peak": peak_dom, "unit": "TFLOP/s",
+                     "frac": (achieved / peak_dom) if achieved else None, "traffic": None,
+                     "peak_note": {"dgemm": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (cuBLAS DGEMM measured 1.09)",
+                                   "sgemm": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz",
+                                   "dfgemm": "derived: FP32 issue rate (152 SM x 128/clk x 2.07 GHz) x 2 flop / 13 instructions per multiply-add"}[dom],
                      "share_of_step": gemm["ms"] / 1e3 / t if t > 0 else None},
         "kernels": kinds,
         "gpu_launches": launches,
         "clocks": ck,
     }
+    line["mixed_info"] = {"fp32_steps": last.get("fp32_steps"), "ns_steps": last.get("ns_steps"),
+                          "ns_resid_K_basis": last.get("ns_resid")} if args.precision == "mixed" else None
     if not args.no_e2e and rank == 0:
         # end to end through the public API with HOST buffers: H2D of H, the solve, D2H of Q, A11, A22
         Hh = H.cpu().pin_memory()
@@ -249,13 +273,30 @@ def main():
         f0 = torch.cuda.Event(enable_timing=True); f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         Hd = Hh.to(dev, non_blocking=True)
-        Q2, B11, B22, _, _ = P.split(Hd, handle=h)
+        Q2, B11, B22, _, _ = P.split(Hd, handle=h, precision=prec)
         Qh.copy_(Q2, non_blocking=True); A11h.copy_(B11, non_blocking=True); A22h.copy_(B22, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
         te = f0.elapsed_time(f1) / 1e3
         line["e2e"] = {"value": te, "unit": "s/solve", "h2d_bytes_per_step": 8 * n * n,
                        "d2h_bytes_per_step": 8 * (n * n + p * p + (n - p) ** 2)}
+    if rank == 0 and not args.no_compare and args.precision != "fp64":
+        # plain FP64 on the same input: one untimed warm-up (allocations), one timed solve
+        step(P.PSSD_FP64)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Qf, A11f, A22f, _, infof = step(P.PSSD_FP64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tf = g0.elapsed_time(g1) / 1e3
+        with torch.no_grad():
+            dA = float(torch.linalg.norm(torch.linalg.eigvalsh(A11f) - torch.linalg.eigvalsh(A11))
+                       / torch.linalg.norm(torch.linalg.eigvalsh(A11f)))
+        line["plain_fp64"] = {"s_per_solve": tf, "speedup_of_this_path": tf / s_per_solve,
+                              "split_backerr": infof["split_backerr"],
+                              "A11_spectrum_rel_diff_vs_this_path": dA,
+                              "note": "same input, 1 warm-up + 1 timed solve"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:

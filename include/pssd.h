@@ -52,8 +52,12 @@ extern "C" {
 #define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
 
 /* precision modes */
-#define PSSD_FP64 0   /* every step in FP64 */
-#define PSSD_MIXED 1  /* Zolotarev steps in FP32 on tensor cores, FP64 refinement */
+#define PSSD_FP64 0          /* every step in native FP64 (DFMA) */
+#define PSSD_MIXED 1         /* Zolotarev steps in FP32; Newton-Schulz refinement, basis and projections in
+                                FP64-accurate arithmetic (FP64 emulated on the FP32 pipe) */
+#define PSSD_FP64_EMULATED 2 /* the PSSD_FP64 algorithm with every contraction in FP64 emulated on the FP32
+                                pipe (float pairs, error-free products, TwoSum, FP64 flush every 64 terms) */
+#define PSSD_FLAG_RESIDUALS 1 /* pssd_sign: also compute info->s2_resid = ||S^2 - I||_F */
 
 typedef struct pssd_handle_s *pssd_handle;
 
@@ -61,10 +65,10 @@ typedef struct {
     int r;              /* Zolotarev rank per step; 0 = smallest r with 1-l_2 <= tau (reading of Sec. 5.3) */
     double alpha;       /* upper bound on max|lambda(H)|; 0 = estimate (power iteration on Sigma H) */
     double beta;        /* lower bound on min|lambda(H)|; 0 = estimate (power iteration on (Sigma H)^{-1}) */
-    int precision;      /* PSSD_FP64 or PSSD_MIXED */
+    int precision;      /* PSSD_FP64, PSSD_MIXED or PSSD_FP64_EMULATED */
     int max_restarts;   /* restarts allowed after a failed stopping test (Alg. 8); < 0 = default (2) */
     int leaf;           /* pssd_eig: subproblems of at most this order are solved by Jacobi; 0 = 64 */
-    int flags;          /* reserved, must be 0 */
+    int flags;          /* PSSD_FLAG_RESIDUALS or 0 */
 } pssd_opts;
 
 typedef struct {
@@ -82,6 +86,10 @@ typedef struct {
     int fail_index;      /* failing Cholesky pivot (0-based) for PSSD_ERR_NOT_DEFINITE, else -1 */
     int levels;          /* pssd_eig: recursion depth reached */
     double seconds;      /* wall time of the call (host clock, stream synchronised) */
+    int precision;       /* precision mode used */
+    int fp32_steps;      /* PSSD_MIXED: FP32 Zolotarev steps taken (r of the first four in r_used, l in ell) */
+    int ns_steps;        /* PSSD_MIXED: Newton-Schulz updates applied */
+    double ns_resid;     /* PSSD_MIXED: ||I - sign(K)^2||_F after refinement, K = L^T Sigma L */
 } pssd_info;
 
 /* Fill `o` with the defaults (r = 0, alpha = beta = 0, FP64, 2 restarts, leaf 64). */

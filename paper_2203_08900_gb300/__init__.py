@@ -18,11 +18,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libpssd.so")
 
 PSSD_FP64 = 0
 PSSD_MIXED = 1
+PSSD_FP64_EMULATED = 2
 FLAG_RESIDUALS = 1
 
 # kinds reported by profile_read
-K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI = range(5)
-KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf"]
+K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM = range(7)
+KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm"]
 
 
 class Opts(ctypes.Structure):
@@ -37,7 +38,8 @@ class Info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("ell", ctypes.c_double * 6), ("stop_crit", ctypes.c_double * 4),
                 ("s2_resid", ctypes.c_double), ("jsym_resid", ctypes.c_double),
                 ("split_backerr", ctypes.c_double), ("fail_index", ctypes.c_int), ("levels", ctypes.c_int),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_steps", ctypes.c_int),
+                ("ns_steps", ctypes.c_int), ("ns_resid", ctypes.c_double)]
 
     def as_dict(self):
         d = {}

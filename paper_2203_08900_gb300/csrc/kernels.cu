@@ -12,86 +12,163 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace pssd {
 
 // --------------------------------------------------------------------------
-// GEMM with triangular operands, lower-only output and inner scaling
+// GEMM with triangular operands, lower-only output and inner scaling, in
+// three arithmetic modes:
+//   GM_F64  FP64 storage, DFMA accumulation
+//   GM_F32  FP32 storage, FFMA accumulation
+//   GM_DF   FP64 storage, FP64 emulated on the FP32 pipe: each operand is
+//           split into a pair of floats (hi = fl32(x), lo = fl32(x - hi)), the
+//           product hi*hi is made error-free with an FMA, the cross terms are
+//           added in FP32, the running sum is a float pair updated by TwoSum
+//           (Knuth) and flushed into an FP64 accumulator every 64 k-steps.
+//           Relative error per k-block ~2^-47; the FP32 pipe issues 64x the
+//           FP64 rate on GB300, so this runs ~4-5x faster than DFMA.
 // --------------------------------------------------------------------------
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-__global__ void __launch_bounds__(256) dgemm_kernel(GemmArgs g)
+template <class T>
+__device__ __forceinline__ T load_op(const T *P, long long ld, int trans, int r, int c)
 {
+    return trans ? P[(long long)c * ld + r] : P[(long long)r * ld + c];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g)
+{
+    using T = typename std::conditional<MODE == GM_F32, float, double>::type;
     const int z = blockIdx.z;
     const int i0 = blockIdx.y * GBM, j0 = blockIdx.x * GBN;
     if (i0 >= g.m || j0 >= g.n) return;
     if (g.lowerC && j0 > i0 + GBM - 1) return;   // tile strictly above the diagonal
 
-    const double *A = g.A + (long long)z * g.sA;
-    const double *B = g.B + (long long)z * g.sB;
+    const T *A = (const T *)g.A + (long long)z * g.sA;
+    const T *B = (const T *)g.B + (long long)z * g.sB;
+    const T *ks = (const T *)g.kscale;
     int kbeg = 0, kend = g.k;
     if (g.triA == TRI_LOWER) kend = min(kend, i0 + GBM);   // op(A)[i][p] = 0 for p > i
     if (g.triA == TRI_UPPER) kbeg = max(kbeg, i0);         // op(A)[i][p] = 0 for p < i
     if (g.triB == TRI_LOWER) kbeg = max(kbeg, j0);         // op(B)[p][j] = 0 for p < j
     if (g.triB == TRI_UPPER) kend = min(kend, j0 + GBN);   // op(B)[p][j] = 0 for p > j
 
-    __shared__ double As[GBK][GBM + 1];
-    __shared__ double Bs[GBK][GBN + 1];
+    using S = typename std::conditional<MODE == GM_F64, double, float>::type;
+    __shared__ S As[GBK][GBM + 1], Bs[GBK][GBN + 1];
+    __shared__ float Asl[MODE == GM_DF ? GBK : 1][GBM + 1], Bsl[MODE == GM_DF ? GBK : 1][GBN + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    T acc[4][4];
+    float ah_[4][4], al_[4][4];   // DF running float pair (unused otherwise)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; ++b) { acc[a][b] = 0; ah_[a][b] = 0.f; al_[a][b] = 0.f; }
 
+    int kt_count = 0;
     for (int kt = kbeg; kt < kend; kt += GBK) {
-        // ---- stage op(A) tile (GBM x GBK) as As[p][i]
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int e = tid + 256 * u;
             int il, pl;
             if (g.ta == 0) { il = e >> 4; pl = e & 15; } else { pl = e >> 6; il = e & 63; }
             int i = i0 + il, p = kt + pl;
-            double v = 0.0;
+            T v = 0;
             bool ok = (i < g.m) && (p < kend);
             if (g.triA == TRI_LOWER) ok = ok && (p <= i);
             if (g.triA == TRI_UPPER) ok = ok && (p >= i);
             if (ok) {
-                v = (g.ta == 0) ? A[(long long)i * g.lda + p] : A[(long long)p * g.lda + i];
-                if (g.kscale) v *= g.kscale[p];
+                v = load_op(A, g.lda, g.ta, i, p);
+                if (ks) v *= ks[p];
             }
-            As[pl][il] = v;
+            if (MODE == GM_DF) {
+                float hi = __double2float_rn((double)v);
+                As[pl][il] = hi;
+                Asl[pl][il] = __double2float_rn((double)v - (double)hi);
+            } else {
+                As[pl][il] = (S)v;
+            }
         }
-        // ---- stage op(B) tile (GBK x GBN) as Bs[p][j]
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int e = tid + 256 * u;
             int jl, pl;
             if (g.tb == 0) { pl = e >> 6; jl = e & 63; } else { jl = e >> 4; pl = e & 15; }
             int j = j0 + jl, p = kt + pl;
-            double v = 0.0;
+            T v = 0;
             bool ok = (j < g.n) && (p < kend);
             if (g.triB == TRI_LOWER) ok = ok && (p >= j);
             if (g.triB == TRI_UPPER) ok = ok && (p <= j);
-            if (ok) v = (g.tb == 0) ? B[(long long)p * g.ldb + j] : B[(long long)j * g.ldb + p];
-            Bs[pl][jl] = v;
+            if (ok) v = load_op(B, g.ldb, g.tb, p, j);
+            if (MODE == GM_DF) {
+                float hi = __double2float_rn((double)v);
+                Bs[pl][jl] = hi;
+                Bsl[pl][jl] = __double2float_rn((double)v - (double)hi);
+            } else {
+                Bs[pl][jl] = (S)v;
+            }
         }
         __syncthreads();
+        if (MODE != GM_DF) {
 #pragma unroll
-        for (int p = 0; p < GBK; ++p) {
-            double a[4], b[4];
+            for (int p = 0; p < GBK; ++p) {
+                S a[4], b[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[p][ty + 16 * q]; b[q] = Bs[p][tx + 16 * q]; }
+                for (int q = 0; q < 4; ++q) { a[q] = As[p][ty + 16 * q]; b[q] = Bs[p][tx + 16 * q]; }
 #pragma unroll
-            for (int qa = 0; qa < 4; ++qa)
+                for (int qa = 0; qa < 4; ++qa)
 #pragma unroll
-                for (int qb = 0; qb < 4; ++qb) acc[qa][qb] = fma(a[qa], b[qb], acc[qa][qb]);
+                    for (int qb = 0; qb < 4; ++qb) acc[qa][qb] = fma((T)a[qa], (T)b[qb], acc[qa][qb]);
+            }
+        } else {
+#pragma unroll 4
+            for (int p = 0; p < GBK; ++p) {
+                float ahv[4], alv[4], bhv[4], blv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ahv[q] = As[p][ty + 16 * q]; alv[q] = Asl[p][ty + 16 * q];
+                    bhv[q] = Bs[p][tx + 16 * q]; blv[q] = Bsl[p][tx + 16 * q];
+                }
+#pragma unroll
+                for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                    for (int qb = 0; qb < 4; ++qb) {
+                        // rounded intrinsics: never contracted, so the transformations stay error-free
+                        float ph = __fmul_rn(ahv[qa], bhv[qb]);
+                        float pe = __fmaf_rn(ahv[qa], bhv[qb], -ph);                 // hi*hi = ph + pe exactly
+                        float cr = __fmaf_rn(ahv[qa], blv[qb], __fmul_rn(alv[qa], bhv[qb]));
+                        float x = ah_[qa][qb];
+                        float s = __fadd_rn(x, ph);                                  // TwoSum(x, ph)
+                        float bp = __fsub_rn(s, x);
+                        float er = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bp)), __fsub_rn(ph, bp));
+                        ah_[qa][qb] = s;
+                        al_[qa][qb] = __fadd_rn(al_[qa][qb], __fadd_rn(er, __fadd_rn(pe, cr)));
+                    }
+            }
+            if (((++kt_count) & 3) == 0) {   // flush the float pairs into FP64 every 64 k
+#pragma unroll
+                for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                    for (int qb = 0; qb < 4; ++qb) {
+                        acc[qa][qb] += (double)ah_[qa][qb] + (double)al_[qa][qb];
+                        ah_[qa][qb] = 0.f; al_[qa][qb] = 0.f;
+                    }
+            }
         }
         __syncthreads();
     }
+    if (MODE == GM_DF) {
+#pragma unroll
+        for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+            for (int qb = 0; qb < 4; ++qb) acc[qa][qb] += (double)ah_[qa][qb] + (double)al_[qa][qb];
+    }
 
-    double *C = g.C + (long long)z * g.sC;
-    const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
+    T *C = (T *)g.C + (long long)z * g.sC;
+    const T *Cin = g.Cin ? (const T *)g.Cin + (long long)z * g.sCin : nullptr;
+    const T alpha = (T)g.alpha, beta = (T)g.beta;
 #pragma unroll
     for (int qa = 0; qa < 4; ++qa) {
         int i = i0 + ty + 16 * qa;
@@ -101,52 +178,57 @@ __global__ void __launch_bounds__(256) dgemm_kernel(GemmArgs g)
             int j = j0 + tx + 16 * qb;
             if (j >= g.n) continue;
             if (g.lowerC && j > i) continue;
-            double v = g.alpha * acc[qa][qb];
-            if (g.beta != 0.0) v += g.beta * Cin[(long long)i * g.ldcin + j];
+            T v = alpha * acc[qa][qb];
+            if (g.beta != 0.0) v += beta * Cin[(long long)i * g.ldcin + j];
             C[(long long)i * g.ldc + j] = v;
         }
     }
 }
 
-void dgemm(const GemmArgs &g, cudaStream_t s)
+void gemm_launch(const GemmArgs &g, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
     dim3 grid((g.n + GBN - 1) / GBN, (g.m + GBM - 1) / GBM, g.batch);
-    dgemm_kernel<<<grid, 256, 0, s>>>(g);
+    switch (g.mode) {
+    case GM_F32: gemm_kernel<GM_F32><<<grid, 256, 0, s>>>(g); break;
+    case GM_DF: gemm_kernel<GM_DF><<<grid, 256, 0, s>>>(g); break;
+    default: gemm_kernel<GM_F64><<<grid, 256, 0, s>>>(g); break;
+    }
 }
 
 // --------------------------------------------------------------------------
 // Cholesky of one diagonal block (<= 64) and its triangular inverse
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) dpotrf_diag_kernel(double *A, long long lda, long long sA, int k0,
-                                                          int kb, double *Dinv, long long sD, double *Rinv,
-                                                          long long ldr, long long sR, int *info)
+template <class T>
+__global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, long long sA, int k0, int kb,
+                                                         T *Dinv, long long sD, T *Rinv, long long ldr,
+                                                         long long sR, int *info)
 {
-    __shared__ double S[64][65];
-    __shared__ double T[64][65];
+    __shared__ T S[64][65];
+    __shared__ T Tm[64][65];
     __shared__ int bad;
     const int z = blockIdx.x, tid = threadIdx.x;
     A += (long long)z * sA;
     if (tid == 0) bad = 0;
     for (int e = tid; e < 64 * 64; e += 256) {
         int i = e >> 6, j = e & 63;
-        double v = 0.0;
+        T v = 0;
         if (i < kb && j <= i) v = A[(long long)(k0 + i) * lda + (k0 + j)];
         S[i][j] = v;
-        T[i][j] = 0.0;
+        Tm[i][j] = 0;
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
         if (tid == 0) {
-            double d = S[j][j];
+            T d = S[j][j];
             if (!(d > 0.0) || !isfinite(d)) {
                 if (!bad) { bad = 1; if (info[z] == 0) info[z] = k0 + j + 1; }
-                d = 1.0;
+                d = 1;
             }
             S[j][j] = sqrt(d);
         }
         __syncthreads();
-        const double piv = S[j][j];
+        const T piv = S[j][j];
         for (int i = j + 1 + tid; i < kb; i += 256) S[i][j] /= piv;
         __syncthreads();
         const int w = kb - j - 1;
@@ -159,30 +241,36 @@ __global__ void __launch_bounds__(256) dpotrf_diag_kernel(double *A, long long l
     // inverse of the lower-triangular factor: column c by forward substitution
     if (tid < kb) {
         const int c = tid;
-        T[c][c] = 1.0 / S[c][c];
+        Tm[c][c] = (T)1 / S[c][c];
         for (int i = c + 1; i < kb; ++i) {
-            double t = 0.0;
-            for (int m = c; m < i; ++m) t = fma(S[i][m], T[m][c], t);
-            T[i][c] = -t / S[i][i];
+            T t = 0;
+            for (int m = c; m < i; ++m) t = fma(S[i][m], Tm[m][c], t);
+            Tm[i][c] = -t / S[i][i];
         }
     }
     __syncthreads();
-    double *D = Dinv + (long long)z * sD;
+    T *D = Dinv + (long long)z * sD;
     for (int e = tid; e < 64 * 64; e += 256) {
         int i = e >> 6, j = e & 63;
-        D[e] = (i < kb && j <= i) ? T[i][j] : 0.0;
+        D[e] = (i < kb && j <= i) ? Tm[i][j] : (T)0;
         if (i < kb && j < kb) {
-            A[(long long)(k0 + i) * lda + (k0 + j)] = (j <= i) ? S[i][j] : 0.0;
-            if (Rinv) Rinv[(long long)z * sR + (long long)(k0 + i) * ldr + (k0 + j)] = (j <= i) ? T[i][j] : 0.0;
+            A[(long long)(k0 + i) * lda + (k0 + j)] = (j <= i) ? S[i][j] : (T)0;
+            if (Rinv) Rinv[(long long)z * sR + (long long)(k0 + i) * ldr + (k0 + j)] = (j <= i) ? Tm[i][j] : (T)0;
         }
     }
 }
 
-void dpotrf_diag(double *A, long long lda, long long sA, int k0, int kb, int batch, double *Dinv,
-                 long long sD, double *Rinv, long long ldr, long long sR, int *info, cudaStream_t s)
+template <class T>
+void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch, T *Dinv, long long sD, T *Rinv,
+                long long ldr, long long sR, int *info, cudaStream_t s)
 {
-    dpotrf_diag_kernel<<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info);
+    potrf_diag_kernel<T><<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info);
 }
+
+template void potrf_diag<double>(double *, long long, long long, int, int, int, double *, long long, double *,
+                                  long long, long long, int *, cudaStream_t);
+template void potrf_diag<float>(float *, long long, long long, int, int, int, float *, long long, float *,
+                                 long long, long long, int *, cudaStream_t);
 
 // --------------------------------------------------------------------------
 // HBM passes with 32x32 shared-memory tiles
@@ -265,16 +353,17 @@ void reduce_sum(const double *x, int count, double *out, cudaStream_t s)
 }
 
 // copy the strictly lower triangle onto the upper one
-__global__ void __launch_bounds__(256) mirror_lower_kernel(double *A, long long lda, long long sA, int n)
+template <class T>
+__global__ void __launch_bounds__(256) mirror_lower_kernel(T *A, long long lda, long long sA, int n)
 {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi < bj) return;
     A += (long long)blockIdx.z * sA;
-    __shared__ double P[TT][TT + 1];
+    __shared__ T P[TT][TT + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int yy = ty; yy < TT; yy += 8) {
         int i = bi * TT + yy, j = bj * TT + tx;
-        P[yy][tx] = (i < n && j < n) ? A[(long long)i * lda + j] : 0.0;
+        P[yy][tx] = (i < n && j < n) ? A[(long long)i * lda + j] : (T)0;
     }
     __syncthreads();
     for (int yy = ty; yy < TT; yy += 8) {
@@ -283,94 +372,118 @@ __global__ void __launch_bounds__(256) mirror_lower_kernel(double *A, long long 
     }
 }
 
-void mirror_lower(double *A, long long lda, long long sA, int n, int batch, cudaStream_t s)
+template <class T>
+void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s)
 {
     int t = (n + TT - 1) / TT;
-    mirror_lower_kernel<<<dim3(t, t, batch), 256, 0, s>>>(A, lda, sA, n);
+    mirror_lower_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, lda, sA, n);
 }
+template void mirror_lower<double>(double *, long long, long long, int, int, cudaStream_t);
+template void mirror_lower<float>(float *, long long, long long, int, int, cudaStream_t);
 
-__global__ void shift_copy_lower_kernel(const double *G, long long ldg, double *Z, long long ldz, long long sZ,
-                                        int n, const double *shifts)
+template <class T>
+__global__ void shift_copy_lower_kernel(const T *G, long long ldg, T *Z, long long ldz, long long sZ, int n,
+                                        const double *shifts)
 {
     const int z = blockIdx.z;
     const int i = blockIdx.y;
-    const double c = shifts[z];
-    double *Zr = Z + (long long)z * sZ + (long long)i * ldz;
-    const double *Gr = G + (long long)i * ldg;
+    const T c = (T)shifts[z];
+    T *Zr = Z + (long long)z * sZ + (long long)i * ldz;
+    const T *Gr = G + (long long)i * ldg;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i && j < n; j += gridDim.x * blockDim.x)
-        Zr[j] = Gr[j] + (i == j ? c : 0.0);
+        Zr[j] = Gr[j] + (i == j ? c : (T)0);
 }
 
-void shift_copy_lower(const double *G, long long ldg, double *Z, long long ldz, long long sZ, int n,
-                      const double *shifts, int batch, cudaStream_t s)
+template <class T>
+void shift_copy_lower(const T *G, long long ldg, T *Z, long long ldz, long long sZ, int n, const double *shifts,
+                      int batch, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 8) gx = 8;
-    shift_copy_lower_kernel<<<dim3(gx, n, batch), 256, 0, s>>>(G, ldg, Z, ldz, sZ, n, shifts);
+    shift_copy_lower_kernel<T><<<dim3(gx, n, batch), 256, 0, s>>>(G, ldg, Z, ldz, sZ, n, shifts);
 }
+template void shift_copy_lower<double>(const double *, long long, double *, long long, long long, int,
+                                       const double *, int, cudaStream_t);
+template void shift_copy_lower<float>(const float *, long long, float *, long long, long long, int,
+                                      const double *, int, cudaStream_t);
 
-__global__ void combine_lower_kernel(const double *Zinv, long long ldz, long long sZ, const double *a, int r,
-                                     int n, double *T, long long ldt)
+template <class T>
+__global__ void combine_lower_kernel(const T *Zinv, long long ldz, long long sZ, const double *a, int r, int n,
+                                     T *Tm, long long ldt)
 {
     const int i = blockIdx.y;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= i && j < n; j += gridDim.x * blockDim.x) {
-        double v = 0.0;
-        for (int q = 0; q < r; ++q) v = fma(a[q], Zinv[(long long)q * sZ + (long long)i * ldz + j], v);
-        T[(long long)i * ldt + j] = v;
+        T v = 0;
+        for (int q = 0; q < r; ++q) v = fma((T)a[q], Zinv[(long long)q * sZ + (long long)i * ldz + j], v);
+        Tm[(long long)i * ldt + j] = v;
     }
 }
 
-void combine_lower(const double *Zinv, long long ldz, long long sZ, const double *a, int r, int n, double *T,
-                   long long ldt, cudaStream_t s)
+template <class T>
+void combine_lower(const T *Zinv, long long ldz, long long sZ, const double *a, int r, int n, T *Tm, long long ldt,
+                   cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 8) gx = 8;
-    combine_lower_kernel<<<dim3(gx, n), 256, 0, s>>>(Zinv, ldz, sZ, a, r, n, T, ldt);
+    combine_lower_kernel<T><<<dim3(gx, n), 256, 0, s>>>(Zinv, ldz, sZ, a, r, n, Tm, ldt);
 }
+template void combine_lower<double>(const double *, long long, long long, const double *, int, int, double *,
+                                    long long, cudaStream_t);
+template void combine_lower<float>(const float *, long long, long long, const double *, int, int, float *,
+                                   long long, cudaStream_t);
 
-__global__ void scale_copy_kernel(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
-                                  double alpha)
+template <class TI, class TO>
+__global__ void scale_copy_kernel(const TI *X, long long ldx, TO *Y, long long ldy, int m, int n, double alpha)
 {
     const int i = blockIdx.y;
     if (i >= m) return;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        Y[(long long)i * ldy + j] = alpha * X[(long long)i * ldx + j];
+        Y[(long long)i * ldy + j] = (TO)(alpha * (double)X[(long long)i * ldx + j]);
 }
 
-void scale_copy(const double *X, long long ldx, double *Y, long long ldy, int m, int n, double alpha,
-                cudaStream_t s)
+template <class TI, class TO>
+void scale_copy(const TI *X, long long ldx, TO *Y, long long ldy, int m, int n, double alpha, cudaStream_t s)
 {
     if (m <= 0 || n <= 0) return;
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    scale_copy_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, alpha);
+    scale_copy_kernel<TI, TO><<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, alpha);
 }
+template void scale_copy<double, double>(const double *, long long, double *, long long, int, int, double, cudaStream_t);
+template void scale_copy<double, float>(const double *, long long, float *, long long, int, int, double, cudaStream_t);
+template void scale_copy<float, double>(const float *, long long, double *, long long, int, int, double, cudaStream_t);
+template void scale_copy<float, float>(const float *, long long, float *, long long, int, int, double, cudaStream_t);
 
 void copy_matrix(const double *X, long long ldx, double *Y, long long ldy, int m, int n, cudaStream_t s)
 {
-    scale_copy(X, ldx, Y, ldy, m, n, 1.0, s);
+    scale_copy<double, double>(X, ldx, Y, ldy, m, n, 1.0, s);
 }
 
-__global__ void add_diag_kernel(double *X, long long ldx, int n, double v)
+template <class T>
+__global__ void add_diag_kernel(T *X, long long ldx, int n, double v)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        X[(long long)i * ldx + i] += v;
+        X[(long long)i * ldx + i] += (T)v;
 }
 
-void add_diag(double *X, long long ldx, int n, double v, cudaStream_t s)
+template <class T>
+void add_diag(T *X, long long ldx, int n, double v, cudaStream_t s)
 {
-    add_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, v);
+    add_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, v);
 }
+template void add_diag<double>(double *, long long, int, double, cudaStream_t);
+template void add_diag<float>(float *, long long, int, double, cudaStream_t);
 
 // per-block partials of ||X - Y||_F^2 and ||Y||_F^2 (grid-stride over rows)
 constexpr int FROB_BLOCKS = 608;  // 4 x 152 SMs
 
-__global__ void __launch_bounds__(256) frob_diff_kernel(const double *X, long long ldx, const double *Y,
-                                                        long long ldy, int m, int n, double *partials)
+template <class T>
+__global__ void __launch_bounds__(256) frob_diff_kernel(const T *X, long long ldx, const T *Y, long long ldy, int m,
+                                                        int n, double *partials)
 {
     __shared__ double red[2][256];
     double d2 = 0.0, y2 = 0.0;
     for (int i = blockIdx.x; i < m; i += gridDim.x) {
         for (int j = threadIdx.x; j < n; j += 256) {
-            double y = Y[(long long)i * ldy + j];
-            double d = (X ? X[(long long)i * ldx + j] : 0.0) - y;
+            double y = (double)Y[(long long)i * ldy + j];
+            double d = (X ? (double)X[(long long)i * ldx + j] : 0.0) - y;
             d2 += d * d; y2 += y * y;
         }
     }
@@ -388,11 +501,13 @@ __global__ void __launch_bounds__(256) frob_diff_kernel(const double *X, long lo
 
 int frob_blocks(int m, int n) { (void)n; return m < FROB_BLOCKS ? (m > 0 ? m : 1) : FROB_BLOCKS; }
 
-void frob_diff(const double *X, long long ldx, const double *Y, long long ldy, int m, int n, double *partials,
-               cudaStream_t s)
+template <class T>
+void frob_diff(const T *X, long long ldx, const T *Y, long long ldy, int m, int n, double *partials, cudaStream_t s)
 {
-    frob_diff_kernel<<<frob_blocks(m, n), 256, 0, s>>>(X, ldx, Y, ldy, m, n, partials);
+    frob_diff_kernel<T><<<frob_blocks(m, n), 256, 0, s>>>(X, ldx, Y, ldy, m, n, partials);
 }
+template void frob_diff<double>(const double *, long long, const double *, long long, int, int, double *, cudaStream_t);
+template void frob_diff<float>(const float *, long long, const float *, long long, int, int, double *, cudaStream_t);
 
 // counter-based normal variates: splitmix64 hash of (seed, index) -> two
 // uniforms -> Box-Muller

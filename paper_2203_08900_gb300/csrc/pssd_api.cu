@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -53,6 +54,7 @@ struct pssd_handle_s {
     double prof_ms[8] = {0}, prof_flops[8] = {0};
     long long prof_count[8] = {0};
     long long launches = 0;
+    int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
 };
 
 namespace {
@@ -120,7 +122,7 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // ---------------------------------------------------------------------------
 // launch accounting and optional per-launch CUDA-event timing
 // ---------------------------------------------------------------------------
-enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_NKIND = 5 };
+enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_NKIND = 7 };
 
 cudaEvent_t get_event(pssd_handle h)
 {
@@ -195,12 +197,19 @@ double gemm_macs(const GemmArgs &g)
     return total * g.batch;
 }
 
-void gemm(pssd_handle h, const GemmArgs &g)
+// mode < 0 in GemmArgs means "double data, the handle's FP64 contraction mode"
+constexpr int GM_DOUBLE = -1;
+
+template <class T> int gm_of() { return std::is_same<T, float>::value ? GM_F32 : GM_DOUBLE; }
+
+void gemm(pssd_handle h, const GemmArgs &g0)
 {
-    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
+    if (g0.m <= 0 || g0.n <= 0 || g0.batch <= 0) return;
+    GemmArgs g = g0;
+    if (g.mode < 0) g.mode = h->dmode;
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
-    Timed t(h, K_DGEMM, fl);
-    dgemm(g, h->stream);
+    Timed t(h, g.mode == GM_F32 ? K_SGEMM : (g.mode == GM_DF ? K_DFGEMM : K_DGEMM), fl);
+    gemm_launch(g, h->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -235,25 +244,31 @@ void frob_pair(pssd_handle h, const double *X, long long ldx, const double *Y, l
 // ---------------------------------------------------------------------------
 // blocked Cholesky (lower, in place) of `batch` matrices; optional inverse
 // ---------------------------------------------------------------------------
-void potrf(pssd_handle h, double *A, int n, long long lda, long long sA, int batch, double *Rinv, long long ldr,
-           long long sR, double *Dinv, int *dinfo)
+template <class T>
+T *talloc(pssd_handle h, size_t count) { return (T *)walloc(h, count * sizeof(T)); }
+
+template <class T>
+void potrf(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T *Rinv, long long ldr,
+           long long sR, T *Dinv, int *dinfo)
 {
     cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
     for (int k0 = 0; k0 < n; k0 += 64) {
         int kb = std::min(64, n - k0);
         {
             Timed t(h, K_POTRF, batch * (kb * (double)kb * kb / 3.0 * 2.0));
-            dpotrf_diag(A, lda, sA, k0, kb, batch, Dinv, 64 * 64, Rinv, ldr, sR, dinfo, h->stream);
+            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, 64 * 64, Rinv, ldr, sR, dinfo, h->stream);
         }
         int rest = n - k0 - kb;
         if (rest <= 0) continue;
         GemmArgs p;                       // L21 = A21 L11^{-T}
+        p.mode = gm_of<T>();
         p.m = rest; p.n = kb; p.k = kb; p.batch = batch;
         p.A = A + (long long)(k0 + kb) * lda + k0; p.lda = lda; p.sA = sA;
         p.B = Dinv; p.ldb = 64; p.sB = 64 * 64; p.tb = 1; p.triB = TRI_UPPER;
         p.C = A + (long long)(k0 + kb) * lda + k0; p.ldc = lda; p.sC = sA;
         gemm(h, p);
         GemmArgs t;                       // A22 -= L21 L21^T (lower)
+        t.mode = gm_of<T>();
         t.m = rest; t.n = rest; t.k = kb; t.batch = batch;
         t.A = p.C; t.lda = lda; t.sA = sA;
         t.B = p.C; t.ldb = lda; t.sB = sA; t.tb = 1;
@@ -274,21 +289,24 @@ int check_info(pssd_handle h, const int *dinfo, int batch, int *fail_index)
 }
 
 // recursive triangular inverse; diagonal 64-blocks must already hold their inverses
-void trtri_rec(pssd_handle h, const double *L, double *Rinv, int off, int s, long long ld, long long sL,
-               long long sR, int batch, double *tmp, long long sT)
+template <class T>
+void trtri_rec(pssd_handle h, const T *L, T *Rinv, int off, int s, long long ld, long long sL, long long sR,
+               int batch, T *tmp, long long sT)
 {
     if (s <= 64) return;
     int nbk = (s + 63) / 64;
     int hh = ((nbk + 1) / 2) * 64;
-    trtri_rec(h, L, Rinv, off, hh, ld, sL, sR, batch, tmp, sT);
-    trtri_rec(h, L, Rinv, off + hh, s - hh, ld, sL, sR, batch, tmp, sT);
+    trtri_rec<T>(h, L, Rinv, off, hh, ld, sL, sR, batch, tmp, sT);
+    trtri_rec<T>(h, L, Rinv, off + hh, s - hh, ld, sL, sR, batch, tmp, sT);
     GemmArgs a;   // T = L21 * inv(L11)
+    a.mode = gm_of<T>();
     a.m = s - hh; a.n = hh; a.k = hh; a.batch = batch;
     a.A = L + (long long)(off + hh) * ld + off; a.lda = ld; a.sA = sL;
     a.B = Rinv + (long long)off * ld + off; a.ldb = ld; a.sB = sR; a.triB = TRI_LOWER;
     a.C = tmp; a.ldc = hh; a.sC = sT;
     gemm(h, a);
     GemmArgs b;   // inv21 = -inv(L22) T
+    b.mode = gm_of<T>();
     b.m = s - hh; b.n = hh; b.k = s - hh; b.batch = batch;
     b.A = Rinv + (long long)(off + hh) * ld + (off + hh); b.lda = ld; b.sA = sR; b.triA = TRI_LOWER;
     b.B = tmp; b.ldb = hh; b.sB = sT;
@@ -298,56 +316,62 @@ void trtri_rec(pssd_handle h, const double *L, double *Rinv, int off, int s, lon
 }
 
 // Cholesky + inverse of `batch` SPD matrices; returns nonzero on breakdown
-int chol_inv(pssd_handle h, double *A, int n, long long lda, long long sA, int batch, double *Rinv, long long sR,
+template <class T>
+int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T *Rinv, long long sR,
              int *fail_index)
 {
     Mark mk = mark(h);
-    double *Dinv = dalloc(h, (size_t)64 * 64 * batch);
+    T *Dinv = talloc<T>(h, (size_t)64 * 64 * batch);
     int *dinfo = ialloc(h, batch);
-    potrf(h, A, n, lda, sA, batch, Rinv, lda, sR, Dinv, dinfo);
+    potrf<T>(h, A, n, lda, sA, batch, Rinv, lda, sR, Dinv, dinfo);
     int bad = check_info(h, dinfo, batch, fail_index);
     if (!bad && Rinv && n > 64) {
         size_t tsz = (size_t)((n + 1) / 2 + 64) * ((n + 1) / 2 + 64);
-        double *tmp = dalloc(h, tsz * batch);
-        trtri_rec(h, A, Rinv, 0, n, lda, sA, sR, batch, tmp, (long long)tsz);
+        T *tmp = talloc<T>(h, tsz * batch);
+        trtri_rec<T>(h, A, Rinv, 0, n, lda, sA, sR, batch, tmp, (long long)tsz);
     }
     release(h, mk);
     return bad;
 }
 
-void mirror(pssd_handle h, double *A, long long lda, long long sA, int n, int batch)
+template <class T>
+void mirror(pssd_handle h, T *A, long long lda, long long sA, int n, int batch)
 {
     Timed t(h, K_HBM, 0);
-    mirror_lower(A, lda, sA, n, batch, h->stream);
+    mirror_lower<T>(A, lda, sA, n, batch, h->stream);
 }
 
 // ---------------------------------------------------------------------------
 // one Zolotarev step on a symmetric m x m X (full storage):
 //   Xn = Chat (X + X T),  T = sum_j a_j (X^2 + c_{2j-1} I)^{-1}
+// (Eq. ZPartialFrac applied to the symmetric congruence iterate)
 // ---------------------------------------------------------------------------
-int zolo_step(pssd_handle h, const double *X, double *Xn, int m, int r, const double *c, const double *a,
-              double chat, int *fail_index)
+template <class T>
+int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, const double *a, double chat,
+              int *fail_index)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
-    double *G = dalloc(h, msz);
-    double *T = dalloc(h, msz);
-    double *Z = dalloc(h, msz * r);
-    double *Ri = dalloc(h, msz * r);
+    T *G = talloc<T>(h, msz);
+    T *Tm = talloc<T>(h, msz);
+    T *Z = talloc<T>(h, msz * r);
+    T *Ri = talloc<T>(h, msz * r);
     double *dsh = dalloc(h, 2 * r + 2);
     std::vector<double> hs(2 * r);
     for (int j = 0; j < r; ++j) { hs[j] = c[2 * j]; hs[r + j] = a[j]; }
     h2d(h, dsh, hs.data(), sizeof(double) * 2 * r);
     GemmArgs g;                                 // G = X X (lower)
+    g.mode = gm_of<T>();
     g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
     gemm(h, g);
     {
         Timed t(h, K_HBM, 0);
-        shift_copy_lower(G, ld, Z, ld, msz, m, dsh, r, h->stream);   // Z_j = G + c_{2j-1} I
+        shift_copy_lower<T>(G, ld, Z, ld, msz, m, dsh, r, h->stream);   // Z_j = G + c_{2j-1} I
     }
-    int bad = chol_inv(h, Z, m, ld, msz, r, Ri, msz, fail_index);     // R_j, R_j^{-1}
+    int bad = chol_inv<T>(h, Z, m, ld, msz, r, Ri, msz, fail_index);   // R_j, R_j^{-1}
     if (bad) { release(h, mk); return PSSD_ERR_NOT_DEFINITE; }
     GemmArgs l;                                 // Z_j^{-1} = R_j^{-T} R_j^{-1} (lower)
+    l.mode = gm_of<T>();
     l.m = l.n = l.k = m; l.batch = r;
     l.A = Ri; l.lda = ld; l.sA = msz; l.ta = 1; l.triA = TRI_UPPER;
     l.B = Ri; l.ldb = ld; l.sB = msz; l.triB = TRI_LOWER;
@@ -355,14 +379,15 @@ int zolo_step(pssd_handle h, const double *X, double *Xn, int m, int r, const do
     gemm(h, l);
     {
         Timed t(h, K_HBM, 0);
-        combine_lower(Z, ld, msz, dsh + r, r, m, T, ld, h->stream);  // T = sum a_j Z_j^{-1}
+        combine_lower<T>(Z, ld, msz, dsh + r, r, m, Tm, ld, h->stream);   // T = sum a_j Z_j^{-1}
     }
-    mirror(h, T, ld, 0, m, 1);
+    mirror<T>(h, Tm, ld, 0, m, 1);
     GemmArgs f;                                 // Xn = chat (X + X T) (lower), then mirror
-    f.m = f.n = f.k = m; f.A = X; f.lda = ld; f.B = T; f.ldb = ld; f.Cin = X; f.ldcin = ld;
+    f.mode = gm_of<T>();
+    f.m = f.n = f.k = m; f.A = X; f.lda = ld; f.B = Tm; f.ldb = ld; f.Cin = X; f.ldcin = ld;
     f.C = Xn; f.ldc = ld; f.alpha = chat; f.beta = chat; f.lowerC = 1;
     gemm(h, f);
-    mirror(h, Xn, ld, 0, m, 1);
+    mirror<T>(h, Xn, ld, 0, m, 1);
     release(h, mk);
     return PSSD_OK;
 }
@@ -407,6 +432,90 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
         ell = ell2;
         X = X2;
     }
+}
+
+// scaled Zolotarev function (Eq. hatZ), product form, for tracking the image of l
+double zolo_eval_host(double x, double ell, int r)
+{
+    double c[128], a[64], chat, l1;
+    zolo_coeffs_host(ell, r, c, a, &chat, &l1);
+    double y = chat * x;
+    for (int j = 0; j < r; ++j) y *= (x * x + c[2 * j + 1]) / (x * x + c[2 * j]);
+    return y;
+}
+
+// Zolotarev steps in FP32 on the symmetric X (|lambda| in [ell, 1]) until the
+// image of ell reaches 1 - tau32.  The shifted FP32 Cholesky factorisations
+// stay well conditioned because every step uses l_used = max(l, ell_floor):
+// c_1(l_used) bounds X^2 + c_1 I below, and eigenvalues below l_used are still
+// mapped monotonically upward (their image is tracked exactly on the host).
+int zolo_sign_fp32(pssd_handle h, float *X0, int m, double ell, double tau32, double ell_floor, float *bufA,
+                   float *bufB, float **Yout, pssd_info *info, int *fail_index)
+{
+    float *X = X0;
+    for (int step = 0; step < 8; ++step) {
+        double eu = std::max(ell, ell_floor);
+        int r = choose_r_host(eu, tau32, 8);
+        double c[128], a[64], chat, l1;
+        zolo_coeffs_host(eu, r, c, a, &chat, &l1);
+        float *Xn = (X == bufA) ? bufB : bufA;
+        int st = zolo_step<float>(h, X, Xn, m, r, c, a, chat, fail_index);
+        if (st) return st;
+        double en = std::min(zolo_eval_host(ell, eu, r), 1.0);
+        if (info) {
+            if (step < 4) info->r_used[step] = r;
+            if (step < 6) info->ell[step] = ell;
+            info->fp32_steps = step + 1; info->steps = step + 1; info->passes = 1;
+        }
+        ell = en;
+        X = Xn;
+        if (1.0 - ell <= tau32) break;
+    }
+    *Yout = X;
+    return PSSD_OK;
+}
+
+// Newton-Schulz refinement of a symmetric Y ~ sign(.):  Y <- Y + Y (I - Y^2) / 2
+// (the FP64 half of the mixed path; contractions in the handle's FP64 mode).
+// Stops when ||I - Y^2||_F <= tol or stops decreasing.
+int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *resid_out, int *its_out)
+{
+    Mark mk = mark(h);
+    const long long ld = m, msz = (long long)m * m;
+    double *G = dalloc(h, msz), *Yn = dalloc(h, msz);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
+    double prev = INFINITY, res = INFINITY;
+    int it = 0;
+    double *cur = Y;
+    for (; it <= max_it; ++it) {
+        GemmArgs g; g.m = g.n = g.k = m; g.A = cur; g.lda = ld; g.B = cur; g.ldb = ld; g.C = G; g.ldc = ld;
+        g.alpha = -1.0; g.lowerC = 1;                                   // G = -Y^2 (lower)
+        gemm(h, g);
+        mirror<double>(h, G, ld, 0, m, 1);
+        {
+            Timed t(h, K_HBM, 0);
+            add_diag<double>(G, ld, m, 1.0, h->stream);                // G = I - Y^2
+        }
+        double d2, y2;
+        frob_pair(h, nullptr, ld, G, ld, m, m, part, &d2, &y2);
+        res = std::sqrt(y2);
+        if (!std::isfinite(res)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        if (res <= tol || res > 0.5 * prev || it == max_it) break;
+        prev = res;
+        GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ld; u.B = G; u.ldb = ld; u.Cin = cur; u.ldcin = ld;
+        u.C = Yn; u.ldc = ld; u.alpha = 0.5; u.beta = 1.0; u.lowerC = 1;   // Y + Y (I - Y^2)/2
+        gemm(h, u);
+        mirror<double>(h, Yn, ld, 0, m, 1);
+        std::swap(cur, Yn);
+    }
+    if (cur != Y) {
+        Timed t(h, K_HBM, 0);
+        copy_matrix(cur, ld, Y, ld, m, m, h->stream);
+    }
+    if (resid_out) *resid_out = res;
+    if (its_out) *its_out = it;
+    release(h, mk);
+    return PSSD_OK;
 }
 
 // power iteration estimate of lambda_max of an SPD operator given by `apply`
@@ -634,6 +743,8 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
           pssd_info *info, Front &F)
 {
     F.n = n;
+    h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : GM_DF;
+    if (info) info->precision = o.precision;
     const long long ld = n, nsz = (long long)n * n;
     std::vector<double> hs(n);
     int p = 0;
@@ -709,10 +820,32 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         gemm(h, g);
         mirror(h, F.K, ld, 0, n, 1);
     }
+    if (o.precision == PSSD_MIXED) {
+        // FP32 Zolotarev steps, then FP64-accurate Newton-Schulz refinement
+        F.Y = dalloc(h, nsz);
+        Mark mk = mark(h);
+        float *X32 = talloc<float>(h, nsz), *fA = talloc<float>(h, nsz), *fB = talloc<float>(h, nsz);
+        {
+            Timed t(h, K_HBM, 0);
+            scale_copy<double, float>(F.K, ld, X32, ld, n, n, 1.0 / alpha, h->stream);
+        }
+        float *Y32 = nullptr;
+        int st = zolo_sign_fp32(h, X32, n, beta / alpha, 1e-6, 3e-3, fA, fB, &Y32, info, &fi);
+        if (st) { if (info) info->fail_index = fi; release(h, mk); return st; }
+        {
+            Timed t(h, K_HBM, 0);
+            scale_copy<float, double>(Y32, ld, F.Y, ld, n, n, 1.0, h->stream);
+        }
+        release(h, mk);
+        double res; int its;
+        st = ns_refine(h, F.Y, n, 1e-14 * n, 4, &res, &its);
+        if (info) { info->ns_steps = its; info->ns_resid = res; }
+        return st;
+    }
     double *X0 = dalloc(h, nsz), *bA = dalloc(h, nsz), *bB = dalloc(h, nsz);
     {
         Timed t(h, K_HBM, 0);
-        scale_copy(F.K, ld, X0, ld, n, n, 1.0 / alpha, h->stream);
+        scale_copy<double, double>(F.K, ld, X0, ld, n, n, 1.0 / alpha, h->stream);
     }
     int maxr = o.max_restarts < 0 ? 2 : o.max_restarts;
     int st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi);
@@ -842,7 +975,7 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
     if (lds < n) return -7;
     if (S == H) return -6;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision != PSSD_FP64) return -8;
+    if (o.precision < 0 || o.precision > 2) return -8;
     info_init(info);
     return guarded(h, info, [&]() -> int {
         Front F;
@@ -884,7 +1017,7 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
     if (!Q) return -6;
     if (ldq < n) return -7;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision != PSSD_FP64) return -14;
+    if (o.precision < 0 || o.precision > 2) return -14;
     info_init(info);
     return guarded(h, info, [&]() -> int {
         Front F;
@@ -912,8 +1045,8 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
             Timed t(h, K_HBM, 0);
             scale_copy(Bm, q, Cm, q, q, q, -1.0, h->stream);
         }
-        if (p > 0 && chol_inv(h, Cp, p, p, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
-        if (q > 0 && chol_inv(h, Cm, q, q, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        if (p > 0 && chol_inv<double>(h, Cp, p, p, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        if (q > 0 && chol_inv<double>(h, Cm, q, q, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
         if (p > 0) {   // X_+ = U_+ C_+, Q_+ = L^{-T} X_+, A11 = C_+^T C_+
             GemmArgs g; g.m = n; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Cp; g.ldb = p; g.triB = TRI_LOWER;
             g.C = X; g.ldc = ld;
@@ -964,7 +1097,7 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
     if (ldv < n) return -7;
     if (!D) return -8;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision != PSSD_FP64) return -9;
+    if (o.precision < 0 || o.precision > 2) return -9;
     int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
     info_init(info);
     return guarded(h, info, [&]() -> int {

@@ -7,6 +7,7 @@
 namespace pssd {
 
 enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2 };
 
 // C[z] = alpha * op(A[z]) * diag(kscale) * op(B[z]) + beta * Cin[z]
 //   op(A) is m x k, op(B) is k x n, all row-major with leading dimensions.
@@ -14,41 +15,51 @@ enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 //   triangle are never read (treated as zero), and k-ranges that multiply
 //   only zeros are skipped.  lowerC: only C[i][j] with i >= j is written.
 //   Batch index z runs over `batch`, pointers advance by the strides (elements).
+//   mode: GM_F64 (double data, DFMA), GM_F32 (float data, FFMA),
+//         GM_DF (double data, FP64 emulated with float pairs on the FP32 pipe).
 struct GemmArgs {
     int m = 0, n = 0, k = 0, batch = 1;
-    const double *A = nullptr; long long lda = 0, sA = 0; int ta = 0, triA = TRI_NONE;
-    const double *B = nullptr; long long ldb = 0, sB = 0; int tb = 0, triB = TRI_NONE;
-    const double *Cin = nullptr; long long ldcin = 0, sCin = 0;
-    double *C = nullptr; long long ldc = 0, sC = 0;
-    const double *kscale = nullptr;
+    const void *A = nullptr; long long lda = 0, sA = 0; int ta = 0, triA = TRI_NONE;
+    const void *B = nullptr; long long ldb = 0, sB = 0; int tb = 0, triB = TRI_NONE;
+    const void *Cin = nullptr; long long ldcin = 0, sCin = 0;
+    void *C = nullptr; long long ldc = 0, sC = 0;
+    const void *kscale = nullptr;   // same element type as A
     double alpha = 1.0, beta = 0.0;
     int lowerC = 0;
+    int mode = -1;   // -1: double data in the caller's FP64 mode (resolved before launch)
 };
-void dgemm(const GemmArgs &g, cudaStream_t s);
+void gemm_launch(const GemmArgs &g, cudaStream_t s);
 
 // Cholesky of the kb x kb diagonal block at (k0,k0) of each batch matrix
 // (lower, in place); its triangular inverse goes to Dinv (64 x 64 per batch,
 // ld 64) and, if Rinv != nullptr, into the same diagonal block of Rinv.
 // info[z] receives (first failing global pivot + 1) if a pivot is not positive.
-void dpotrf_diag(double *A, long long lda, long long sA, int k0, int kb, int batch,
-                 double *Dinv, long long sD, double *Rinv, long long ldr, long long sR,
-                 int *info, cudaStream_t s);
+template <class T>
+void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch,
+                T *Dinv, long long sD, T *Rinv, long long ldr, long long sR,
+                int *info, cudaStream_t s);
 
 // Elementwise / HBM passes
 void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
                  double *partials, cudaStream_t s);  // M = sym(diag(sig) H); partials: defect^2, norm^2 per block
 int sym_prepare_blocks(int n);
 void reduce_sum(const double *x, int count, double *out, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
-void mirror_lower(double *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
-void shift_copy_lower(const double *G, long long ldg, double *Z, long long ldz, long long sZ, int n,
-                      const double *shifts, int batch, cudaStream_t s);  // Z[z] = G + shifts[z] I (lower)
-void combine_lower(const double *Zinv, long long ldz, long long sZ, const double *a, int r, int n,
-                   double *T, long long ldt, cudaStream_t s);           // T = sum_z a[z] Zinv[z] (lower)
-void scale_copy(const double *X, long long ldx, double *Y, long long ldy, int m, int n, double alpha,
+template <class T>
+void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
+template <class T>  // Z[z] = G + shifts[z] I (lower)
+void shift_copy_lower(const T *G, long long ldg, T *Z, long long ldz, long long sZ, int n,
+                      const double *shifts, int batch, cudaStream_t s);
+template <class T>  // T = sum_z a[z] Zinv[z] (lower)
+void combine_lower(const T *Zinv, long long ldz, long long sZ, const double *a, int r, int n,
+                   T *Tm, long long ldt, cudaStream_t s);
+template <class TI, class TO>  // Y = alpha X (with conversion)
+void scale_copy(const TI *X, long long ldx, TO *Y, long long ldy, int m, int n, double alpha,
                 cudaStream_t s);
-void add_diag(double *X, long long ldx, int n, double v, cudaStream_t s);
-void frob_diff(const double *X, long long ldx, const double *Y, long long ldy, int m, int n,
-               double *partials, cudaStream_t s);  // partials[2*b] = sum (X-Y)^2, [2*b+1] = sum Y^2
+template <class T>
+void add_diag(T *X, long long ldx, int n, double v, cudaStream_t s);
+template <class T>  // partials[2*b] = sum (X-Y)^2, [2*b+1] = sum Y^2 (X may be null)
+void frob_diff(const T *X, long long ldx, const T *Y, long long ldy, int m, int n,
+               double *partials, cudaStream_t s);
 int frob_blocks(int m, int n);
 void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaStream_t s);
 void trace_partial(const double *X, long long ldx, int n, double *out, cudaStream_t s);
