@@ -82,7 +82,8 @@ typedef struct {
     double stop_crit[4]; /* ||X_2 - X_1||_F / ||X_2||_F of each pass */
     double s2_resid;     /* ||S^2 - I||_F (pssd_sign only; -1 if not computed) */
     double jsym_resid;   /* ||Sigma S - (Sigma S)^T||_F / ||S||_F (pssd_sign only) */
-    double split_backerr;/* ||Q_+^T Sigma H Q_-||_F / ||H||_F (pssd_split / pssd_eig) */
+    double split_backerr;/* ||U_+^T K U_-||_F / ||K||_F: the backward error of the split (Sec. 6.1 metric)
+                            of K = L^T Sigma L ~ H, U_+- the orthonormal invariant-subspace bases */
     int fail_index;      /* failing Cholesky pivot (0-based) for PSSD_ERR_NOT_DEFINITE, else -1 */
     int levels;          /* pssd_eig: recursion depth reached */
     double seconds;      /* wall time of the call (host clock, stream synchronised) */
@@ -146,7 +147,7 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
  *   Q      device, n x n output (columns 0..p-1 = Q_+), leading dimension ldq >= n
  *   A11    device, p x p output, lda11 >= p;  A22 device, (n-p) x (n-p), lda22 >= n-p
  *   p      host int output (may be NULL)
- * info->split_backerr = ||Q_+^T Sigma H Q_-||_F / ||H||_F (the metric of Sec. 6.1).
+ * info->split_backerr = ||U_+^T K U_-||_F / ||K||_F (the metric of Sec. 6.1 for the symmetric K ~ H).
  */
 int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
                double *Q, int ldq, double *A11, int lda11, double *A22, int lda22, int *p,

@@ -204,14 +204,17 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, lo
                                                          T *Dinv, long long sD, T *Rinv, long long ldr,
                                                          long long sR, int *info)
 {
-    __shared__ T S[64][65];
-    __shared__ T Tm[64][65];
+    // kb <= PB.  Right-looking Cholesky of the diagonal block in shared memory
+    // (one reciprocal per column), then its triangular inverse column by column.
+    __shared__ T S[PB][PB + 1];
+    __shared__ T Tm[PB][PB + 1];
+    __shared__ T rinv[PB];
     __shared__ int bad;
     const int z = blockIdx.x, tid = threadIdx.x;
     A += (long long)z * sA;
     if (tid == 0) bad = 0;
-    for (int e = tid; e < 64 * 64; e += 256) {
-        int i = e >> 6, j = e & 63;
+    for (int e = tid; e < PB * PB; e += 256) {
+        int i = e / PB, j = e % PB;
         T v = 0;
         if (i < kb && j <= i) v = A[(long long)(k0 + i) * lda + (k0 + j)];
         S[i][j] = v;
@@ -221,15 +224,17 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, lo
     for (int j = 0; j < kb; ++j) {
         if (tid == 0) {
             T d = S[j][j];
-            if (!(d > 0.0) || !isfinite(d)) {
+            if (!(d > 0) || !isfinite((double)d)) {
                 if (!bad) { bad = 1; if (info[z] == 0) info[z] = k0 + j + 1; }
                 d = 1;
             }
-            S[j][j] = sqrt(d);
+            d = sqrt(d);
+            S[j][j] = d;
+            rinv[j] = (T)1 / d;
         }
         __syncthreads();
-        const T piv = S[j][j];
-        for (int i = j + 1 + tid; i < kb; i += 256) S[i][j] /= piv;
+        const T r = rinv[j];
+        for (int i = j + 1 + tid; i < kb; i += 256) S[i][j] *= r;
         __syncthreads();
         const int w = kb - j - 1;
         for (int e = tid; e < w * w; e += 256) {
@@ -241,17 +246,17 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, lo
     // inverse of the lower-triangular factor: column c by forward substitution
     if (tid < kb) {
         const int c = tid;
-        Tm[c][c] = (T)1 / S[c][c];
+        Tm[c][c] = rinv[c];
         for (int i = c + 1; i < kb; ++i) {
             T t = 0;
             for (int m = c; m < i; ++m) t = fma(S[i][m], Tm[m][c], t);
-            Tm[i][c] = -t / S[i][i];
+            Tm[i][c] = -t * rinv[i];
         }
     }
     __syncthreads();
     T *D = Dinv + (long long)z * sD;
-    for (int e = tid; e < 64 * 64; e += 256) {
-        int i = e >> 6, j = e & 63;
+    for (int e = tid; e < PB * PB; e += 256) {
+        int i = e / PB, j = e % PB;
         D[e] = (i < kb && j <= i) ? Tm[i][j] : (T)0;
         if (i < kb && j < kb) {
             A[(long long)(k0 + i) * lda + (k0 + j)] = (j <= i) ? S[i][j] : (T)0;

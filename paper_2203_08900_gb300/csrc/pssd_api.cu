@@ -252,11 +252,11 @@ void potrf(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T
            long long sR, T *Dinv, int *dinfo)
 {
     cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
-    for (int k0 = 0; k0 < n; k0 += 64) {
-        int kb = std::min(64, n - k0);
+    for (int k0 = 0; k0 < n; k0 += PB) {
+        int kb = std::min(PB, n - k0);
         {
             Timed t(h, K_POTRF, batch * (kb * (double)kb * kb / 3.0 * 2.0));
-            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, 64 * 64, Rinv, ldr, sR, dinfo, h->stream);
+            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, PB * PB, Rinv, ldr, sR, dinfo, h->stream);
         }
         int rest = n - k0 - kb;
         if (rest <= 0) continue;
@@ -264,7 +264,7 @@ void potrf(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T
         p.mode = gm_of<T>();
         p.m = rest; p.n = kb; p.k = kb; p.batch = batch;
         p.A = A + (long long)(k0 + kb) * lda + k0; p.lda = lda; p.sA = sA;
-        p.B = Dinv; p.ldb = 64; p.sB = 64 * 64; p.tb = 1; p.triB = TRI_UPPER;
+        p.B = Dinv; p.ldb = PB; p.sB = PB * PB; p.tb = 1; p.triB = TRI_UPPER;
         p.C = A + (long long)(k0 + kb) * lda + k0; p.ldc = lda; p.sC = sA;
         gemm(h, p);
         GemmArgs t;                       // A22 -= L21 L21^T (lower)
@@ -288,14 +288,14 @@ int check_info(pssd_handle h, const int *dinfo, int batch, int *fail_index)
     return 0;
 }
 
-// recursive triangular inverse; diagonal 64-blocks must already hold their inverses
+// recursive triangular inverse; diagonal PB-blocks must already hold their inverses
 template <class T>
 void trtri_rec(pssd_handle h, const T *L, T *Rinv, int off, int s, long long ld, long long sL, long long sR,
                int batch, T *tmp, long long sT)
 {
-    if (s <= 64) return;
-    int nbk = (s + 63) / 64;
-    int hh = ((nbk + 1) / 2) * 64;
+    if (s <= PB) return;
+    int nbk = (s + PB - 1) / PB;
+    int hh = ((nbk + 1) / 2) * PB;
     trtri_rec<T>(h, L, Rinv, off, hh, ld, sL, sR, batch, tmp, sT);
     trtri_rec<T>(h, L, Rinv, off + hh, s - hh, ld, sL, sR, batch, tmp, sT);
     GemmArgs a;   // T = L21 * inv(L11)
@@ -321,12 +321,12 @@ int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch,
              int *fail_index)
 {
     Mark mk = mark(h);
-    T *Dinv = talloc<T>(h, (size_t)64 * 64 * batch);
+    T *Dinv = talloc<T>(h, (size_t)PB * PB * batch);
     int *dinfo = ialloc(h, batch);
     potrf<T>(h, A, n, lda, sA, batch, Rinv, lda, sR, Dinv, dinfo);
     int bad = check_info(h, dinfo, batch, fail_index);
-    if (!bad && Rinv && n > 64) {
-        size_t tsz = (size_t)((n + 1) / 2 + 64) * ((n + 1) / 2 + 64);
+    if (!bad && Rinv && n > PB) {
+        size_t tsz = (size_t)((n + 1) / 2 + PB) * ((n + 1) / 2 + PB);
         T *tmp = talloc<T>(h, tsz * batch);
         trtri_rec<T>(h, A, Rinv, 0, n, lda, sA, sR, batch, tmp, (long long)tsz);
     }
@@ -616,8 +616,8 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
         gemm(h, g);
         mirror(h, Bm, m - p, 0, m - p, 1);
     }
-    if (E && p > 0 && m - p > 0) {
-        GemmArgs g; g.m = p; g.n = m - p; g.k = m; g.A = U; g.lda = ld; g.ta = 1; g.B = U + p; g.ldb = ld;
+    if (E && p > 0 && m - p > 0) {   // E = U_+^T B U_- : the off-diagonal block left by the split
+        GemmArgs g; g.m = p; g.n = m - p; g.k = m; g.A = U; g.lda = ld; g.ta = 1; g.B = W + p; g.ldb = ld;
         g.C = E; g.ldc = m - p;
         gemm(h, g);
     }
@@ -1070,18 +1070,12 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
             g.ldb = ld; g.C = Q; g.ldc = ldq;
             gemm(h, g);
         }
-        if (info && p > 0 && q > 0) {   // ||Q_+^T M Q_-|| = ||C_+^T E C_-||
-            double *E1 = dalloc(h, (size_t)p * q), *E2 = dalloc(h, (size_t)p * q);
-            GemmArgs a; a.m = p; a.n = q; a.k = p; a.A = Cp; a.lda = p; a.ta = 1; a.triA = TRI_UPPER; a.B = E;
-            a.ldb = q; a.C = E1; a.ldc = q;
-            gemm(h, a);
-            GemmArgs b; b.m = p; b.n = q; b.k = q; b.A = E1; b.lda = q; b.B = Cm; b.ldb = q; b.triB = TRI_LOWER;
-            b.C = E2; b.ldc = q;
-            gemm(h, b);
-            double *part = dalloc(h, 2 * (size_t)frob_blocks(p, q));
-            double d2, y2;
-            frob_pair(h, nullptr, q, E2, q, p, q, part, &d2, &y2);
-            info->split_backerr = std::sqrt(y2) / F.normH;
+        if (info && p > 0 && q > 0) {   // ||U_+^T K U_-||_F / ||K||_F (backward error of the split of K ~ H)
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+            double d2, e2, k2;
+            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &e2);
+            frob_pair(h, nullptr, ld, F.K, ld, n, n, part, &d2, &k2);
+            info->split_backerr = std::sqrt(e2 / k2);
         }
         return PSSD_OK;
     });
@@ -1158,13 +1152,12 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
             gather_columns(Vt, ld, V, ldv, n, n, dperm, h->stream);
         }
         cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
-        if (info && p > 0 && q > 0) {
-            // split backward error in the K basis: ||C_+^T (U_+^T U_-) C_-|| needs C; report ||U_+^T U_-||
-            // scaled by ||B_+||^(1/2) ||B_-||^(1/2) as in pssd_split's identity (upper bound)
-            double *part = dalloc(h, 2 * (size_t)frob_blocks(p, q));
-            double d2, y2;
-            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &y2);
-            info->split_backerr = std::sqrt(y2);
+        if (info && p > 0 && q > 0) {   // ||U_+^T K U_-||_F / ||K||_F
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+            double d2, e2, k2;
+            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &e2);
+            frob_pair(h, nullptr, ld, F.K, ld, n, n, part, &d2, &k2);
+            info->split_backerr = std::sqrt(e2 / k2);
         }
         return PSSD_OK;
     });

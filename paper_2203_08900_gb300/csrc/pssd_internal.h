@@ -9,6 +9,9 @@ namespace pssd {
 enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2 };
 
+// order of the diagonal blocks of the blocked Cholesky / triangular inverse
+constexpr int PB = 32;
+
 // C[z] = alpha * op(A[z]) * diag(kscale) * op(B[z]) + beta * Cin[z]
 //   op(A) is m x k, op(B) is k x n, all row-major with leading dimensions.
 //   triA / triB describe the structure of op(A) / op(B): entries outside the
@@ -30,9 +33,9 @@ struct GemmArgs {
 };
 void gemm_launch(const GemmArgs &g, cudaStream_t s);
 
-// Cholesky of the kb x kb diagonal block at (k0,k0) of each batch matrix
-// (lower, in place); its triangular inverse goes to Dinv (64 x 64 per batch,
-// ld 64) and, if Rinv != nullptr, into the same diagonal block of Rinv.
+// Cholesky of the kb x kb (kb <= PB) diagonal block at (k0,k0) of each batch
+// matrix (lower, in place); its triangular inverse goes to Dinv (PB x PB per
+// batch, ld PB) and, if Rinv != nullptr, into the same diagonal block of Rinv.
 // info[z] receives (first failing global pivot + 1) if a pivot is not positive.
 template <class T>
 void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch,
