@@ -337,6 +337,36 @@ void sym_prepare(const double *H, long long ldh, const double *sig, int n, doubl
     sym_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(H, ldh, sig, n, M, ldm, partials);
 }
 
+// S <- (S + Sigma S^T Sigma) / 2: the nearest Sigma-symmetric matrix (Sigma S symmetric), in
+// place, over 32x32 tile pairs
+__global__ void __launch_bounds__(256) j_resym_kernel(double *S, long long lds, const double *sig, int n)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi < bj) return;
+    __shared__ double P[TT][TT + 1], Q[TT][TT + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bi * TT + yy, j = bj * TT + tx;
+        P[yy][tx] = (i < n && j < n) ? S[(long long)i * lds + j] : 0.0;
+        int i2 = bj * TT + yy, j2 = bi * TT + tx;
+        Q[yy][tx] = (i2 < n && j2 < n) ? S[(long long)i2 * lds + j2] : 0.0;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bi * TT + yy, j = bj * TT + tx;
+        if (i < n && j < n) S[(long long)i * lds + j] = 0.5 * (P[yy][tx] + sig[i] * sig[j] * Q[tx][yy]);
+        int i2 = bj * TT + yy, j2 = bi * TT + tx;
+        if (bi != bj && i2 < n && j2 < n)
+            S[(long long)i2 * lds + j2] = 0.5 * (Q[yy][tx] + sig[i2] * sig[j2] * P[tx][yy]);
+    }
+}
+
+void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s)
+{
+    int t = (n + TT - 1) / TT;
+    j_resym_kernel<<<dim3(t, t), 256, 0, s>>>(S, lds, sig, n);
+}
+
 // fixed-order single-block sum (deterministic)
 __global__ void reduce_sum_kernel(const double *x, int count, int stride, double *out)
 {

@@ -478,20 +478,23 @@ int zolo_sign_fp32(pssd_handle h, float *X0, int m, double ell, double tau32, do
 // Newton-Schulz refinement of a symmetric Y ~ sign(.):  Y <- Y + Y (I - Y^2) / 2
 // (the FP64 half of the mixed path; contractions in the handle's FP64 mode).
 // Stops when ||I - Y^2||_F <= tol or stops decreasing.
-int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *resid_out, int *its_out)
+int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *resid_out, int *its_out,
+              bool symmetric = true, long long ldy = 0)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
+    if (ldy == 0) ldy = ld;
     double *G = dalloc(h, msz), *Yn = dalloc(h, msz);
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
     double prev = INFINITY, res = INFINITY;
     int it = 0;
     double *cur = Y;
+    long long ldc = ldy;
     for (; it <= max_it; ++it) {
-        GemmArgs g; g.m = g.n = g.k = m; g.A = cur; g.lda = ld; g.B = cur; g.ldb = ld; g.C = G; g.ldc = ld;
-        g.alpha = -1.0; g.lowerC = 1;                                   // G = -Y^2 (lower)
+        GemmArgs g; g.m = g.n = g.k = m; g.A = cur; g.lda = ldc; g.B = cur; g.ldb = ldc; g.C = G; g.ldc = ld;
+        g.alpha = -1.0; g.lowerC = symmetric ? 1 : 0;                   // G = -Y^2
         gemm(h, g);
-        mirror<double>(h, G, ld, 0, m, 1);
+        if (symmetric) mirror<double>(h, G, ld, 0, m, 1);
         {
             Timed t(h, K_HBM, 0);
             add_diag<double>(G, ld, m, 1.0, h->stream);                // G = I - Y^2
@@ -502,15 +505,16 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
         if (!std::isfinite(res)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (res <= tol || res > 0.5 * prev || it == max_it) break;
         prev = res;
-        GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ld; u.B = G; u.ldb = ld; u.Cin = cur; u.ldcin = ld;
-        u.C = Yn; u.ldc = ld; u.alpha = 0.5; u.beta = 1.0; u.lowerC = 1;   // Y + Y (I - Y^2)/2
+        GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ldc; u.B = G; u.ldb = ld; u.Cin = cur; u.ldcin = ldc;
+        u.C = Yn; u.ldc = ld; u.alpha = 0.5; u.beta = 1.0; u.lowerC = symmetric ? 1 : 0;   // Y + Y (I - Y^2)/2
         gemm(h, u);
-        mirror<double>(h, Yn, ld, 0, m, 1);
-        std::swap(cur, Yn);
+        if (symmetric) mirror<double>(h, Yn, ld, 0, m, 1);
+        if (cur == Y) { cur = Yn; Yn = dalloc(h, msz); } else std::swap(cur, Yn);
+        ldc = ld;
     }
     if (cur != Y) {
         Timed t(h, K_HBM, 0);
-        copy_matrix(cur, ld, Y, ld, m, m, h->stream);
+        copy_matrix(cur, ld, Y, ldy, m, m, h->stream);
     }
     if (resid_out) *resid_out = res;
     if (its_out) *its_out = it;
@@ -991,6 +995,18 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
         b.m = b.n = b.k = n; b.A = F.Linv; b.lda = ld; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = ld;
         b.C = S; b.ldc = lds;
         gemm(h, b);
+        if (o.precision == PSSD_MIXED) {
+            // north star (1): J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
+            // Sigma-symmetric S stay Sigma-symmetric), in FP64-accurate arithmetic
+            {
+                Timed t(h, K_HBM, 0);
+                j_resym(S, lds, F.sig, n, h->stream);
+            }
+            double res; int its;
+            int st2 = ns_refine(h, S, n, 1e-14 * n, 3, &res, &its, false, lds);
+            if (st2) return st2;
+            if (info) info->ns_steps += its;
+        }
         if (o.flags & 1) {   // residuals
             double *S2 = dalloc(h, nsz);
             GemmArgs c; c.m = c.n = c.k = n; c.A = S; c.lda = lds; c.B = S; c.ldb = lds; c.C = S2; c.ldc = ld;

@@ -46,7 +46,8 @@ void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch,
 void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
                  double *partials, cudaStream_t s);  // M = sym(diag(sig) H); partials: defect^2, norm^2 per block
 int sym_prepare_blocks(int n);
-void reduce_sum(const double *x, int count, double *out, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
+void reduce_sum(const double *x, int count, double *out, cudaStream_t s);
+void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s);  // S = (S + Sig S^T Sig)/2  // out[0] = sum x (one block, fixed order)
 template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
 template <class T>  // Z[z] = G + shifts[z] I (lower)
