@@ -367,6 +367,46 @@ void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s)
     j_resym_kernel<<<dim3(t, t), 256, 0, s>>>(S, lds, sig, n);
 }
 
+// Daleckii-Krein weights of the sign function:
+//   X[i][j] = W[i][j] (s_i - s_j) / (lam_i - lam_j) + [i == j] lambar_i,  s = sign(lam)
+// (divided differences of sign(x); zero between eigenvalues of the same sign)
+__global__ void dk_combine_kernel(const double *W, long long ldw, const double *lam, const double *lambar, int n,
+                                  double *X, long long ldx)
+{
+    const int i = blockIdx.y;
+    const double li = lam[i];
+    const double si = li > 0.0 ? 1.0 : -1.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double lj = lam[j];
+        const double sj = lj > 0.0 ? 1.0 : -1.0;
+        double v = (si != sj) ? W[(long long)i * ldw + j] * (si - sj) / (li - lj) : 0.0;
+        if (i == j && lambar) v += lambar[i];
+        X[(long long)i * ldx + j] = v;
+    }
+}
+
+void dk_combine(const double *W, long long ldw, const double *lam, const double *lambar, int n, double *X,
+                long long ldx, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    dk_combine_kernel<<<dim3(gx, n), 256, 0, s>>>(W, ldw, lam, lambar, n, X, ldx);
+}
+
+// X[i][j] *= r[i] (row scaling)
+__global__ void scale_rows_kernel(double *X, long long ldx, int m, int n, const double *r)
+{
+    const int i = blockIdx.y;
+    const double f = r[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        X[(long long)i * ldx + j] *= f;
+}
+
+void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    scale_rows_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, r);
+}
+
 // fixed-order single-block sum (deterministic)
 __global__ void reduce_sum_kernel(const double *x, int count, int stride, double *out)
 {

@@ -47,7 +47,10 @@ void sym_prepare(const double *H, long long ldh, const double *sig, int n, doubl
                  double *partials, cudaStream_t s);  // M = sym(diag(sig) H); partials: defect^2, norm^2 per block
 int sym_prepare_blocks(int n);
 void reduce_sum(const double *x, int count, double *out, cudaStream_t s);
-void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s);  // S = (S + Sig S^T Sig)/2  // out[0] = sum x (one block, fixed order)
+void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s);  // S = (S + Sig S^T Sig)/2
+void dk_combine(const double *W, long long ldw, const double *lam, const double *lambar, int n, double *X,
+                long long ldx, cudaStream_t s);  // Daleckii-Krein weights of sign(), plus diag(lambar)
+void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
 template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
 template <class T>  // Z[z] = G + shifts[z] I (lower)
