@@ -50,6 +50,7 @@ extern "C" {
 #define PSSD_ERR_CUDA 6                /* a CUDA call failed; see pssd_last_cuda_error */
 #define PSSD_ERR_ALLOC 7               /* workspace allocation failed */
 #define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
+#define PSSD_ERR_NOALLOC_TOO_LARGE 9   /* pssd_sign_noalloc: n exceeds PSSD_NOALLOC_MAX_N */
 
 /* precision modes */
 #define PSSD_FP64 0          /* every step in native FP64 (DFMA) */
@@ -165,6 +166,34 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
  */
 int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
              double *V, int ldv, double *D, const pssd_opts *opts, pssd_info *info);
+
+/*
+ * Allocation-free pssd_sign for small problems (the paper has no counterpart;
+ * this exists for callers of the library).
+ *
+ * Some callers cannot call cudaMalloc: code running while a CUDA graph is
+ * being captured, applications whose device memory belongs to their own pool,
+ * and latency-critical loops that cannot afford a first-call allocation.
+ * pssd_sign_noalloc computes exactly what pssd_sign computes (same arguments,
+ * same results) but takes every temporary from one fixed scratch array of
+ * PSSD_NOALLOC_SCRATCH_BYTES in the library's device memory, which every GPU
+ * that loads the library holds until the process exits.  It calls no
+ * cudaMalloc or cudaFree, and the handle's own workspace is not touched.
+ *   - n must be at most PSSD_NOALLOC_MAX_N; larger n returns
+ *     PSSD_ERR_NOALLOC_TOO_LARGE without doing any work.
+ *   - The first call on each device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture begins.
+ *   - All calls on a device share the one array and it keeps the previous
+ *     call's contents (every value the computation reads is written first in
+ *     the same call).  Calls that can overlap on the GPU -- on different
+ *     streams, or from several host threads -- race on the array: serialise
+ *     them.
+ */
+#define PSSD_NOALLOC_MAX_N 128
+#define PSSD_NOALLOC_SCRATCH_BYTES (8u << 20)
+int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                      double *S, int lds, const pssd_opts *opts, pssd_info *info);
 
 #ifdef __cplusplus
 }

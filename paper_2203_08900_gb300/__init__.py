@@ -60,7 +60,9 @@ _lib = None
 # C-ABI symbols declared in include/pssd.h plus the measurement hooks
 EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
-           "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count"]
+           "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
+           "pssd_sign_noalloc"]
+NOALLOC_MAX_N = 128
 
 
 def lib():
@@ -88,6 +90,7 @@ def lib():
     L.pssd_split.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ip,
                                    ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_eig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pssd_profile_reset.argtypes = [vp]
     L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
@@ -213,6 +216,24 @@ def sign(H, sigma=None, handle=None, **kw):
     o = _opts(**kw)
     st = lib().pssd_sign(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
                          S.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return S, info.as_dict()
+
+
+def sign_noalloc(H, S=None, sigma=None, handle=None, **kw):
+    """pssd_sign_noalloc: S = sign(H) for n <= 128 with every temporary taken
+    from the library's fixed device scratch array (no device allocation by the
+    library; pass a preallocated S to allocate nothing at all).  Returns
+    (S, info dict)."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    if S is None:
+        S = torch.empty_like(H)
+    keep, sp = _sigma(n, sigma)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_sign_noalloc(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
+                                 S.stride(0), ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return S, info.as_dict()
 

@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -952,6 +953,7 @@ const char *pssd_status_string(int status)
     case PSSD_ERR_CUDA: return "CUDA error";
     case PSSD_ERR_ALLOC: return "device allocation failed";
     case PSSD_ERR_NOT_PSEUDOSYMMETRIC: return "Sigma*H is not symmetric";
+    case PSSD_ERR_NOALLOC_TOO_LARGE: return "n exceeds the allocation-free scratch limit (PSSD_NOALLOC_MAX_N)";
     default: return status < 0 ? "invalid argument" : "unknown status";
     }
 }
@@ -1211,3 +1213,72 @@ int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *laun
 long long pssd_launch_count(pssd_handle h) { return h ? h->launches : -1; }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of pssd_sign for small problems.
+//
+// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
+// graph is being captured, applications whose device memory is owned by a
+// pool or arena that the library must not bypass, and latency-critical
+// loops where a first-call allocation (and the implicit synchronisation it
+// can cause) is not acceptable.  For them, pssd_sign_noalloc carves every
+// temporary of the sign computation out of one file-scope device array of
+// PSSD_NOALLOC_SCRATCH_BYTES bytes (8 MiB), which every GPU that loads this
+// library holds until the process exits.  The caller still supplies H and S.
+// ===========================================================================
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;
+constexpr int NOALLOC_MAX_N = 128;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// g_noalloc_scratch names a host-side shadow, not device memory, so the
+// address must come from cudaGetSymbolAddress, once per device, with that
+// device current.
+int noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PSSD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return PSSD_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return PSSD_OK;
+}
+
+}  // namespace
+
+extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                                 double *S, int lds, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    if (n > NOALLOC_MAX_N) return PSSD_ERR_NOALLOC_TOO_LARGE;
+    void *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != PSSD_OK) return PSSD_ERR_CUDA;
+    // a private handle whose only workspace chunk is the scratch array: every
+    // temporary of pssd_sign is carved from it, nothing is allocated
+    pssd_handle_s local;
+    local.stream = h->stream;
+    local.chunks.push_back({(char *)scratch, NOALLOC_SCRATCH_BYTES, 0});
+    int st = pssd_sign(&local, n, sigma, H, ldh, S, lds, opts, info);
+    if (local.chunks.size() != 1) {   // cannot happen for n <= NOALLOC_MAX_N (bounded workspace)
+        cudaStreamSynchronize(local.stream);
+        for (size_t i = 1; i < local.chunks.size(); ++i) cudaFree(local.chunks[i].base);
+        local.chunks.resize(1);
+        if (st == PSSD_OK) st = PSSD_ERR_NOALLOC_TOO_LARGE;
+    }
+    local.chunks.clear();   // the scratch array is not owned by the local handle
+    h->launches += local.launches;
+    if (st == PSSD_ERR_CUDA) h->last_err = local.last_err;
+    return st;
+}
