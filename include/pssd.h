@@ -168,6 +168,24 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
              double *V, int ldv, double *D, const pssd_opts *opts, pssd_info *info);
 
 /*
+ * Adjoint (reverse mode) of S = sign(H) and of the eigenvalues of H.
+ * For the scalar loss L = <Sbar, S> + sum_i lambar_i lambda_i (S = sign(H) of
+ * Eq. signDef, lambda_i in the output order of pssd_eig) returns Hbar = dL/dH.
+ * Uses H = V Lambda V^{-1} with V^{-1} = Sigma_hat V^T Sigma (Eq. VSigmaOrth)
+ * and the Daleckii-Krein form of the Frechet derivative of the sign function:
+ *   Hbar = V^{-T} (F o (V^T Sbar V^{-T}) + diag(lambar)) V^T,
+ *   F_ij = (sign lambda_i - sign lambda_j) / (lambda_i - lambda_j).
+ *   Sbar    device n x n (ld ldsb >= n), or NULL (no sign term)
+ *   lambar  device vector of n, or NULL (no eigenvalue term); e.g. 1 for the p
+ *           positive eigenvalues and 0 otherwise gives d(sum of positive eigenvalues)/dH
+ *   Hbar    device n x n output, ld ldhb >= n
+ * opts/info as for pssd_eig (the eigendecomposition is computed internally).
+ */
+int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                  const double *Sbar, int ldsb, const double *lambar, double *Hbar, int ldhb,
+                  const pssd_opts *opts, pssd_info *info);
+
+/*
  * Allocation-free pssd_sign for small problems (the paper has no counterpart;
  * this exists for callers of the library).
  *

@@ -61,7 +61,7 @@ _lib = None
 EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
-           "pssd_sign_noalloc"]
+           "pssd_sign_noalloc", "pssd_sign_vjp"]
 NOALLOC_MAX_N = 128
 
 
@@ -91,6 +91,8 @@ def lib():
                                    ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_eig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_sign_vjp.argtypes = sig + [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(Opts),
+                                      ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pssd_profile_reset.argtypes = [vp]
     L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
@@ -271,3 +273,61 @@ def eig(H, sigma=None, handle=None, **kw):
                         V.stride(0), ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return D, V, info.as_dict()
+
+
+def sign_vjp(H, Sbar=None, lambar=None, sigma=None, handle=None, **kw):
+    """dL/dH for L = <Sbar, sign(H)> + sum_i lambar_i lambda_i (eigenvalues in
+    the output order of eig).  Sbar: n x n float64 CUDA tensor or None;
+    lambar: length-n float64 CUDA tensor or None."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    if Sbar is not None:
+        Sbar = Sbar.contiguous()
+        if Sbar.shape != H.shape or Sbar.dtype != torch.float64 or not Sbar.is_cuda:
+            raise ValueError("Sbar must match H")
+    if lambar is not None:
+        lambar = lambar.contiguous()
+        if lambar.shape != (n,) or lambar.dtype != torch.float64 or not lambar.is_cuda:
+            raise ValueError("lambar must be a length-n float64 CUDA tensor")
+    Hbar = torch.empty_like(H)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_sign_vjp(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh,
+                             ctypes.c_void_p(Sbar.data_ptr() if Sbar is not None else 0), n,
+                             ctypes.c_void_p(lambar.data_ptr() if lambar is not None else 0),
+                             ctypes.c_void_p(Hbar.data_ptr()), Hbar.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return Hbar
+
+
+class SignFn(torch.autograd.Function):
+    """S = sign(H) with the library's adjoint as backward (FP64)."""
+
+    @staticmethod
+    def forward(ctx, H, sigma=None):
+        S, _ = sign(H.detach(), sigma=sigma)
+        ctx.save_for_backward(H)
+        ctx.sigma = sigma
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        (H,) = ctx.saved_tensors
+        return sign_vjp(H.detach(), Sbar=gS.contiguous(), sigma=ctx.sigma), None
+
+
+class EigvalsFn(torch.autograd.Function):
+    """Eigenvalues of H (output order of eig) with the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, H, sigma=None):
+        D, _, _ = eig(H.detach(), sigma=sigma)
+        ctx.save_for_backward(H)
+        ctx.sigma = sigma
+        return D
+
+    @staticmethod
+    def backward(ctx, gD):
+        (H,) = ctx.saved_tensors
+        return sign_vjp(H.detach(), lambar=gD.contiguous(), sigma=ctx.sigma), None

@@ -25,9 +25,10 @@ namespace pssd {
 //           split into a pair of floats (hi = fl32(x), lo = fl32(x - hi)), the
 //           product hi*hi is made error-free with an FMA, the cross terms are
 //           added in FP32, the running sum is a float pair updated by TwoSum
-//           (Knuth) and flushed into an FP64 accumulator every 64 k-steps.
-//           Relative error per k-block ~2^-47; the FP32 pipe issues 64x the
-//           FP64 rate on GB300, so this runs ~4-5x faster than DFMA.
+//           (Knuth) and flushed into an FP64 accumulator every 128 k-steps.
+//           The operands arrive already split (split_pairs, one HBM pass),
+//           so the FP64 pipe -- 1/64 of the FP32 rate on GB300 -- only sees
+//           the flushes.  Relative error per 128-term block ~2^-46.
 // --------------------------------------------------------------------------
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
@@ -49,6 +50,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g)
     const T *A = (const T *)g.A + (long long)z * g.sA;
     const T *B = (const T *)g.B + (long long)z * g.sB;
     const T *ks = (const T *)g.kscale;
+    // GM_DF: float pairs split beforehand
+    const float *Ah = (const float *)g.A + (long long)z * g.sA, *Al = (const float *)g.Alo + (long long)z * g.sA;
+    const float *Bh = (const float *)g.B + (long long)z * g.sB, *Bl = (const float *)g.Blo + (long long)z * g.sB;
     int kbeg = 0, kend = g.k;
     if (g.triA == TRI_LOWER) kend = min(kend, i0 + GBM);   // op(A)[i][p] = 0 for p > i
     if (g.triA == TRI_UPPER) kbeg = max(kbeg, i0);         // op(A)[i][p] = 0 for p < i
@@ -75,19 +79,23 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g)
             int il, pl;
             if (g.ta == 0) { il = e >> 4; pl = e & 15; } else { pl = e >> 6; il = e & 63; }
             int i = i0 + il, p = kt + pl;
-            T v = 0;
             bool ok = (i < g.m) && (p < kend);
             if (g.triA == TRI_LOWER) ok = ok && (p <= i);
             if (g.triA == TRI_UPPER) ok = ok && (p >= i);
-            if (ok) {
-                v = load_op(A, g.lda, g.ta, i, p);
-                if (ks) v *= ks[p];
-            }
             if (MODE == GM_DF) {
-                float hi = __double2float_rn((double)v);
+                float hi = 0.f, lo = 0.f;
+                if (ok) {
+                    hi = load_op(Ah, g.lda, g.ta, i, p); lo = load_op(Al, g.lda, g.ta, i, p);
+                    if (ks) { float f = (float)ks[p]; hi *= f; lo *= f; }
+                }
                 As[pl][il] = hi;
-                Asl[pl][il] = __double2float_rn((double)v - (double)hi);
+                Asl[pl][il] = lo;
             } else {
+                T v = 0;
+                if (ok) {
+                    v = load_op(A, g.lda, g.ta, i, p);
+                    if (ks) v *= ks[p];
+                }
                 As[pl][il] = (S)v;
             }
         }
@@ -97,16 +105,17 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g)
             int jl, pl;
             if (g.tb == 0) { pl = e >> 6; jl = e & 63; } else { jl = e >> 4; pl = e & 15; }
             int j = j0 + jl, p = kt + pl;
-            T v = 0;
             bool ok = (j < g.n) && (p < kend);
             if (g.triB == TRI_LOWER) ok = ok && (p >= j);
             if (g.triB == TRI_UPPER) ok = ok && (p <= j);
-            if (ok) v = load_op(B, g.ldb, g.tb, p, j);
             if (MODE == GM_DF) {
-                float hi = __double2float_rn((double)v);
+                float hi = 0.f, lo = 0.f;
+                if (ok) { hi = load_op(Bh, g.ldb, g.tb, p, j); lo = load_op(Bl, g.ldb, g.tb, p, j); }
                 Bs[pl][jl] = hi;
-                Bsl[pl][jl] = __double2float_rn((double)v - (double)hi);
+                Bsl[pl][jl] = lo;
             } else {
+                T v = 0;
+                if (ok) v = load_op(B, g.ldb, g.tb, p, j);
                 Bs[pl][jl] = (S)v;
             }
         }
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g)
                         al_[qa][qb] = __fadd_rn(al_[qa][qb], __fadd_rn(er, __fadd_rn(pe, cr)));
                     }
             }
-            if (((++kt_count) & 3) == 0) {   // flush the float pairs into FP64 every 64 k
+            if (((++kt_count) & 7) == 0) {   // flush the float pairs into FP64 every 128 k
 #pragma unroll
                 for (int qa = 0; qa < 4; ++qa)
 #pragma unroll
@@ -405,6 +414,29 @@ void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStr
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
     scale_rows_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, r);
+}
+
+// (hi, lo) = (fl32(x), fl32(x - hi)) for a batch of rows x cols blocks (source
+// leading dimension ld, batch stride sb), written compactly (ld = cols)
+__global__ void split_pairs_kernel(const double *x, long long ld, long long sb, int rows, int cols, float *hi,
+                                   float *lo)
+{
+    const int z = blockIdx.z, i = blockIdx.y;
+    const double *xr = x + (long long)z * sb + (long long)i * ld;
+    const long long o = ((long long)z * rows + i) * cols;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
+        double v = xr[j];
+        float h = __double2float_rn(v);
+        hi[o + j] = h;
+        lo[o + j] = __double2float_rn(v - (double)h);
+    }
+}
+
+void split_pairs(const double *x, long long ld, long long sb, int rows, int cols, int batch, float *hi, float *lo,
+                 cudaStream_t s)
+{
+    int gx = (cols + 255) / 256; if (gx > 16) gx = 16;
+    split_pairs_kernel<<<dim3(gx, rows, batch), 256, 0, s>>>(x, ld, sb, rows, cols, hi, lo);
 }
 
 // fixed-order single-block sum (deterministic)

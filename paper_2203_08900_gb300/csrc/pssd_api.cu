@@ -209,8 +209,33 @@ void gemm(pssd_handle h, const GemmArgs &g0)
     GemmArgs g = g0;
     if (g.mode < 0) g.mode = h->dmode;
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
-    Timed t(h, g.mode == GM_F32 ? K_SGEMM : (g.mode == GM_DF ? K_DFGEMM : K_DGEMM), fl);
-    gemm_launch(g, h->stream);
+    Mark mk = mark(h);
+    if (g.mode == GM_DF) {
+        // split each FP64 operand into compact float pairs once (stream-ordered temporaries)
+        const int ra = g.ta ? g.k : g.m, cla = g.ta ? g.m : g.k;
+        const int rb = g.tb ? g.n : g.k, clb = g.tb ? g.k : g.n;
+        const size_t na = (size_t)g.batch * ra * cla, nb = (size_t)g.batch * rb * clb;
+        float *ah = (float *)walloc(h, sizeof(float) * na), *al = (float *)walloc(h, sizeof(float) * na);
+        {
+            Timed t(h, K_HBM, 0);
+            split_pairs((const double *)g.A, g.lda, g.sA, ra, cla, g.batch, ah, al, h->stream);
+        }
+        float *bh = ah, *bl = al;
+        const bool same = g.B == g.A && rb == ra && clb == cla && g.ldb == g.lda && g.sB == g.sA;
+        if (!same) {
+            bh = (float *)walloc(h, sizeof(float) * nb); bl = (float *)walloc(h, sizeof(float) * nb);
+            Timed t(h, K_HBM, 0);
+            split_pairs((const double *)g.B, g.ldb, g.sB, rb, clb, g.batch, bh, bl, h->stream);
+        }
+        g.lda = cla; g.sA = (long long)ra * cla;
+        g.ldb = clb; g.sB = (long long)rb * clb;
+        g.A = ah; g.Alo = al; g.B = bh; g.Blo = bl;
+    }
+    {
+        Timed t(h, g.mode == GM_F32 ? K_SGEMM : (g.mode == GM_DF ? K_DFGEMM : K_DGEMM), fl);
+        gemm_launch(g, h->stream);
+    }
+    release(h, mk);
 }
 
 // ---------------------------------------------------------------------------
@@ -1099,20 +1124,13 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
     });
 }
 
-int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
-             double *D, const pssd_opts *opts, pssd_info *info)
+}  // extern "C"
+
+namespace {
+// full diagonalisation (the body of pssd_eig), inside a guarded call
+int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
+             double *D, const pssd_opts &o, pssd_info *info, int leaf)
 {
-    if (!h) return -1;
-    int v = validate(n, sigma, H, ldh);
-    if (v) return v;
-    if (!V) return -6;
-    if (ldv < n) return -7;
-    if (!D) return -8;
-    pssd_opts o = opts ? *opts : defaults();
-    if (o.precision < 0 || o.precision > 2) return -9;
-    int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
-    info_init(info);
-    return guarded(h, info, [&]() -> int {
         Front F;
         int st = front(h, n, sigma, H, ldh, o, info, F);
         if (st) return st;
@@ -1178,7 +1196,25 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
             info->split_backerr = std::sqrt(e2 / k2);
         }
         return PSSD_OK;
-    });
+}
+}  // namespace
+
+extern "C" {
+
+int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
+             double *D, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!V) return -6;
+    if (ldv < n) return -7;
+    if (!D) return -8;
+    pssd_opts o = opts ? *opts : defaults();
+    if (o.precision < 0 || o.precision > 2) return -9;
+    int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int { return eig_core(h, n, sigma, H, ldh, V, ldv, D, o, info, leaf); });
 }
 
 // --------------------------------------------------------------------------
@@ -1281,4 +1317,75 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
     h->launches += local.launches;
     if (st == PSSD_ERR_CUDA) h->last_err = local.last_err;
     return st;
+}
+
+// ===========================================================================
+// Adjoint (north star (3)): cotangents of S = sign(H) and of the eigenvalues
+// pulled back to H.  With H = V Lambda V^{-1} (V from pssd_eig, V^{-1} =
+// Sigma_hat V^T Sigma by Eq. VSigmaOrth) the Frechet derivative of the sign
+// function is the Daleckii-Krein form
+//     dS = V (F o (V^{-1} dH V)) V^{-1},   F_ij = (s_i - s_j)/(lambda_i - lambda_j),
+// and d lambda_i = (V^{-1} dH V)_ii, so for L = <Sbar, S> + sum_i lambar_i lambda_i
+//     Hbar = V^{-T} (F o (V^T Sbar V^{-T}) + diag(lambar)) V^T,   V^{-T} = Sigma V Sigma_hat.
+// F vanishes between eigenvalues of the same sign and is at most 1/min|lambda|
+// elsewhere, so the pull-back is as well conditioned as the split itself.
+// ===========================================================================
+extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                             const double *Sbar, int ldsb, const double *lambar, double *Hbar, int ldhb,
+                             const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (Sbar && ldsb < n) return -7;
+    if (!Hbar) return -9;
+    if (ldhb < n) return -10;
+    pssd_opts o = opts ? *opts : defaults();
+    if (o.precision < 0 || o.precision > 2) return -11;
+    int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        const long long ld = n, nsz = (long long)n * n;
+        double *V = dalloc(h, nsz), *D = dalloc(h, n);
+        int st = eig_core(h, n, sigma, H, ldh, V, n, D, o, info, leaf);
+        if (st) return st;
+        std::vector<double> hs(n), hD(n), hsh(n);
+        for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+        d2h_sync(h, hD.data(), D, sizeof(double) * n);
+        for (int i = 0; i < n; ++i) hsh[i] = hD[i] > 0 ? 1.0 : -1.0;
+        double *dsig = dalloc(h, n), *dsh = dalloc(h, n);
+        h2d(h, dsig, hs.data(), sizeof(double) * n);
+        h2d(h, dsh, hsh.data(), sizeof(double) * n);
+        double *Vit = dalloc(h, nsz);   // V^{-T} = Sigma V Sigma_hat
+        {
+            Timed t(h, K_HBM, 0, 3);
+            copy_matrix(V, ld, Vit, ld, n, n, h->stream);
+            scale_rows(Vit, ld, n, n, dsig, h->stream);
+            scale_columns(Vit, ld, n, n, dsh, 0, h->stream);
+        }
+        double *W = dalloc(h, nsz), *T = dalloc(h, nsz);
+        if (Sbar) {
+            GemmArgs a; a.m = a.n = a.k = n; a.A = Sbar; a.lda = ldsb; a.B = Vit; a.ldb = ld; a.C = T; a.ldc = ld;
+            gemm(h, a);                                   // T = Sbar V^{-T}
+            GemmArgs b; b.m = b.n = b.k = n; b.A = V; b.lda = ld; b.ta = 1; b.B = T; b.ldb = ld; b.C = W; b.ldc = ld;
+            gemm(h, b);                                   // W = V^T Sbar V^{-T}
+        } else {
+            cuda_check(h, cudaMemsetAsync(W, 0, sizeof(double) * nsz, h->stream), "memset");
+        }
+        double *dlb = nullptr;
+        if (lambar) {   // lambar is a device vector in the output order of pssd_eig
+            dlb = dalloc(h, n);
+            cuda_check(h, cudaMemcpyAsync(dlb, lambar, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream),
+                       "memcpy");
+        }
+        {
+            Timed t(h, K_HBM, 0);
+            dk_combine(W, ld, D, dlb, n, T, ld, h->stream);   // T = F o W + diag(lambar)
+        }
+        GemmArgs c; c.m = c.n = c.k = n; c.A = Vit; c.lda = ld; c.B = T; c.ldb = ld; c.C = W; c.ldc = ld;
+        gemm(h, c);                                       // W = V^{-T} T
+        GemmArgs d; d.m = d.n = d.k = n; d.A = W; d.lda = ld; d.B = V; d.ldb = ld; d.tb = 1; d.C = Hbar; d.ldc = ldhb;
+        gemm(h, d);                                       // Hbar = W V^T
+        return PSSD_OK;
+    });
 }

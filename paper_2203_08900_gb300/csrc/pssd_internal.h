@@ -30,7 +30,13 @@ struct GemmArgs {
     double alpha = 1.0, beta = 0.0;
     int lowerC = 0;
     int mode = -1;   // -1: double data in the caller's FP64 mode (resolved before launch)
+    // GM_DF only: A, B point to the float high parts and Alo, Blo to the float low parts
+    // of the operands, split once by split_pairs(); kscale must be exact in FP32 (e.g. +-1)
+    const void *Alo = nullptr, *Blo = nullptr;
 };
+// x -> (hi, lo) = (fl32(x), fl32(x - hi)) for a batch of rows x cols blocks, written compactly
+void split_pairs(const double *x, long long ld, long long sb, int rows, int cols, int batch, float *hi, float *lo,
+                 cudaStream_t s);
 void gemm_launch(const GemmArgs &g, cudaStream_t s);
 
 // Cholesky of the kb x kb (kb <= PB) diagonal block at (k0,k0) of each batch
