@@ -168,6 +168,22 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
              double *V, int ldv, double *D, const pssd_opts *opts, pssd_info *info);
 
 /*
+ * Batched full diagonalisation of `count` independent definite pseudosymmetric
+ * matrices of (possibly) different orders: for each i, what pssd_eig computes
+ * for (n[i], sigma[i], H[i], ldh[i]) into (V[i], ldv[i], D[i]).
+ * All arrays are HOST arrays of `count` entries; H[i], V[i], D[i] are device
+ * pointers; sigma may be NULL (every instance Casida-signed) or hold per-
+ * instance host signatures (NULL entries allowed); infos NULL or `count` entries.
+ * Instances run concurrently on up to PSSD_BATCH_WORKERS internal streams (one
+ * workspace each, kept by the handle); the handle's stream is ordered before
+ * and after the whole batch.  Returns the first failing instance's status.
+ */
+#define PSSD_BATCH_WORKERS 16
+int pssd_eig_batched(pssd_handle h, int count, const int *n, const signed char *const *sigma,
+                     const double *const *H, const int *ldh, double *const *V, const int *ldv,
+                     double *const *D, const pssd_opts *opts, pssd_info *infos);
+
+/*
  * Adjoint (reverse mode) of S = sign(H) and of the eigenvalues of H.
  * For the scalar loss L = <Sbar, S> + sum_i lambar_i lambda_i (S = sign(H) of
  * Eq. signDef, lambda_i in the output order of pssd_eig) returns Hbar = dL/dH.

@@ -61,7 +61,7 @@ _lib = None
 EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
-           "pssd_sign_noalloc", "pssd_sign_vjp"]
+           "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched"]
 NOALLOC_MAX_N = 128
 
 
@@ -93,6 +93,8 @@ def lib():
     L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_sign_vjp.argtypes = sig + [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(Opts),
                                       ctypes.POINTER(Info)]
+    L.pssd_eig_batched.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts),
+                                   ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pssd_profile_reset.argtypes = [vp]
     L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
@@ -331,3 +333,31 @@ class EigvalsFn(torch.autograd.Function):
     def backward(ctx, gD):
         (H,) = ctx.saved_tensors
         return sign_vjp(H.detach(), lambar=gD.contiguous(), sigma=ctx.sigma), None
+
+
+def eig_batched(Hs, sigmas=None, handle=None, **kw):
+    """Full diagonalisation of a list of square float64 CUDA tensors of any
+    orders in one call.  Returns (list of D, list of V, list of info dicts)."""
+    count = len(Hs)
+    h = _handle(handle)
+    ns = (ctypes.c_int * count)(); lds = (ctypes.c_int * count)(); ldv = (ctypes.c_int * count)()
+    Hp = (ctypes.c_void_p * count)(); Vp = (ctypes.c_void_p * count)(); Dp = (ctypes.c_void_p * count)()
+    Vs, Ds, keep = [], [], []
+    sp = None
+    if sigmas is not None:
+        sp = (ctypes.c_void_p * count)()
+    for i, H in enumerate(Hs):
+        n, ld = _check_H(H)
+        V = torch.empty_like(H); D = torch.empty(n, dtype=H.dtype, device=H.device)
+        ns[i] = n; lds[i] = ld; ldv[i] = V.stride(0)
+        Hp[i] = H.data_ptr(); Vp[i] = V.data_ptr(); Dp[i] = D.data_ptr()
+        Vs.append(V); Ds.append(D)
+        if sigmas is not None:
+            k, ptr = _sigma(n, sigmas[i])
+            keep.append(k)
+            sp[i] = ptr.value if ptr is not None else None
+    infos = (Info * count)()
+    o = _opts(**kw)
+    st = lib().pssd_eig_batched(h._h, count, ns, sp, Hp, lds, Vp, ldv, Dp, ctypes.byref(o), infos)
+    h._check(st)
+    return Ds, Vs, [infos[i].as_dict() for i in range(count)]

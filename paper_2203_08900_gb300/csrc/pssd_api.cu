@@ -24,8 +24,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <string>
 #include <vector>
@@ -56,6 +58,7 @@ struct pssd_handle_s {
     long long prof_count[8] = {0};
     long long launches = 0;
     int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
+    std::vector<pssd_handle_s *> workers;   // pssd_eig_batched: one handle (own stream, workspace) per worker
 };
 
 namespace {
@@ -950,6 +953,13 @@ int pssd_destroy(pssd_handle h)
 {
     if (!h) return -1;
     cudaStreamSynchronize(h->stream);
+    for (auto *w : h->workers) {
+        cudaStreamSynchronize(w->stream);
+        for (auto &c : w->chunks) cudaFree(c.base);
+        for (auto &e : w->free_events) cudaEventDestroy(e);
+        cudaStreamDestroy(w->stream);
+        delete w;
+    }
     for (auto &c : h->chunks) cudaFree(c.base);
     for (auto &e : h->free_events) cudaEventDestroy(e);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -1388,4 +1398,80 @@ extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, con
         gemm(h, d);                                       // Hbar = W V^T
         return PSSD_OK;
     });
+}
+
+
+// ===========================================================================
+// Batching (north star (2)): many independent Hamiltonians of uneven sizes.
+// A host work queue hands instances, largest first, to a pool of workers;
+// each worker owns a handle with its own non-blocking stream and workspace and
+// runs the full pssd_eig pipeline of its instance there, so the kernels of up
+// to PSSD_BATCH_WORKERS instances execute concurrently on the GPU.  The
+// workers' streams wait on the caller's stream at entry and the caller's
+// stream waits on them at exit.
+// ===========================================================================
+extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const signed char *const *sigma,
+                                const double *const *H, const int *ldh, double *const *V, const int *ldv,
+                                double *const *D, const pssd_opts *opts, pssd_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return PSSD_OK;
+    if (!n) return -3;
+    if (!H || !ldh) return -5;
+    if (!V || !ldv) return -7;
+    if (!D) return -9;
+    for (int i = 0; i < count; ++i) {
+        int v = validate(n[i], sigma ? sigma[i] : nullptr, H[i], ldh[i]);
+        if (v) return v;
+        if (!V[i] || ldv[i] < n[i] || !D[i]) return -7;
+    }
+    const int nw = std::min(count, PSSD_BATCH_WORKERS);
+    try {
+        while ((int)h->workers.size() < nw) {
+            auto *w = new pssd_handle_s();
+            cudaError_t e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) { delete w; h->last_err = cudaGetErrorString(e); return PSSD_ERR_CUDA; }
+            h->workers.push_back(w);
+        }
+        cudaEvent_t start;
+        cuda_check(h, cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "cudaEventCreate");
+        cuda_check(h, cudaEventRecord(start, h->stream), "cudaEventRecord");
+        for (int w = 0; w < nw; ++w)
+            cuda_check(h, cudaStreamWaitEvent(h->workers[w]->stream, start, 0), "cudaStreamWaitEvent");
+        std::vector<int> order(count);
+        for (int i = 0; i < count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+        std::atomic<int> next(0);
+        std::vector<int> status(count, PSSD_OK);
+        auto run = [&](int w) {
+            pssd_handle_s *wh = h->workers[w];
+            for (;;) {
+                int q = next.fetch_add(1);
+                if (q >= count) break;
+                int i = order[q];
+                status[i] = pssd_eig(wh, n[i], sigma ? sigma[i] : nullptr, H[i], ldh[i], V[i], ldv[i], D[i], opts,
+                                     infos ? &infos[i] : nullptr);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nw; ++w) pool.emplace_back(run, w);
+        run(0);
+        for (auto &t : pool) t.join();
+        for (int w = 0; w < nw; ++w) {
+            cudaEvent_t done;
+            cuda_check(h, cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "cudaEventCreate");
+            cuda_check(h, cudaEventRecord(done, h->workers[w]->stream), "cudaEventRecord");
+            cuda_check(h, cudaStreamWaitEvent(h->stream, done, 0), "cudaStreamWaitEvent");
+            cudaEventDestroy(done);
+            h->launches += h->workers[w]->launches;
+            h->workers[w]->launches = 0;
+        }
+        cudaEventDestroy(start);
+        for (int i = 0; i < count; ++i)
+            if (status[i] != PSSD_OK) return status[i];
+        return PSSD_OK;
+    } catch (Fail &f) {
+        return f.code;
+    }
 }
