@@ -46,7 +46,7 @@ extern "C" {
 #define PSSD_ERR_NO_CONVERGENCE 2      /* Alg. 8 stopping test still failing after max_restarts restarts */
 #define PSSD_ERR_BASIS 3               /* split: basis rank or orthogonalisation breakdown */
 #define PSSD_ERR_NONFINITE 4           /* NaN/Inf in the input or an iterate */
-#define PSSD_ERR_TIMEOUT 5             /* a bounded device wait gave up */
+#define PSSD_ERR_TIMEOUT 5             /* a bounded device wait gave up (tensor-core pipeline) */
 #define PSSD_ERR_CUDA 6                /* a CUDA call failed; see pssd_last_cuda_error */
 #define PSSD_ERR_ALLOC 7               /* workspace allocation failed */
 #define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
@@ -59,6 +59,8 @@ extern "C" {
 #define PSSD_FP64_EMULATED 2 /* the PSSD_FP64 algorithm with every contraction in FP64 emulated on the FP32
                                 pipe (float pairs, error-free products, TwoSum, FP64 flush every 64 terms) */
 #define PSSD_FLAG_RESIDUALS 1 /* pssd_sign: also compute info->s2_resid = ||S^2 - I||_F */
+#define PSSD_FLAG_NO_TENSOR_CORES 2 /* PSSD_MIXED: FP32 contractions on the FP32 SIMT kernel instead of
+                                       the tcgen05 tensor-core kernel (for comparison) */
 
 typedef struct pssd_handle_s *pssd_handle;
 
@@ -228,6 +230,20 @@ int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *
 #define PSSD_NOALLOC_SCRATCH_BYTES (8u << 20)
 int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
                       double *S, int lds, const pssd_opts *opts, pssd_info *info);
+
+/*
+ * Test hook (not part of the method): one FP32 contraction
+ *   C = alpha op(A) diag(kscale) op(B) + beta Cin   (batched, strides in elements)
+ * through the library's GEMM dispatch, on the tcgen05 tensor-core kernel
+ * (use_tc = 1, 3xTF32) or the FP32 SIMT kernel (use_tc = 0).  ta/tb: 1 = transpose;
+ * triA/triB: 0 none, 1 lower, 2 upper (structure of op(A), op(B)); lowerC: write
+ * only C[i][j] with i >= j.  All pointers are device pointers.
+ */
+int pssd_test_gemm_f32(pssd_handle h, int use_tc, int m, int n, int k, int batch, int ta, int tb, int triA,
+                       int triB, int lowerC, double alpha, double beta, const float *A, long long lda,
+                       long long sA, const float *B, long long ldb, long long sB, const float *Cin,
+                       long long ldcin, long long sCin, float *C, long long ldc, long long sC,
+                       const float *kscale);
 
 #ifdef __cplusplus
 }

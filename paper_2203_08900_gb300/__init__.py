@@ -22,8 +22,9 @@ PSSD_FP64_EMULATED = 2
 FLAG_RESIDUALS = 1
 
 # kinds reported by profile_read
-K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM = range(7)
-KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm"]
+K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM = range(8)
+KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm"]
+FLAG_NO_TENSOR_CORES = 2
 
 
 class Opts(ctypes.Structure):
@@ -61,7 +62,7 @@ _lib = None
 EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
-           "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched"]
+           "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32"]
 NOALLOC_MAX_N = 128
 
 
@@ -93,6 +94,9 @@ def lib():
     L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_sign_vjp.argtypes = sig + [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(Opts),
                                       ctypes.POINTER(Info)]
+    ll = ctypes.c_longlong
+    L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
+                                     vp, ll, ll, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
     L.pssd_eig_batched.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts),
                                    ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -361,3 +365,29 @@ def eig_batched(Hs, sigmas=None, handle=None, **kw):
     st = lib().pssd_eig_batched(h._h, count, ns, sp, Hp, lds, Vp, ldv, Dp, ctypes.byref(o), infos)
     h._check(st)
     return Ds, Vs, [infos[i].as_dict() for i in range(count)]
+
+
+def test_gemm_f32(A, B, use_tc=True, ta=0, tb=0, triA=0, triB=0, lowerC=0, alpha=1.0, beta=0.0, Cin=None,
+                  kscale=None, handle=None):
+    """Test hook: C = alpha op(A) diag(kscale) op(B) + beta Cin with the library's FP32 GEMM
+    (tensor cores or SIMT).  A, B: float32 CUDA tensors, 2-D or 3-D (batch first)."""
+    h = _handle(handle)
+    batched = A.dim() == 3
+    A3 = A if batched else A[None]; B3 = B if batched else B[None]
+    nb = A3.shape[0]
+    m = A3.shape[2] if ta else A3.shape[1]; k = A3.shape[1] if ta else A3.shape[2]
+    n = B3.shape[1] if tb else B3.shape[2]
+    C = torch.empty(nb, m, n, dtype=torch.float32, device=A.device)
+    if Cin is None:
+        Cin3 = C
+    else:
+        Cin3 = Cin if Cin.dim() == 3 else Cin[None]
+    st = lib().pssd_test_gemm_f32(h._h, 1 if use_tc else 0, m, n, k, nb, ta, tb, triA, triB, lowerC,
+                                  float(alpha), float(beta),
+                                  ctypes.c_void_p(A3.data_ptr()), A3.stride(1), A3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(B3.data_ptr()), B3.stride(1), B3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(Cin3.data_ptr()), Cin3.stride(1), Cin3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(C.data_ptr()), C.stride(1), C.stride(0),
+                                  ctypes.c_void_p(kscale.data_ptr() if kscale is not None else 0))
+    h._check(st)
+    return C if batched else C[0]

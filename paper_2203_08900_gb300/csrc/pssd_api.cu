@@ -59,6 +59,8 @@ struct pssd_handle_s {
     long long launches = 0;
     int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
     std::vector<pssd_handle_s *> workers;   // pssd_eig_batched: one handle (own stream, workspace) per worker
+    int *derr = nullptr;    // device error flag of the current call (bounded waits in the tensor-core kernel)
+    int use_tc = 1;         // FP32 contractions on tcgen05 tensor cores (0: FP32 SIMT kernel)
 };
 
 namespace {
@@ -126,7 +128,8 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // ---------------------------------------------------------------------------
 // launch accounting and optional per-launch CUDA-event timing
 // ---------------------------------------------------------------------------
-enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_NKIND = 7 };
+enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
+            K_NKIND = 8 };
 
 cudaEvent_t get_event(pssd_handle h)
 {
@@ -234,7 +237,12 @@ void gemm(pssd_handle h, const GemmArgs &g0)
         g.ldb = clb; g.sB = (long long)rb * clb;
         g.A = ah; g.Alo = al; g.B = bh; g.Blo = bl;
     }
-    {
+    if (g.mode == GM_F32 && h->use_tc && h->derr) {
+        void *ws = walloc(h, tc_gemm_workspace_bytes(g));
+        Timed t(h, K_TCGEMM, fl);
+        int st = tc_gemm_launch(g, ws, h->derr, h->stream);
+        if (st) { h->last_err = "tensor-core GEMM setup failed"; throw Fail{PSSD_ERR_CUDA}; }
+    } else {
         Timed t(h, g.mode == GM_F32 ? K_SGEMM : (g.mode == GM_DF ? K_DFGEMM : K_DGEMM), fl);
         gemm_launch(g, h->stream);
     }
@@ -777,6 +785,7 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
 {
     F.n = n;
     h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : GM_DF;
+    h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
     if (info) info->precision = o.precision;
     const long long ld = n, nsz = (long long)n * n;
     std::vector<double> hs(n);
@@ -910,14 +919,26 @@ int guarded(pssd_handle h, pssd_info *info, F body)
     auto t0 = std::chrono::steady_clock::now();
     Mark mk = mark(h);
     int st;
+    int *outer_err = h->derr;
     try {
+        if (!outer_err) {
+            h->derr = ialloc(h, 1);
+            cuda_check(h, cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream), "memset");
+        }
         st = body();
         if (st == PSSD_OK) cuda_check(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { h->last_err = cudaGetErrorString(e); st = PSSD_ERR_CUDA; }
+        if (!outer_err) {
+            int herr = 0;
+            cudaMemcpyAsync(&herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            cudaStreamSynchronize(h->stream);
+            if (herr && st == PSSD_OK) st = PSSD_ERR_TIMEOUT;
+        }
     } catch (Fail &f) {
         st = f.code;
     }
+    if (!outer_err) h->derr = nullptr;
     cudaStreamSynchronize(h->stream);
     prof_collect(h);
     release(h, mk);
@@ -1474,4 +1495,30 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
     } catch (Fail &f) {
         return f.code;
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// test hook: one FP32 contraction through the library's GEMM dispatch
+// (tensor-core kernel or FP32 SIMT kernel), for parity tests of the kernels
+// ---------------------------------------------------------------------------
+extern "C" int pssd_test_gemm_f32(pssd_handle h, int use_tc, int m, int n, int k, int batch, int ta, int tb,
+                                  int triA, int triB, int lowerC, double alpha, double beta, const float *A,
+                                  long long lda, long long sA, const float *B, long long ldb, long long sB,
+                                  const float *Cin, long long ldcin, long long sCin, float *C, long long ldc,
+                                  long long sC, const float *kscale)
+{
+    if (!h) return -1;
+    if (m < 0 || n < 0 || k < 0 || batch < 1) return -3;
+    return guarded(h, nullptr, [&]() -> int {
+        h->use_tc = use_tc ? 1 : 0;
+        GemmArgs g; g.mode = GM_F32; g.m = m; g.n = n; g.k = k; g.batch = batch;
+        g.A = A; g.lda = lda; g.sA = sA; g.ta = ta; g.triA = triA;
+        g.B = B; g.ldb = ldb; g.sB = sB; g.tb = tb; g.triB = triB;
+        g.Cin = Cin; g.ldcin = ldcin; g.sCin = sCin; g.C = C; g.ldc = ldc; g.sC = sC;
+        g.kscale = kscale; g.alpha = alpha; g.beta = beta; g.lowerC = lowerC;
+        gemm(h, g);
+        h->use_tc = 1;
+        return PSSD_OK;
+    });
 }

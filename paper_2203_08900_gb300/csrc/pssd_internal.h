@@ -38,6 +38,10 @@ struct GemmArgs {
 void split_pairs(const double *x, long long ld, long long sb, int rows, int cols, int batch, float *hi, float *lo,
                  cudaStream_t s);
 void gemm_launch(const GemmArgs &g, cudaStream_t s);
+// FP32 GEMM on tcgen05 tensor cores (3xTF32), same conventions as GM_F32;
+// ws: tc_gemm_workspace_bytes(g) bytes of device memory; err: device flag.
+size_t tc_gemm_workspace_bytes(const GemmArgs &g);
+int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
 
 // Cholesky of the kb x kb (kb <= PB) diagonal block at (k0,k0) of each batch
 // matrix (lower, in place); its triangular inverse goes to Dinv (PB x PB per
