@@ -54,13 +54,16 @@ extern "C" {
 
 /* precision modes */
 #define PSSD_FP64 0          /* every step in native FP64 (DFMA) */
-#define PSSD_MIXED 1         /* Zolotarev steps in FP32; Newton-Schulz refinement, basis and projections in
-                                FP64-accurate arithmetic (FP64 emulated on the FP32 pipe) */
-#define PSSD_FP64_EMULATED 2 /* the PSSD_FP64 algorithm with every contraction in FP64 emulated on the FP32
-                                pipe (float pairs, error-free products, TwoSum, FP64 flush every 64 terms) */
+#define PSSD_MIXED 1         /* Zolotarev steps in FP32 on tensor cores (3xTF32); Newton-Schulz refinement,
+                                basis and projections in FP64-accurate emulated arithmetic */
+#define PSSD_FP64_EMULATED 2 /* the PSSD_FP64 algorithm with every contraction FP64-accurate but emulated:
+                                by default exact integer slices of the operands multiplied on the BF16
+                                tensor cores; with PSSD_FLAG_EMU_SIMT, float pairs on the FP32 pipe */
 #define PSSD_FLAG_RESIDUALS 1 /* pssd_sign: also compute info->s2_resid = ||S^2 - I||_F */
-#define PSSD_FLAG_NO_TENSOR_CORES 2 /* PSSD_MIXED: FP32 contractions on the FP32 SIMT kernel instead of
-                                       the tcgen05 tensor-core kernel (for comparison) */
+#define PSSD_FLAG_NO_TENSOR_CORES 2 /* no tensor-core kernels: FP32 contractions on the FP32 SIMT kernel,
+                                       emulated FP64 contractions with float pairs (for comparison) */
+#define PSSD_FLAG_EMU_SIMT 4        /* emulated FP64 contractions with float pairs on the FP32 pipe instead of
+                                       integer slices on the tensor cores (for comparison) */
 
 typedef struct pssd_handle_s *pssd_handle;
 
@@ -244,6 +247,13 @@ int pssd_test_gemm_f32(pssd_handle h, int use_tc, int m, int n, int k, int batch
                        long long sA, const float *B, long long ldb, long long sB, const float *Cin,
                        long long ldcin, long long sCin, float *C, long long ldc, long long sC,
                        const float *kscale);
+/* Test hook: the same for FP64 data with engine 0 (native DFMA), 1 (float pairs on the FP32
+ * pipe) or 2 (exact integer slices on the BF16 tensor cores). */
+int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch, int ta, int tb, int triA,
+                       int triB, int lowerC, double alpha, double beta, const double *A, long long lda,
+                       long long sA, const double *B, long long ldb, long long sB, const double *Cin,
+                       long long ldcin, long long sCin, double *C, long long ldc, long long sC,
+                       const double *kscale);
 
 #ifdef __cplusplus
 }

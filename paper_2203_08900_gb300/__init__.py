@@ -22,9 +22,10 @@ PSSD_FP64_EMULATED = 2
 FLAG_RESIDUALS = 1
 
 # kinds reported by profile_read
-K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM = range(8)
-KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm"]
+K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM, K_OZGEMM = range(9)
+KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm", "ozgemm"]
 FLAG_NO_TENSOR_CORES = 2
+FLAG_EMU_SIMT = 4
 
 
 class Opts(ctypes.Structure):
@@ -62,7 +63,8 @@ _lib = None
 EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "pssd_last_cuda_error",
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
-           "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32"]
+           "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
+           "pssd_test_gemm_f64"]
 NOALLOC_MAX_N = 128
 
 
@@ -97,6 +99,7 @@ def lib():
     ll = ctypes.c_longlong
     L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
                                      vp, ll, ll, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
+    L.pssd_test_gemm_f64.argtypes = L.pssd_test_gemm_f32.argtypes
     L.pssd_eig_batched.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts),
                                    ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -383,6 +386,28 @@ def test_gemm_f32(A, B, use_tc=True, ta=0, tb=0, triA=0, triB=0, lowerC=0, alpha
     else:
         Cin3 = Cin if Cin.dim() == 3 else Cin[None]
     st = lib().pssd_test_gemm_f32(h._h, 1 if use_tc else 0, m, n, k, nb, ta, tb, triA, triB, lowerC,
+                                  float(alpha), float(beta),
+                                  ctypes.c_void_p(A3.data_ptr()), A3.stride(1), A3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(B3.data_ptr()), B3.stride(1), B3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(Cin3.data_ptr()), Cin3.stride(1), Cin3.stride(0) if nb > 1 else 0,
+                                  ctypes.c_void_p(C.data_ptr()), C.stride(1), C.stride(0),
+                                  ctypes.c_void_p(kscale.data_ptr() if kscale is not None else 0))
+    h._check(st)
+    return C if batched else C[0]
+
+
+def test_gemm_f64(A, B, engine=2, ta=0, tb=0, triA=0, triB=0, lowerC=0, alpha=1.0, beta=0.0, Cin=None,
+                  kscale=None, handle=None):
+    """Test hook: the FP64 contraction with engine 0 (DFMA), 1 (float pairs) or 2 (tensor-core slices)."""
+    h = _handle(handle)
+    batched = A.dim() == 3
+    A3 = A if batched else A[None]; B3 = B if batched else B[None]
+    nb = A3.shape[0]
+    m = A3.shape[2] if ta else A3.shape[1]; k = A3.shape[1] if ta else A3.shape[2]
+    n = B3.shape[1] if tb else B3.shape[2]
+    C = torch.empty(nb, m, n, dtype=torch.float64, device=A.device)
+    Cin3 = C if Cin is None else (Cin if Cin.dim() == 3 else Cin[None])
+    st = lib().pssd_test_gemm_f64(h._h, int(engine), m, n, k, nb, ta, tb, triA, triB, lowerC,
                                   float(alpha), float(beta),
                                   ctypes.c_void_p(A3.data_ptr()), A3.stride(1), A3.stride(0) if nb > 1 else 0,
                                   ctypes.c_void_p(B3.data_ptr()), B3.stride(1), B3.stride(0) if nb > 1 else 0,

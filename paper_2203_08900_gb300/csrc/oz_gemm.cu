@@ -1,0 +1,477 @@
+// FP64-accurate GEMM on the BF16 tensor cores of sm_103a (tcgen05), by exact
+// integer slicing (the error-free splitting scheme of Ozaki, Ogita, Oishi and
+// Rump, 2012).
+//
+//   C = alpha * op(A) * diag(kscale) * op(B) + beta * Cin        (FP64 data)
+//
+// 1. Every row i of op(A) is scaled by 2^{-e_i} and every column j of op(B)
+//    by 2^{-f_j} (exact) so that all entries lie in (-1, 1).
+// 2. Each scaled entry x is cut into S = 7 integer slices of 7 bits:
+//      d_t = rint(r_{t-1} 2^{7t}),  r_t = r_{t-1} - d_t 2^{-7t},  r_0 = x,
+//    |d_1| <= 128, |d_t| <= 64 (t > 1), |x - sum_t d_t 2^{-7t}| <= 2^-50;
+//    the d_t are exact in BF16.
+// 3. For every level L = a + b (2 <= L <= S+1) the slice products
+//    sum_{a+b=L} D^A_a D^B_b are integers below 2^24 over any 256-term
+//    stretch of k, so the tensor cores' FP32 accumulation of them is exact;
+//    each level has its own accumulator in tensor memory.
+// 4. Every 256 terms of k the seven level sums are scaled by 2^{-7L} (exact)
+//    and added into a float-pair (TwoSum) accumulator per output; at the end
+//    C = alpha 2^{e_i + f_j} (hi + lo) + beta Cin in FP64.
+// Products with a + b > S + 1 are dropped: they are below 2^-56 relative.
+//
+// Kernel layout: one CTA of 128 threads per 128 x 64 output tile; 2-stage
+// ring of 7 A-slice tiles (128 x 32 BF16, 64-byte swizzle) and 7 B-slice
+// tiles (64 x 32) fed by TMA; thread 0 issues tcgen05.mma kind::f16 (M=128,
+// N=64, K=16) into 7 accumulators of 64 TMEM columns; all four warps flush.
+// Every mbarrier wait is bounded (error flag, TMEM freed, return).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <mutex>
+
+#include "pssd_internal.h"
+
+namespace pssd {
+
+namespace {
+
+constexpr int OZ_S = 7;                    // slices
+constexpr int OZ_LEVELS = OZ_S;            // levels L = 2 .. S+1
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;   // BK in BF16 elements = 64 bytes
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_CHUNK_STAGES = 8;         // flush every 8 x 32 = 256 terms of k
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 8 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 4 KB
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 84 KB
+constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;
+constexpr int OZ_TMEM_COLS = 512;
+
+struct OzArgs {
+    CUtensorMap ta, tb;                    // slices stacked: row = (slice * batch + z) * pad + i
+    int m, n, k, batch, m_pad, n_pad;
+    int triA, triB, lowerC;
+    const int *ea, *eb;                    // exponents per row of op(A) (batch*m_pad), per column of op(B)
+    double *C; long long ldc, sC;
+    const double *Cin; long long ldcin, sCin;
+    double alpha, beta;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (unsigned long long it = 0; it < OZ_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// K-major operand, 64-byte swizzle: rows of 64 bytes, 8-row groups 512 bytes apart
+__device__ __forceinline__ unsigned long long smem_desc_sw64(uint32_t addr)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFF);
+    d |= (unsigned long long)(16 >> 4) << 16;
+    d |= (unsigned long long)(512 >> 4) << 32;
+    d |= 1ull << 46;
+    d |= 4ull << 61;                       // 64-byte swizzle
+    return d;
+}
+
+// kind::f16, D = F32, A = B = BF16, both K-major, N = 64, M = 128
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// float-pair accumulation (TwoSum, then renormalisation)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
+{
+    float s = __fadd_rn(hi, x);
+    float bp = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    float l = __fadd_rn(lo, e);
+    float s2 = __fadd_rn(s, l);              // Fast2Sum renormalisation (|s| >= |l|)
+    lo = __fsub_rn(l, __fsub_rn(s2, s));
+    hi = s2;
+}
+
+__global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__ OzArgs g)
+{
+    const int i0 = blockIdx.y * OZ_BM, j0 = blockIdx.x * OZ_BN, z = blockIdx.z;
+    if (i0 >= g.m || j0 >= g.n) return;
+    if (g.lowerC && j0 > i0 + OZ_BM - 1) return;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned long long *bars = (unsigned long long *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
+    // bars[0..S): full, [S..2S): empty, [2S]: flush
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * OZ_STAGES + 2);
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int kbeg = 0, kend = g.k;
+    if (g.triA == TRI_LOWER) kend = min(kend, i0 + OZ_BM);
+    if (g.triA == TRI_UPPER) kbeg = max(kbeg, i0);
+    if (g.triB == TRI_LOWER) kbeg = max(kbeg, j0);
+    if (g.triB == TRI_UPPER) kend = min(kend, j0 + OZ_BN);
+    const int kb0 = kbeg / OZ_BK;
+    const int nkb = (kend > kbeg) ? (kend + OZ_BK - 1) / OZ_BK - kb0 : 0;
+    const int nchunks = (nkb + OZ_CHUNK_STAGES - 1) / OZ_CHUNK_STAGES;
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
+        }
+        mbar_init(smem_u32(&bars[2 * OZ_STAGES]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(OZ_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    float hi[OZ_BN], lo[OZ_BN];
+#pragma unroll
+    for (int q = 0; q < OZ_BN; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+
+    // producer state (thread 0)
+    int issued = 0;
+    const int ya = z * g.m_pad + i0, yb = z * g.n_pad + j0;
+    auto issue = [&](int q) {
+        const int s = q % OZ_STAGES;
+        const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
+        const uint32_t full = smem_u32(&bars[s]);
+        const int x = (kb0 + q) * OZ_BK;
+        mbar_expect_tx(full, OZ_STAGE_BYTES);
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t) {
+            tma_load_2d(st + t * OZ_A_TILE, &g.ta, x, (t * g.batch) * g.m_pad + ya, full);
+            tma_load_2d(st + OZ_S * OZ_A_TILE + t * OZ_B_TILE, &g.tb, x, (t * g.batch) * g.n_pad + yb, full);
+        }
+    };
+    if (tid == 0)
+        for (; issued < nkb && issued < OZ_STAGES; ++issued) issue(issued);
+
+    for (int c = 0; c < nchunks; ++c) {
+        if (tid == 0 && !s_abort) {
+            const int q0 = c * OZ_CHUNK_STAGES, q1 = min(nkb, q0 + OZ_CHUNK_STAGES);
+            bool ok = true;
+            for (int q = q0; q < q1 && ok; ++q) {
+                const int s = q % OZ_STAGES;
+                if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((q / OZ_STAGES) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < OZ_BK / 16; ++kk) {     // K = 16 BF16 = 32 bytes per instruction
+                    const uint32_t off = kk * 32;
+#pragma unroll
+                    for (int a = 1; a <= OZ_S; ++a) {
+                        const unsigned long long ad = smem_desc_sw64(st + (a - 1) * OZ_A_TILE + off);
+#pragma unroll
+                        for (int b = 1; a + b <= OZ_S + 1; ++b) {
+                            const int L = a + b - 2;                         // 0 .. S-1
+                            const unsigned long long bd =
+                                smem_desc_sw64(st + OZ_S * OZ_A_TILE + (b - 1) * OZ_B_TILE + off);
+                            // the a = 1 pass reaches every level first: it overwrites at the chunk start
+                            const uint32_t acc = (q == q0 && kk == 0 && a == 1) ? 0u : 1u;
+                            mma_bf16(tmem + (uint32_t)(L * OZ_BN), ad, bd, acc);
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&bars[OZ_STAGES + s]));
+                if (q >= 1 && issued < nkb) {
+                    const int sp = (q - 1) % OZ_STAGES;
+                    if (!mbar_wait(smem_u32(&bars[OZ_STAGES + sp]), (uint32_t)(((q - 1) / OZ_STAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    issue(issued++);
+                }
+            }
+            if (ok) {
+                mma_commit(smem_u32(&bars[2 * OZ_STAGES]));           // flush point
+            } else {
+                s_abort = 1;
+                atomicExch(g.err, 1);
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (!mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), (uint32_t)(c & 1))) {
+            atomicExch(g.err, 2);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // flush: level L accumulator holds an exact integer sum; scale by 2^{-7(L+2)}
+#pragma unroll
+        for (int L = 0; L < OZ_LEVELS; ++L) {
+            const float sc = __int_as_float((127 - 7 * (L + 2)) << 23);   // 2^{-7(L+2)}
+#pragma unroll
+            for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * OZ_BN + c0), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) df_add(hi[c0 + q], lo[c0 + q], __fmul_rn(v[q], sc));
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // accumulators free for the next chunk
+    }
+    if (s_abort && tid == 0) {
+        for (int q = 0; q < issued; ++q) mbar_wait(smem_u32(&bars[q % OZ_STAGES]), (uint32_t)((q / OZ_STAGES) & 1));
+    }
+
+    // epilogue
+    const int i = i0 + warp * 32 + lane;
+    if (i < g.m && !s_abort) {
+        double *C = g.C + (long long)z * g.sC;
+        const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
+        const int ei = g.ea[z * g.m_pad + i];
+#pragma unroll
+        for (int q = 0; q < OZ_BN; ++q) {
+            const int j = j0 + q;
+            if (j >= g.n || (g.lowerC && j > i)) continue;
+            double v = ((double)hi[q] + (double)lo[q]);
+            v = ldexp(v, ei + g.eb[z * g.n_pad + j]);
+            double o = g.alpha * v;
+            if (g.beta != 0.0) o += g.beta * Cin[(long long)i * g.ldcin + j];
+            C[(long long)i * g.ldc + j] = o;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation
+//   logical operand X(r, p), r < rows, p < k:  trans ? src[p][r] : src[r][p],
+//   structural zeros (tri, in (r, p) terms) forced to 0, optional ks[p] scaling
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double oz_load(const double *X, long long ld, int trans, int rows, int k, int tri,
+                                          const double *ks, int r, int p)
+{
+    if (r >= rows || p >= k) return 0.0;
+    if (tri == TRI_LOWER && p > r) return 0.0;
+    if (tri == TRI_UPPER && p < r) return 0.0;
+    double v = trans ? X[(long long)p * ld + r] : X[(long long)r * ld + p];
+    if (ks) v *= ks[p];
+    return v;
+}
+
+// exponent e(r) with max_p |X(r,p)| < 2^e, by 32 x 32 tiles and atomicMax
+__global__ void __launch_bounds__(256) oz_exp_kernel(const double *X, long long ld, long long sb, int trans, int rows,
+                                                     int k, int tri, const double *ks, int rows_pad, int *e)
+{
+    __shared__ double T[32][33];
+    const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    X += (long long)z * sb;
+    for (int yy = ty; yy < 32; yy += 8) {
+        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = fabs(oz_load(X, ld, 1, rows, k, tri, ks, r, p)); }
+        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = fabs(oz_load(X, ld, 0, rows, k, tri, ks, r, p)); }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        double mx = 0.0;
+        for (int q = 0; q < 32; ++q) mx = fmax(mx, T[threadIdx.x][q]);
+        if (r < rows && mx > 0.0) {
+            int ex;
+            frexp(mx, &ex);                  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
+            atomicMax(&e[z * rows_pad + r], ex);
+        }
+    }
+}
+
+// seven BF16 slices, K-major: out[((t * batch + z) * rows_pad + r) * k_pad + p]
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long long ld, long long sb, int trans,
+                                                       int rows, int k, int tri, const double *ks, int rows_pad,
+                                                       int k_pad, int batch, const int *e, __nv_bfloat16 *out)
+{
+    __shared__ double T[32][33];
+    const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    X += (long long)z * sb;
+    for (int yy = ty; yy < 32; yy += 8) {
+        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = oz_load(X, ld, 1, rows, k, tri, ks, r, p); }
+        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = oz_load(X, ld, 0, rows, k, tri, ks, r, p); }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int r = r0 + yy, p = p0 + tx;
+        if (r >= rows_pad || p >= k_pad) continue;
+        double rem = 0.0;
+        if (r < rows) {
+            int ex = e[z * rows_pad + r];
+            if (ex > -2000) rem = ldexp(T[yy][tx], -ex);   // |rem| < 1
+        }
+        for (int t = 1; t <= OZ_S; ++t) {
+            double scaled = ldexp(rem, 7 * t);
+            double d = rint(scaled);
+            rem -= ldexp(d, -7 * t);
+            out[(((long long)(t - 1) * batch + z) * rows_pad + r) * k_pad + p] = __float2bfloat16_rn((float)d);
+        }
+    }
+}
+
+__global__ void fill_int_kernel(int *x, long long n, int v)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
+std::once_flag g_enc_once;
+
+bool get_enc()
+{
+    std::call_once(g_enc_once, []() {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_enc != nullptr;
+}
+
+bool make_map_bf16(CUtensorMap *m, const void *base, long long rows_total, int k_pad, int box_rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows_total};
+    cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
+    cuuint32_t box[2] = {OZ_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t oz_gemm_workspace_bytes(const GemmArgs &g)
+{
+    const long long kp = (g.k + 7) / 8 * 8;
+    const long long mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+    return (size_t)(OZ_S * (mp + np) * kp * g.batch) * 2 + (size_t)(mp + np) * g.batch * sizeof(int) + 2048;
+}
+
+int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+{
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
+    if (!get_enc()) return -1;
+    static bool attr_done = false;
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES) !=
+            cudaSuccess)
+            return -2;
+        attr_done = true;
+    }
+    const int kp = (g.k + 7) / 8 * 8;
+    const int mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+    unsigned char *base = (unsigned char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    __nv_bfloat16 *sa = (__nv_bfloat16 *)base;
+    __nv_bfloat16 *sb = sa + (size_t)OZ_S * mp * kp * g.batch;
+    int *ea = (int *)(sb + (size_t)OZ_S * np * kp * g.batch);
+    int *eb = ea + (size_t)mp * g.batch;
+    const int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
+    fill_int_kernel<<<64, 256, 0, s>>>(ea, (long long)(mp + np) * g.batch, INT_MIN / 2);
+    {
+        dim3 gr((kp + 31) / 32, (mp + 31) / 32, g.batch);
+        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
+                                         (const double *)g.kscale, mp, ea);
+        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
+                                           (const double *)g.kscale, mp, kp, g.batch, ea, sa);
+    }
+    {
+        dim3 gr((kp + 31) / 32, (np + 31) / 32, g.batch);
+        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
+                                         np, eb);
+        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
+                                           np, kp, g.batch, eb, sb);
+    }
+    OzArgs a;
+    if (!make_map_bf16(&a.ta, sa, (long long)OZ_S * mp * g.batch, kp, OZ_BM) ||
+        !make_map_bf16(&a.tb, sb, (long long)OZ_S * np * g.batch, kp, OZ_BN))
+        return -3;
+    a.m = g.m; a.n = g.n; a.k = g.k; a.batch = g.batch; a.m_pad = mp; a.n_pad = np;
+    a.triA = g.triA; a.triB = g.triB; a.lowerC = g.lowerC;
+    a.ea = ea; a.eb = eb;
+    a.C = (double *)g.C; a.ldc = g.ldc; a.sC = g.sC;
+    a.Cin = (const double *)g.Cin; a.ldcin = g.ldcin; a.sCin = g.sCin;
+    a.alpha = g.alpha; a.beta = g.beta; a.err = err;
+    dim3 grid((g.n + OZ_BN - 1) / OZ_BN, (g.m + OZ_BM - 1) / OZ_BM, g.batch);
+    oz_gemm_kernel<<<grid, 128, OZ_SMEM_BYTES, s>>>(a);
+    return 0;
+}
+
+}  // namespace pssd

@@ -129,7 +129,7 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // launch accounting and optional per-launch CUDA-event timing
 // ---------------------------------------------------------------------------
 enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
-            K_NKIND = 8 };
+            K_OZGEMM = 8, K_NKIND = 9 };
 
 cudaEvent_t get_event(pssd_handle h)
 {
@@ -216,6 +216,7 @@ void gemm(pssd_handle h, const GemmArgs &g0)
     if (g.mode < 0) g.mode = h->dmode;
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
     Mark mk = mark(h);
+    if (g.mode == GM_OZ && !h->derr) g.mode = GM_DF;   // (no error flag outside a guarded call)
     if (g.mode == GM_DF) {
         // split each FP64 operand into compact float pairs once (stream-ordered temporaries)
         const int ra = g.ta ? g.k : g.m, cla = g.ta ? g.m : g.k;
@@ -237,7 +238,12 @@ void gemm(pssd_handle h, const GemmArgs &g0)
         g.ldb = clb; g.sB = (long long)rb * clb;
         g.A = ah; g.Alo = al; g.B = bh; g.Blo = bl;
     }
-    if (g.mode == GM_F32 && h->use_tc && h->derr) {
+    if (g.mode == GM_OZ) {
+        void *ws = walloc(h, oz_gemm_workspace_bytes(g));
+        Timed t(h, K_OZGEMM, fl);
+        int st = oz_gemm_launch(g, ws, h->derr, h->stream);
+        if (st) { h->last_err = "tensor-core FP64 GEMM setup failed"; throw Fail{PSSD_ERR_CUDA}; }
+    } else if (g.mode == GM_F32 && h->use_tc && h->derr) {
         void *ws = walloc(h, tc_gemm_workspace_bytes(g));
         Timed t(h, K_TCGEMM, fl);
         int st = tc_gemm_launch(g, ws, h->derr, h->stream);
@@ -784,8 +790,8 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
           pssd_info *info, Front &F)
 {
     F.n = n;
-    h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : GM_DF;
     h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+    h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
     if (info) info->precision = o.precision;
     const long long ld = n, nsz = (long long)n * n;
     std::vector<double> hs(n);
@@ -1519,6 +1525,30 @@ extern "C" int pssd_test_gemm_f32(pssd_handle h, int use_tc, int m, int n, int k
         g.kscale = kscale; g.alpha = alpha; g.beta = beta; g.lowerC = lowerC;
         gemm(h, g);
         h->use_tc = 1;
+        return PSSD_OK;
+    });
+}
+
+
+// test hook: one FP64 contraction with a chosen engine (0 DFMA, 1 float pairs on
+// the FP32 pipe, 2 integer slices on the BF16 tensor cores)
+extern "C" int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch, int ta, int tb,
+                                  int triA, int triB, int lowerC, double alpha, double beta, const double *A,
+                                  long long lda, long long sA, const double *B, long long ldb, long long sB,
+                                  const double *Cin, long long ldcin, long long sCin, double *C, long long ldc,
+                                  long long sC, const double *kscale)
+{
+    if (!h) return -1;
+    if (engine < 0 || engine > 2) return -2;
+    if (m < 0 || n < 0 || k < 0 || batch < 1) return -3;
+    return guarded(h, nullptr, [&]() -> int {
+        GemmArgs g; g.mode = engine == 0 ? GM_F64 : (engine == 1 ? GM_DF : GM_OZ);
+        g.m = m; g.n = n; g.k = k; g.batch = batch;
+        g.A = A; g.lda = lda; g.sA = sA; g.ta = ta; g.triA = triA;
+        g.B = B; g.ldb = ldb; g.sB = sB; g.tb = tb; g.triB = triB;
+        g.Cin = Cin; g.ldcin = ldcin; g.sCin = sCin; g.C = C; g.ldc = ldc; g.sC = sC;
+        g.kscale = kscale; g.alpha = alpha; g.beta = beta; g.lowerC = lowerC;
+        gemm(h, g);
         return PSSD_OK;
     });
 }

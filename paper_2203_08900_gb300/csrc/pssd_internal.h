@@ -7,7 +7,7 @@
 namespace pssd {
 
 enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
-enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2 };
+enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2, GM_OZ = 3 };
 
 // order of the diagonal blocks of the blocked Cholesky / triangular inverse
 constexpr int PB = 32;
@@ -42,6 +42,10 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s);
 // ws: tc_gemm_workspace_bytes(g) bytes of device memory; err: device flag.
 size_t tc_gemm_workspace_bytes(const GemmArgs &g);
 int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
+// FP64-accurate GEMM on tcgen05 BF16 tensor cores by exact integer slicing
+// (double data, conventions of GM_F64); ws: oz_gemm_workspace_bytes(g) bytes.
+size_t oz_gemm_workspace_bytes(const GemmArgs &g);
+int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
 
 // Cholesky of the kb x kb (kb <= PB) diagonal block at (k0,k0) of each batch
 // matrix (lower, in place); its triangular inverse goes to Dinv (PB x PB per
