@@ -265,7 +265,7 @@ def main():
         t = float(tt.item())
     kinds = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
     # dominant kernel of this precision mode
-    dom = max(["dgemm", "sgemm", "dfgemm"], key=lambda kk: kinds[kk]["ms"])
+    dom = max(["dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm"], key=lambda kk: kinds[kk]["ms"])
     gemm = kinds[dom]
     last = infos[-1]
     rs = [x for x in last["r_used"][:last["passes"]]]
@@ -296,7 +296,19 @@ def main():
     achieved = (gemm["flops"] / gemm["launches"]) / (gemm["ms"] / gemm["launches"] / 1e3) / 1e12 if gemm["launches"] else None
     # the FP64-emulating kernel spends 13 FP32 instructions per multiply-add (see the design notes):
     # its ALU roof is the FP32 issue rate / 6.5 in FP64-equivalent FLOP/s
-    peak_dom = {"dgemm": peak_fp64, "sgemm": peak_fp32, "dfgemm": peak_fp32 / 13.0}[dom]
+    bf16_meas = 1901.5    # measured cuBLAS BF16 dense TFLOP/s on this machine's GB300 (burst)
+    try:
+        bf16_meas = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    # tensor-core kernels are reported in the tensor pipe's own operations:
+    #   tcgemm: 3 TF32 products per FP32 product; TF32 peak = BF16 peak x (1.1 / 2.25) nominal ratio
+    #   ozgemm: 28 BF16 slice products per FP64 product; peak = measured BF16
+    tensor_factor = {"tcgemm": 3.0, "ozgemm": 28.0}.get(dom, 1.0)
+    if achieved is not None:
+        achieved *= tensor_factor
+    peak_dom = {"dgemm": peak_fp64, "sgemm": peak_fp32, "dfgemm": peak_fp32 / 13.0,
+                "tcgemm": bf16_meas * 1.1 / 2.25, "ozgemm": bf16_meas}[dom]
     line = {
         "metric": METRIC, "value": s_per_solve, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": False,
@@ -312,12 +324,17 @@ def main():
                      "split_backerr_K": last["split_backerr"]},
         "roofline": {"kernel": {"dgemm": "gemm_kernel<GM_F64> (FP64 DFMA, 64x64x16 tiles)",
                                 "sgemm": "gemm_kernel<GM_F32> (FP32 FFMA)",
-                                "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated on the FP32 pipe)"}[dom],
-                     "bound": "alu", "achieved": achieved, "peak": peak_dom, "unit": "TFLOP/s",
+                                "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated on the FP32 pipe)",
+                                "tcgemm": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
+                                "ozgemm": "oz_gemm_kernel (tcgen05 kind::f16 BF16, 28 integer-slice products)"}[dom],
+                     "bound": "tensor" if dom in ("tcgemm", "ozgemm") else "alu",
+                     "achieved": achieved, "peak": peak_dom, "unit": "TFLOP/s",
                      "frac": (achieved / peak_dom) if achieved else None, "traffic": None,
                      "peak_note": {"dgemm": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (cuBLAS DGEMM measured 1.09)",
                                    "sgemm": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz",
-                                   "dfgemm": "derived: FP32 issue rate (152 SM x 128/clk x 2.07 GHz) / 13 instructions per multiply-add x 2 flop"}[dom],
+                                   "dfgemm": "derived: FP32 issue rate (152 SM x 128/clk x 2.07 GHz) / 13 instructions per multiply-add x 2 flop",
+                                   "tcgemm": "of measured: BF16 burst x 1.1/2.25 (TF32 nominal ratio); achieved counts the 3 TF32 products",
+                                   "ozgemm": "of measured: BF16 burst; achieved counts the 28 BF16 slice products (FP64-equivalent = achieved/28)"}[dom],
                      "share_of_step": gemm["ms"] / 1e3 / t if t > 0 else None},
         "kernels": kinds,
         "gpu_launches": launches,
