@@ -6,23 +6,24 @@
 //
 // 1. Every row i of op(A) is scaled by 2^{-e_i} and every column j of op(B)
 //    by 2^{-f_j} (exact) so that all entries lie in (-1, 1).
-// 2. Each scaled entry x is cut into S = 7 integer slices of 7 bits:
+// 2. Each scaled entry x is cut into S = 8 integer slices of 7 bits:
 //      d_t = rint(r_{t-1} 2^{7t}),  r_t = r_{t-1} - d_t 2^{-7t},  r_0 = x,
-//    |d_1| <= 128, |d_t| <= 64 (t > 1), |x - sum_t d_t 2^{-7t}| <= 2^-50;
+//    |d_1| <= 128, |d_t| <= 64 (t > 1), |x - sum_t d_t 2^{-7t}| <= 2^-57;
 //    the d_t are exact in BF16.
 // 3. For every level L = a + b (2 <= L <= S+1) the slice products
 //    sum_{a+b=L} D^A_a D^B_b are integers below 2^24 over any 256-term
-//    stretch of k, so the tensor cores' FP32 accumulation of them is exact;
-//    each level has its own accumulator in tensor memory.
+//    stretch of k (at most 2 x 2^13 + 6 x 2^12 per term), so the tensor
+//    cores' FP32 accumulation of them is exact; each level has its own
+//    accumulator in tensor memory (8 levels x 64 columns = all 512).
 // 4. Every 256 terms of k the seven level sums are scaled by 2^{-7L} (exact)
 //    and added into a float-pair (TwoSum) accumulator per output; at the end
 //    C = alpha 2^{e_i + f_j} (hi + lo) + beta Cin in FP64.
-// Products with a + b > S + 1 are dropped: they are below 2^-56 relative.
+// Products with a + b > S + 1 (36 of 64 kept) are dropped: below 2^-63 relative.
 //
 // Kernel layout: one CTA of 128 threads per 128 x 64 output tile; 2-stage
-// ring of 7 A-slice tiles (128 x 32 BF16, 64-byte swizzle) and 7 B-slice
+// ring of 8 A-slice tiles (128 x 32 BF16, 64-byte swizzle) and 8 B-slice
 // tiles (64 x 32) fed by TMA; thread 0 issues tcgen05.mma kind::f16 (M=128,
-// N=64, K=16) into 7 accumulators of 64 TMEM columns; all four warps flush.
+// N=64, K=16) into 8 accumulators of 64 TMEM columns; all four warps flush.
 // Every mbarrier wait is bounded (error flag, TMEM freed, return).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -38,14 +39,14 @@ namespace pssd {
 
 namespace {
 
-constexpr int OZ_S = 7;                    // slices
+constexpr int OZ_S = 8;                    // slices
 constexpr int OZ_LEVELS = OZ_S;            // levels L = 2 .. S+1
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;   // BK in BF16 elements = 64 bytes
 constexpr int OZ_STAGES = 2;
 constexpr int OZ_CHUNK_STAGES = 8;         // flush every 8 x 32 = 256 terms of k
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 8 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 4 KB
-constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 84 KB
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 96 KB
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;
 constexpr int OZ_TMEM_COLS = 512;

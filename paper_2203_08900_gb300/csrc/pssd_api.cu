@@ -54,13 +54,14 @@ struct pssd_handle_s {
     int prof = 0;
     std::vector<ProfEvent> events;
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[8] = {0}, prof_flops[8] = {0};
-    long long prof_count[8] = {0};
+    double prof_ms[16] = {0}, prof_flops[16] = {0};
+    long long prof_count[16] = {0};
     long long launches = 0;
     int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
     std::vector<pssd_handle_s *> workers;   // pssd_eig_batched: one handle (own stream, workspace) per worker
     int *derr = nullptr;    // device error flag of the current call (bounded waits in the tensor-core kernel)
     int use_tc = 1;         // FP32 contractions on tcgen05 tensor cores (0: FP32 SIMT kernel)
+    int force_engine = 0;   // test hooks: no size-based engine selection
 };
 
 namespace {
@@ -217,6 +218,9 @@ void gemm(pssd_handle h, const GemmArgs &g0)
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
     Mark mk = mark(h);
     if (g.mode == GM_OZ && !h->derr) g.mode = GM_DF;   // (no error flag outside a guarded call)
+    // thin or small products: the slicing passes would dominate; use float pairs
+    if (g.mode == GM_OZ && !h->force_engine && (g.k < 128 || (double)g.m * g.n * g.k * g.batch < 33554432.0))
+        g.mode = GM_DF;
     if (g.mode == GM_DF) {
         // split each FP64 operand into compact float pairs once (stream-ordered temporaries)
         const int ra = g.ta ? g.k : g.m, cla = g.ta ? g.m : g.k;
@@ -1268,7 +1272,7 @@ int pssd_profile_enable(pssd_handle h, int on)
 int pssd_profile_reset(pssd_handle h)
 {
     if (!h) return -1;
-    for (int i = 0; i < 8; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_count[i] = 0; }
+    for (int i = 0; i < 16; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_count[i] = 0; }
     h->launches = 0;
     return PSSD_OK;
 }
@@ -1542,6 +1546,7 @@ extern "C" int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k
     if (engine < 0 || engine > 2) return -2;
     if (m < 0 || n < 0 || k < 0 || batch < 1) return -3;
     return guarded(h, nullptr, [&]() -> int {
+        h->force_engine = 1;
         GemmArgs g; g.mode = engine == 0 ? GM_F64 : (engine == 1 ? GM_DF : GM_OZ);
         g.m = m; g.n = n; g.k = k; g.batch = batch;
         g.A = A; g.lda = lda; g.sA = sA; g.ta = ta; g.triA = triA;
@@ -1549,6 +1554,7 @@ extern "C" int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k
         g.Cin = Cin; g.ldcin = ldcin; g.sCin = sCin; g.C = C; g.ldc = ldc; g.sC = sC;
         g.kscale = kscale; g.alpha = alpha; g.beta = beta; g.lowerC = lowerC;
         gemm(h, g);
+        h->force_engine = 0;
         return PSSD_OK;
     });
 }
