@@ -211,7 +211,7 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s)
 template <class T>
 __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, long long sA, int k0, int kb,
                                                          T *Dinv, long long sD, T *Rinv, long long ldr,
-                                                         long long sR, int *info)
+                                                         long long sR, int *info, int info_off)
 {
     // kb <= PB.  Right-looking Cholesky of the diagonal block in shared memory
     // (one reciprocal per column), then its triangular inverse column by column.
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, lo
         if (tid == 0) {
             T d = S[j][j];
             if (!(d > 0) || !isfinite((double)d)) {
-                if (!bad) { bad = 1; if (info[z] == 0) info[z] = k0 + j + 1; }
+                if (!bad) { bad = 1; if (info[z] == 0) info[z] = info_off + k0 + j + 1; }
                 d = 1;
             }
             d = sqrt(d);
@@ -276,15 +276,15 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, lo
 
 template <class T>
 void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch, T *Dinv, long long sD, T *Rinv,
-                long long ldr, long long sR, int *info, cudaStream_t s)
+                long long ldr, long long sR, int *info, int info_off, cudaStream_t s)
 {
-    potrf_diag_kernel<T><<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info);
+    potrf_diag_kernel<T><<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info, info_off);
 }
 
 template void potrf_diag<double>(double *, long long, long long, int, int, int, double *, long long, double *,
-                                  long long, long long, int *, cudaStream_t);
+                                  long long, long long, int *, int, cudaStream_t);
 template void potrf_diag<float>(float *, long long, long long, int, int, int, float *, long long, float *,
-                                 long long, long long, int *, cudaStream_t);
+                                 long long, long long, int *, int, cudaStream_t);
 
 // --------------------------------------------------------------------------
 // HBM passes with 32x32 shared-memory tiles

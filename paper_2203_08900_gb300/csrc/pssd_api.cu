@@ -296,14 +296,13 @@ T *talloc(pssd_handle h, size_t count) { return (T *)walloc(h, count * sizeof(T)
 
 template <class T>
 void potrf(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T *Rinv, long long ldr,
-           long long sR, T *Dinv, int *dinfo)
+           long long sR, T *Dinv, int *dinfo, int info_off = 0)
 {
-    cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
     for (int k0 = 0; k0 < n; k0 += PB) {
         int kb = std::min(PB, n - k0);
         {
             Timed t(h, K_POTRF, batch * (kb * (double)kb * kb / 3.0 * 2.0));
-            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, PB * PB, Rinv, ldr, sR, dinfo, h->stream);
+            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, PB * PB, Rinv, ldr, sR, dinfo, info_off, h->stream);
         }
         int rest = n - k0 - kb;
         if (rest <= 0) continue;
@@ -362,6 +361,61 @@ void trtri_rec(pssd_handle h, const T *L, T *Rinv, int off, int s, long long ld,
     gemm(h, b);
 }
 
+// Recursive Cholesky with inverse, in place on the diagonal block (off, s):
+//   L11 = chol(A11), L21 = A21 L11^{-T}, A22 <- A22 - L21 L21^T, L22 = chol(A22),
+//   L^{-1}_21 = -L22^{-1} L21 L11^{-1};
+// the work sits in GEMMs of order s/2, which the tensor-core engines take;
+// blocks of at most CHOL_LEAF use the right-looking blocked factorisation.
+constexpr int CHOL_LEAF = 256;
+
+template <class T>
+void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, int batch, T *Rinv, long long sR,
+              T *Dinv, int *dinfo, T *tmp, long long sT)
+{
+    if (s <= CHOL_LEAF) {
+        potrf<T>(h, A + (long long)off * lda + off, s, lda, sA, batch,
+                 Rinv ? Rinv + (long long)off * lda + off : nullptr, lda, sR, Dinv, dinfo, off);
+        if (Rinv) trtri_rec<T>(h, A, Rinv, off, s, lda, sA, sR, batch, tmp, sT);
+        return;
+    }
+    const int nbk = (s + PB - 1) / PB;
+    const int hh = ((nbk + 1) / 2) * PB, q = s - hh;
+    chol_rec<T>(h, A, off, hh, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, sT);
+    T *A21 = A + (long long)(off + hh) * lda + off;
+    T *A22 = A + (long long)(off + hh) * lda + (off + hh);
+    {   // L21 = A21 L11^{-T} into tmp (the product reads whole rows of A21), then back
+        GemmArgs g; g.mode = gm_of<T>(); g.m = q; g.n = hh; g.k = hh; g.batch = batch;
+        g.A = A21; g.lda = lda; g.sA = sA;
+        g.B = Rinv + (long long)off * lda + off; g.ldb = lda; g.sB = sR; g.tb = 1; g.triB = TRI_UPPER;
+        g.C = tmp; g.ldc = hh; g.sC = sT;
+        gemm(h, g);
+        Timed t(h, K_HBM, 0);
+        for (int z = 0; z < batch; ++z)
+            scale_copy<T, T>(tmp + (long long)z * sT, hh, A21 + (long long)z * sA, lda, q, hh, 1.0, h->stream);
+    }
+    {   // A22 -= L21 L21^T (lower)
+        GemmArgs g; g.mode = gm_of<T>(); g.m = q; g.n = q; g.k = hh; g.batch = batch;
+        g.A = A21; g.lda = lda; g.sA = sA; g.B = A21; g.ldb = lda; g.sB = sA; g.tb = 1;
+        g.Cin = A22; g.ldcin = lda; g.sCin = sA; g.C = A22; g.ldc = lda; g.sC = sA;
+        g.alpha = -1.0; g.beta = 1.0; g.lowerC = 1;
+        gemm(h, g);
+    }
+    chol_rec<T>(h, A, off + hh, q, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, sT);
+    if (Rinv) {   // L^{-1}_21 = -L22^{-1} (L21 L11^{-1})
+        GemmArgs a; a.mode = gm_of<T>(); a.m = q; a.n = hh; a.k = hh; a.batch = batch;
+        a.A = A21; a.lda = lda; a.sA = sA;
+        a.B = Rinv + (long long)off * lda + off; a.ldb = lda; a.sB = sR; a.triB = TRI_LOWER;
+        a.C = tmp; a.ldc = hh; a.sC = sT;
+        gemm(h, a);
+        GemmArgs b; b.mode = gm_of<T>(); b.m = q; b.n = hh; b.k = q; b.batch = batch;
+        b.A = Rinv + (long long)(off + hh) * lda + (off + hh); b.lda = lda; b.sA = sR; b.triA = TRI_LOWER;
+        b.B = tmp; b.ldb = hh; b.sB = sT;
+        b.C = Rinv + (long long)(off + hh) * lda + off; b.ldc = lda; b.sC = sR;
+        b.alpha = -1.0;
+        gemm(h, b);
+    }
+}
+
 // Cholesky + inverse of `batch` SPD matrices; returns nonzero on breakdown
 template <class T>
 int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T *Rinv, long long sR,
@@ -370,13 +424,15 @@ int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch,
     Mark mk = mark(h);
     T *Dinv = talloc<T>(h, (size_t)PB * PB * batch);
     int *dinfo = ialloc(h, batch);
-    potrf<T>(h, A, n, lda, sA, batch, Rinv, lda, sR, Dinv, dinfo);
-    int bad = check_info(h, dinfo, batch, fail_index);
-    if (!bad && Rinv && n > PB) {
-        size_t tsz = (size_t)((n + 1) / 2 + PB) * ((n + 1) / 2 + PB);
-        T *tmp = talloc<T>(h, tsz * batch);
-        trtri_rec<T>(h, A, Rinv, 0, n, lda, sA, sR, batch, tmp, (long long)tsz);
+    cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
+    size_t tsz = (size_t)((n + 1) / 2 + PB) * ((n + 1) / 2 + PB);
+    T *tmp = talloc<T>(h, tsz * batch);
+    if (!Rinv) {   // the recursion needs L11^{-1}; keep it in a temporary
+        Rinv = talloc<T>(h, (size_t)lda * n * batch);
+        sR = lda * (long long)n;
     }
+    chol_rec<T>(h, A, 0, n, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, (long long)tsz);
+    int bad = check_info(h, dinfo, batch, fail_index);
     release(h, mk);
     return bad;
 }

@@ -51,10 +51,10 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
 // matrix (lower, in place); its triangular inverse goes to Dinv (PB x PB per
 // batch, ld PB) and, if Rinv != nullptr, into the same diagonal block of Rinv.
 // info[z] receives (first failing global pivot + 1) if a pivot is not positive.
-template <class T>
+template <class T>   // info[z] = info_off + first failing pivot (block-relative) + 1
 void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch,
                 T *Dinv, long long sD, T *Rinv, long long ldr, long long sR,
-                int *info, cudaStream_t s);
+                int *info, int info_off, cudaStream_t s);
 
 // Elementwise / HBM passes
 void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
