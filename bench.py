@@ -128,6 +128,44 @@ def run_reference(args):
     return 0
 
 
+def run_gemm_probe(args):
+    """One n x n x n contraction C = A B through a single engine of the library
+    (the engines' test hooks), W warm-ups and K timed launches, CUDA events."""
+    import torch
+
+    import paper_2203_08900_gb300 as P
+    from paper_2203_08900_gb300 import build as B
+    B.build()
+    n = args.n
+    g = torch.Generator(device="cuda"); g.manual_seed(5)
+    f64 = args.gemm_probe in ("dfma", "df", "oz")
+    dt = torch.float64 if f64 else torch.float32
+    A = torch.randn(n, n, device="cuda", dtype=dt, generator=g)
+    Bm = torch.randn(n, n, device="cuda", dtype=dt, generator=g)
+    h = P.Handle()
+
+    def run():
+        if f64:
+            return P.test_gemm_f64(A, Bm, engine={"dfma": 0, "df": 1, "oz": 2}[args.gemm_probe], handle=h)
+        return P.test_gemm_f32(A, Bm, use_tc=args.gemm_probe == "tc", handle=h)
+
+    for _ in range(args.warmup):
+        C = run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        C = run()
+    e1.record(); torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    ref = (A.double() @ Bm.double())
+    err = float((C.double() - ref).abs().max() / (A.double().abs() @ Bm.double().abs()).max())
+    print(json.dumps({"metric": "gemm probe", "engine": args.gemm_probe, "n": n, "s_per_gemm": t,
+                      "tflops": 2.0 * n ** 3 / t / 1e12, "max_rel_err": err,
+                      "note": "includes the engine's operand preparation passes"}))
+    return 0
+
+
 def run_batch(args):
     """Batched workload: one step = pssd_eig_batched over `count` instances."""
     import torch
@@ -195,11 +233,15 @@ def main():
                     help="split: one n x n sign + split per step (headline); batch: full diagonalisation of "
                          "512 Casida matrices with k log-uniform in [16, 1024], d ~ U[0.5, 50]")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--gemm-probe", default=None, choices=["dfma", "df", "oz", "tc", "f32"],
+                    help="time one n x n x n contraction on one engine (no solve)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.gemm_probe:
+        return run_gemm_probe(args)
 
     import numpy as np
     import torch
