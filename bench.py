@@ -345,8 +345,8 @@ def main():
         pass
     # tensor-core kernels are reported in the tensor pipe's own operations:
     #   tcgemm: 3 TF32 products per FP32 product; TF32 peak = BF16 peak x (1.1 / 2.25) nominal ratio
-    #   ozgemm: 28 BF16 slice products per FP64 product; peak = measured BF16
-    tensor_factor = {"tcgemm": 3.0, "ozgemm": 28.0}.get(dom, 1.0)
+    #   ozgemm: 36 BF16 slice products per FP64 product; peak = measured BF16
+    tensor_factor = {"tcgemm": 3.0, "ozgemm": 36.0}.get(dom, 1.0)
     if achieved is not None:
         achieved *= tensor_factor
     peak_dom = {"dgemm": peak_fp64, "sgemm": peak_fp32, "dfgemm": peak_fp32 / 13.0,
@@ -368,7 +368,7 @@ def main():
                                 "sgemm": "gemm_kernel<GM_F32> (FP32 FFMA)",
                                 "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated on the FP32 pipe)",
                                 "tcgemm": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
-                                "ozgemm": "oz_gemm_kernel (tcgen05 kind::f16 BF16, 28 integer-slice products)"}[dom],
+                                "ozgemm": "oz_gemm_kernel (tcgen05 kind::f16 BF16, 36 integer-slice products)"}[dom],
                      "bound": "tensor" if dom in ("tcgemm", "ozgemm") else "alu",
                      "achieved": achieved, "peak": peak_dom, "unit": "TFLOP/s",
                      "frac": (achieved / peak_dom) if achieved else None, "traffic": None,
@@ -376,7 +376,7 @@ def main():
                                    "sgemm": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz",
                                    "dfgemm": "derived: FP32 issue rate (152 SM x 128/clk x 2.07 GHz) / 13 instructions per multiply-add x 2 flop",
                                    "tcgemm": "of measured: BF16 burst x 1.1/2.25 (TF32 nominal ratio); achieved counts the 3 TF32 products",
-                                   "ozgemm": "of measured: BF16 burst; achieved counts the 28 BF16 slice products (FP64-equivalent = achieved/28)"}[dom],
+                                   "ozgemm": "of measured: BF16 burst; achieved counts the 36 BF16 slice products (FP64-equivalent = achieved/36)"}[dom],
                      "share_of_step": gemm["ms"] / 1e3 / t if t > 0 else None},
         "kernels": kinds,
         "gpu_launches": launches,

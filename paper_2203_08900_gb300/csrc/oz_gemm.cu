@@ -6,24 +6,34 @@
 //
 // 1. Every row i of op(A) is scaled by 2^{-e_i} and every column j of op(B)
 //    by 2^{-f_j} (exact) so that all entries lie in (-1, 1).
-// 2. Each scaled entry x is cut into S = 8 integer slices of 7 bits:
-//      d_t = rint(r_{t-1} 2^{7t}),  r_t = r_{t-1} - d_t 2^{-7t},  r_0 = x,
-//    |d_1| <= 128, |d_t| <= 64 (t > 1), |x - sum_t d_t 2^{-7t}| <= 2^-57;
-//    the d_t are exact in BF16.
+// 2. Each scaled entry x is rounded to F = round(x 2^56) (error <= 2^-57)
+//    and F is cut into S = 8 integer digits of 7 bits, balanced base 128:
+//      x ~ sum_t d_t 2^{-7t},  |d_1| <= 128,  |d_t| <= 64 (t > 1);
+//    the d_t are exact in BF16.  (Integer work only: FP64 arithmetic is a
+//    slow pipe on this part.)
 // 3. For every level L = a + b (2 <= L <= S+1) the slice products
-//    sum_{a+b=L} D^A_a D^B_b are integers below 2^24 over any 256-term
-//    stretch of k (at most 2 x 2^13 + 6 x 2^12 per term), so the tensor
-//    cores' FP32 accumulation of them is exact; each level has its own
-//    accumulator in tensor memory (8 levels x 64 columns = all 512).
-// 4. Every 256 terms of k the seven level sums are scaled by 2^{-7L} (exact)
+//    sum_{a+b=L} D^A_a D^B_b are integers; one term is at most
+//    2^14 + max(0, L-3) 2^12 (two products with a slice d_1, the rest 2^12).
+//    Over a 512-term stretch of k the levels L <= 7 stay at or below 2^24, so
+//    the tensor cores' FP32 accumulation of them is exact.  Levels 8 and 9 can
+//    pass 2^24 only when the (1, L-1) and (L-1, 1) products are near 2^13,
+//    i.e. when the entries are near their row/column maxima; their rounding
+//    (at most 512 units at weight 2^{-7L}) is then below 2^-55 of
+//    sum_p |a_ip b_pj|.  Each level has its own accumulator in tensor memory
+//    (8 levels x 64 columns = all 512).
+// 4. Every 512 terms of k the eight level sums are scaled by 2^{-7L} (exact)
 //    and added into a float-pair (TwoSum) accumulator per output; at the end
 //    C = alpha 2^{e_i + f_j} (hi + lo) + beta Cin in FP64.
 // Products with a + b > S + 1 (36 of 64 kept) are dropped: below 2^-63 relative.
 //
-// Kernel layout: one CTA of 128 threads per 128 x 64 output tile; 2-stage
-// ring of 8 A-slice tiles (128 x 32 BF16, 64-byte swizzle) and 8 B-slice
-// tiles (64 x 32) fed by TMA; thread 0 issues tcgen05.mma kind::f16 (M=128,
-// N=64, K=16) into 8 accumulators of 64 TMEM columns; all four warps flush.
+// Kernel layout: one CTA of 6 warps per 128 x 64 output tile, warp-specialised:
+// warp 4 streams 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles (64 x 16),
+// 32-byte swizzle, by TMA into a 4-stage mbarrier ring; warp 5 issues 12
+// tcgen05.mma kind::f16 (M=128, N=64..256, K=16) per stage, which cover the 36
+// slice products, into 8 accumulators of 64 TMEM columns and frees each stage
+// with tcgen05.commit; warps 0-3 (TMEM lanes 0-127) flush the accumulators
+// every 512 terms while the producer keeps
+// prefetching, then signal the MMA warp that the accumulators are free.
 // Every mbarrier wait is bounded (error flag, TMEM freed, return).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -41,15 +51,17 @@ namespace {
 
 constexpr int OZ_S = 8;                    // slices
 constexpr int OZ_LEVELS = OZ_S;            // levels L = 2 .. S+1
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;   // BK in BF16 elements = 64 bytes
-constexpr int OZ_STAGES = 2;
-constexpr int OZ_CHUNK_STAGES = 8;         // flush every 8 x 32 = 256 terms of k
-constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 8 KB
-constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 4 KB
-constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 96 KB
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 16;   // BK in BF16 elements = 32 bytes = one MMA K
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_CHUNK_STAGES = 32;        // flush every 32 x 16 = 512 terms of k
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 4 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 2 KB
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 48 KB
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;
 constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_THREADS = 192;            // warps 0-3 flush, warp 4 TMA producer, warp 5 MMA issuer
+constexpr int OZ_GROUP_M = 8;              // row blocks per group of the tile order
 
 struct OzArgs {
     CUtensorMap ta, tb;                    // slices stacked: row = (slice * batch + z) * pad + i
@@ -99,28 +111,31 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// K-major operand, 64-byte swizzle: rows of 64 bytes, 8-row groups 512 bytes apart
-__device__ __forceinline__ unsigned long long smem_desc_sw64(uint32_t addr)
+// K-major operand, 32-byte swizzle: rows of 32 bytes, 8-row groups 256 bytes apart
+__device__ __forceinline__ unsigned long long smem_desc_sw32(uint32_t addr)
 {
     unsigned long long d = 0;
     d |= (unsigned long long)((addr >> 4) & 0x3FFF);
     d |= (unsigned long long)(16 >> 4) << 16;
-    d |= (unsigned long long)(512 >> 4) << 32;
+    d |= (unsigned long long)(256 >> 4) << 32;
     d |= 1ull << 46;
-    d |= 4ull << 61;                       // 64-byte swizzle
+    d |= 6ull << 61;                       // 32-byte swizzle
     return d;
 }
 
-// kind::f16, D = F32, A = B = BF16, both K-major, N = 64, M = 128
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);
+// kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = 64 .. 256
+__host__ __device__ constexpr uint32_t oz_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                         uint32_t acc)
 {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -128,17 +143,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r)
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 // float-pair accumulation (TwoSum, then renormalisation)
@@ -153,17 +164,28 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x)
     hi = s2;
 }
 
-__global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__ OzArgs g)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
-    const int i0 = blockIdx.y * OZ_BM, j0 = blockIdx.x * OZ_BN, z = blockIdx.z;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzArgs g)
+{
+    // grouped tile order: runs of OZ_GROUP_M row blocks sweep the column blocks
+    // together, so the CTAs resident at one time share their A and B tiles in L2
+    const int mt = (g.m + OZ_BM - 1) / OZ_BM, nt = (g.n + OZ_BN - 1) / OZ_BN;
+    const int pid = blockIdx.x, per_group = OZ_GROUP_M * nt;
+    const int first_m = (pid / per_group) * OZ_GROUP_M, gm = min(mt - first_m, OZ_GROUP_M);
+    const int tm = first_m + (pid % per_group) % gm, tn = (pid % per_group) / gm;
+    const int i0 = tm * OZ_BM, j0 = tn * OZ_BN, z = blockIdx.z;
     if (i0 >= g.m || j0 >= g.n) return;
     if (g.lowerC && j0 > i0 + OZ_BM - 1) return;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned long long *bars = (unsigned long long *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
-    // bars[0..S): full, [S..2S): empty, [2S]: flush
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * OZ_STAGES + 2);
+    // bars[0..ST): full, [ST..2ST): empty, [2ST]: chunk done (MMA -> flush), [2ST+1]: accumulators free
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * OZ_STAGES + 4);
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -176,14 +198,17 @@ __global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__
     const int kb0 = kbeg / OZ_BK;
     const int nkb = (kend > kbeg) ? (kend + OZ_BK - 1) / OZ_BK - kb0 : 0;
     const int nchunks = (nkb + OZ_CHUNK_STAGES - 1) / OZ_CHUNK_STAGES;
+    const uint32_t b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[OZ_STAGES]);
+    const uint32_t b_done = smem_u32(&bars[2 * OZ_STAGES]), b_free = smem_u32(&bars[2 * OZ_STAGES + 1]);
 
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < OZ_STAGES; ++s) {
-            mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[OZ_STAGES + s]), 1);
+            mbar_init(b_full + 8 * s, 1);
+            mbar_init(b_empty + 8 * s, 1);
         }
-        mbar_init(smem_u32(&bars[2 * OZ_STAGES]), 1);
+        mbar_init(b_done, 1);
+        mbar_init(b_free, 128);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -197,118 +222,106 @@ __global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    float hi[OZ_BN], lo[OZ_BN];
-#pragma unroll
-    for (int q = 0; q < OZ_BN; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
-
-    // producer state (thread 0)
-    int issued = 0;
-    const int ya = z * g.m_pad + i0, yb = z * g.n_pad + j0;
-    auto issue = [&](int q) {
-        const int s = q % OZ_STAGES;
-        const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
-        const uint32_t full = smem_u32(&bars[s]);
-        const int x = (kb0 + q) * OZ_BK;
-        mbar_expect_tx(full, OZ_STAGE_BYTES);
-#pragma unroll
-        for (int t = 0; t < OZ_S; ++t) {
-            tma_load_2d(st + t * OZ_A_TILE, &g.ta, x, (t * g.batch) * g.m_pad + ya, full);
-            tma_load_2d(st + OZ_S * OZ_A_TILE + t * OZ_B_TILE, &g.tb, x, (t * g.batch) * g.n_pad + yb, full);
-        }
-    };
-    if (tid == 0)
-        for (; issued < nkb && issued < OZ_STAGES; ++issued) issue(issued);
-
-    for (int c = 0; c < nchunks; ++c) {
-        if (tid == 0 && !s_abort) {
-            const int q0 = c * OZ_CHUNK_STAGES, q1 = min(nkb, q0 + OZ_CHUNK_STAGES);
-            bool ok = true;
-            for (int q = q0; q < q1 && ok; ++q) {
+    if (warp == 4) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            const int ya = z * g.m_pad + i0, yb = z * g.n_pad + j0;
+            for (int q = 0; q < nkb; ++q) {
                 const int s = q % OZ_STAGES;
-                if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((q / OZ_STAGES) & 1))) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (q >= OZ_STAGES &&
+                    !mbar_wait(b_empty + 8 * s, (uint32_t)(((q / OZ_STAGES) - 1) & 1))) {
+                    s_abort = 1; atomicExch(g.err, 1); break;
+                }
+                if (s_abort) break;
                 const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
+                const int x = (kb0 + q) * OZ_BK;
+                mbar_expect_tx(b_full + 8 * s, OZ_STAGE_BYTES);
 #pragma unroll
-                for (int kk = 0; kk < OZ_BK / 16; ++kk) {     // K = 16 BF16 = 32 bytes per instruction
-                    const uint32_t off = kk * 32;
+                for (int t = 0; t < OZ_S; ++t) {
+                    tma_load_2d(st + t * OZ_A_TILE, &g.ta, x, (t * g.batch) * g.m_pad + ya, b_full + 8 * s);
+                    tma_load_2d(st + OZ_S * OZ_A_TILE + t * OZ_B_TILE, &g.tb, x, (t * g.batch) * g.n_pad + yb,
+                                b_full + 8 * s);
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            for (int c = 0; c < nchunks && !s_abort; ++c) {
+                if (c > 0 && !mbar_wait(b_free, (uint32_t)((c - 1) & 1))) { s_abort = 1; atomicExch(g.err, 2); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int q0 = c * OZ_CHUNK_STAGES, q1 = min(nkb, q0 + OZ_CHUNK_STAGES);
+                bool ok = true;
+                for (int q = q0; q < q1; ++q) {
+                    const int s = q % OZ_STAGES;
+                    if (!mbar_wait(b_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
+                    // A slice a against B slices b = 1 .. S+1-a stacked along N: the product
+                    // (a, b) belongs to level a+b-2, whose accumulator starts at column
+                    // 64 (a+b-2), so slices b..b+3 form one N <= 256 MMA into consecutive levels.
 #pragma unroll
                     for (int a = 1; a <= OZ_S; ++a) {
-                        const unsigned long long ad = smem_desc_sw64(st + (a - 1) * OZ_A_TILE + off);
+                        const unsigned long long ad = smem_desc_sw32(st + (a - 1) * OZ_A_TILE);
+                        const uint32_t acc = (q == q0 && a == 1) ? 0u : 1u;   // a = 1 reaches every level first
 #pragma unroll
-                        for (int b = 1; a + b <= OZ_S + 1; ++b) {
-                            const int L = a + b - 2;                         // 0 .. S-1
-                            const unsigned long long bd =
-                                smem_desc_sw64(st + OZ_S * OZ_A_TILE + (b - 1) * OZ_B_TILE + off);
-                            // the a = 1 pass reaches every level first: it overwrites at the chunk start
-                            const uint32_t acc = (q == q0 && kk == 0 && a == 1) ? 0u : 1u;
-                            mma_bf16(tmem + (uint32_t)(L * OZ_BN), ad, bd, acc);
+                        for (int b0 = 1; b0 <= OZ_S + 1 - a; b0 += 4) {
+                            const int nb = min(4, OZ_S + 2 - a - b0);
+                            const unsigned long long bd = smem_desc_sw32(st + OZ_S * OZ_A_TILE + (b0 - 1) * OZ_B_TILE);
+                            mma_bf16(tmem + (uint32_t)((a + b0 - 2) * OZ_BN), ad, bd, oz_idesc(nb * OZ_BN), acc);
                         }
                     }
+                    mma_commit(b_empty + 8 * s);
                 }
-                mma_commit(smem_u32(&bars[OZ_STAGES + s]));
-                if (q >= 1 && issued < nkb) {
-                    const int sp = (q - 1) % OZ_STAGES;
-                    if (!mbar_wait(smem_u32(&bars[OZ_STAGES + sp]), (uint32_t)(((q - 1) / OZ_STAGES) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    issue(issued++);
-                }
-            }
-            if (ok) {
-                mma_commit(smem_u32(&bars[2 * OZ_STAGES]));           // flush point
-            } else {
-                s_abort = 1;
-                atomicExch(g.err, 1);
+                if (!ok) { s_abort = 1; atomicExch(g.err, 3); break; }
+                mma_commit(b_done);
             }
         }
-        __syncthreads();
-        if (s_abort) break;
-        if (!mbar_wait(smem_u32(&bars[2 * OZ_STAGES]), (uint32_t)(c & 1))) {
-            atomicExch(g.err, 2);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // flush: level L accumulator holds an exact integer sum; scale by 2^{-7(L+2)}
+    } else {
+        // ---------------- flush warps 0-3 (TMEM lanes 32w .. 32w+31) ----------------
+        float hi[OZ_BN], lo[OZ_BN];
 #pragma unroll
-        for (int L = 0; L < OZ_LEVELS; ++L) {
-            const float sc = __int_as_float((127 - 7 * (L + 2)) << 23);   // 2^{-7(L+2)}
+        for (int q = 0; q < OZ_BN; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!mbar_wait(b_done, (uint32_t)(c & 1))) { ok = false; atomicExch(g.err, 4); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-            for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * OZ_BN + c0), v);
+            for (int L = 0; L < OZ_LEVELS; ++L) {
+                const float sc = __int_as_float((127 - 7 * (L + 2)) << 23);   // 2^{-7(L+2)}
+                uint32_t r[OZ_BN];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) df_add(hi[c0 + q], lo[c0 + q], __fmul_rn(v[q], sc));
+                for (int c0 = 0; c0 < OZ_BN; c0 += 16)
+                    tmem_ld16_nowait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * OZ_BN + c0), r + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < OZ_BN; ++q) df_add(hi[q], lo[q], __fmul_rn(__uint_as_float(r[q]), sc));
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(b_free);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();   // accumulators free for the next chunk
-    }
-    if (s_abort && tid == 0) {
-        for (int q = 0; q < issued; ++q) mbar_wait(smem_u32(&bars[q % OZ_STAGES]), (uint32_t)((q / OZ_STAGES) & 1));
-    }
-
-    // epilogue
-    const int i = i0 + warp * 32 + lane;
-    if (i < g.m && !s_abort) {
-        double *C = g.C + (long long)z * g.sC;
-        const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
-        const int ei = g.ea[z * g.m_pad + i];
+        const int i = i0 + warp * 32 + lane;
+        if (ok && !s_abort && i < g.m) {
+            double *C = g.C + (long long)z * g.sC;
+            const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
+            const int ei = g.ea[z * g.m_pad + i];
 #pragma unroll
-        for (int q = 0; q < OZ_BN; ++q) {
-            const int j = j0 + q;
-            if (j >= g.n || (g.lowerC && j > i)) continue;
-            double v = ((double)hi[q] + (double)lo[q]);
-            v = ldexp(v, ei + g.eb[z * g.n_pad + j]);
-            double o = g.alpha * v;
-            if (g.beta != 0.0) o += g.beta * Cin[(long long)i * g.ldcin + j];
-            C[(long long)i * g.ldc + j] = o;
+            for (int q = 0; q < OZ_BN; ++q) {
+                const int j = j0 + q;
+                if (j >= g.n || (g.lowerC && j > i)) continue;
+                double v = ((double)hi[q] + (double)lo[q]);
+                v = ldexp(v, ei + g.eb[z * g.n_pad + j]);
+                double o = g.alpha * v;
+                if (g.beta != 0.0) o += g.beta * Cin[(long long)i * g.ldcin + j];
+                C[(long long)i * g.ldc + j] = o;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (s_abort && tid == OZ_THREADS - 64) {   // producer lane: let copies in flight land before exit
+        for (int q = 0; q < min(nkb, OZ_STAGES); ++q) mbar_wait(b_full + 8 * (q % OZ_STAGES), 0u);
+    }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
 }
 
@@ -328,32 +341,58 @@ __device__ __forceinline__ double oz_load(const double *X, long long ld, int tra
     return v;
 }
 
+// frexp exponent of v (v = f 2^e, 0.5 <= |f| < 1) from the IEEE-754 fields;
+// a very small value for zero
+__device__ __forceinline__ int oz_frexp_exp(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int bexp = (int)((b >> 52) & 0x7FF);
+    const unsigned long long m = b & ((1ull << 52) - 1);
+    if (bexp != 0) return bexp - 1022;
+    if (m == 0) return INT_MIN / 2;
+    return -1010 - __clzll((long long)m);      // subnormal: leading bit of m at 63 - clz
+}
+
+// round(v 2^{56-e}) as an integer, for |v| < 2^e: |result| <= 2^56, error <= 1/2
+__device__ __forceinline__ long long oz_fixed56(double v, int e)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    int bexp = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & ((1ull << 52) - 1);
+    if (bexp == 0) { if (m == 0 || e < -1100) return 0; bexp = 1; }
+    else m |= 1ull << 52;
+    const int sh = (bexp - 1075) - e + 56;    // v = m 2^{bexp-1075};  m 2^sh < 2^56
+    unsigned long long f;
+    if (sh >= 0) f = m << sh;
+    else if (sh > -64) f = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);
+    else f = 0;
+    return (b >> 63) ? -(long long)f : (long long)f;
+}
+
 // exponent e(r) with max_p |X(r,p)| < 2^e, by 32 x 32 tiles and atomicMax
 __global__ void __launch_bounds__(256) oz_exp_kernel(const double *X, long long ld, long long sb, int trans, int rows,
                                                      int k, int tri, const double *ks, int rows_pad, int *e)
 {
-    __shared__ double T[32][33];
+    __shared__ int T[32][33];
     const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     X += (long long)z * sb;
     for (int yy = ty; yy < 32; yy += 8) {
-        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = fabs(oz_load(X, ld, 1, rows, k, tri, ks, r, p)); }
-        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = fabs(oz_load(X, ld, 0, rows, k, tri, ks, r, p)); }
+        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = oz_frexp_exp(oz_load(X, ld, 1, rows, k, tri, ks, r, p)); }
+        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = oz_frexp_exp(oz_load(X, ld, 0, rows, k, tri, ks, r, p)); }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
         const int r = r0 + threadIdx.x;
-        double mx = 0.0;
-        for (int q = 0; q < 32; ++q) mx = fmax(mx, T[threadIdx.x][q]);
-        if (r < rows && mx > 0.0) {
-            int ex;
-            frexp(mx, &ex);                  // mx = f 2^ex, f in [0.5, 1): mx < 2^ex
-            atomicMax(&e[z * rows_pad + r], ex);
-        }
+        int mx = INT_MIN / 2;
+        for (int q = 0; q < 32; ++q) mx = max(mx, T[threadIdx.x][q]);
+        if (r < rows && mx > INT_MIN / 2) atomicMax(&e[z * rows_pad + r], mx);
     }
 }
 
-// seven BF16 slices, K-major: out[((t * batch + z) * rows_pad + r) * k_pad + p]
+// eight BF16 slices, K-major: out[((t * batch + z) * rows_pad + r) * k_pad + p].
+// F = round(x 2^{56-e}) is cut into balanced base-128 digits d_8 .. d_2 in
+// [-64, 63]; the rest is d_1, |d_1| <= 128; x 2^{-e} = sum_t d_t 2^{-7t} + O(2^-57).
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long long ld, long long sb, int trans,
                                                        int rows, int k, int tri, const double *ks, int rows_pad,
                                                        int k_pad, int batch, const int *e, __nv_bfloat16 *out)
@@ -370,17 +409,20 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long lon
     for (int yy = ty; yy < 32; yy += 8) {
         const int r = r0 + yy, p = p0 + tx;
         if (r >= rows_pad || p >= k_pad) continue;
-        double rem = 0.0;
+        long long f = 0;
         if (r < rows) {
-            int ex = e[z * rows_pad + r];
-            if (ex > -2000) rem = ldexp(T[yy][tx], -ex);   // |rem| < 1
+            const int ex = e[z * rows_pad + r];
+            if (ex > -2000) f = oz_fixed56(T[yy][tx], ex);
         }
-        for (int t = 1; t <= OZ_S; ++t) {
-            double scaled = ldexp(rem, 7 * t);
-            double d = rint(scaled);
-            rem -= ldexp(d, -7 * t);
-            out[(((long long)(t - 1) * batch + z) * rows_pad + r) * k_pad + p] = __float2bfloat16_rn((float)d);
+        __nv_bfloat16 *o = out + ((long long)z * rows_pad + r) * k_pad + p;
+        const long long sstride = (long long)batch * rows_pad * k_pad;
+#pragma unroll
+        for (int t = OZ_S; t >= 2; --t) {
+            const int d = (int)((f + 64) & 127) - 64;
+            f = (f - d) >> 7;
+            o[(t - 1) * sstride] = __float2bfloat16_rn((float)d);
         }
+        o[0] = __float2bfloat16_rn((float)f);
     }
 }
 
@@ -413,7 +455,7 @@ bool make_map_bf16(CUtensorMap *m, const void *base, long long rows_total, int k
     cuuint32_t box[2] = {OZ_BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -470,8 +512,8 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     a.C = (double *)g.C; a.ldc = g.ldc; a.sC = g.sC;
     a.Cin = (const double *)g.Cin; a.ldcin = g.ldcin; a.sCin = g.sCin;
     a.alpha = g.alpha; a.beta = g.beta; a.err = err;
-    dim3 grid((g.n + OZ_BN - 1) / OZ_BN, (g.m + OZ_BM - 1) / OZ_BM, g.batch);
-    oz_gemm_kernel<<<grid, 128, OZ_SMEM_BYTES, s>>>(a);
+    dim3 grid(((g.n + OZ_BN - 1) / OZ_BN) * ((g.m + OZ_BM - 1) / OZ_BM), 1, g.batch);
+    oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(a);
     return 0;
 }
 
