@@ -27,21 +27,19 @@
 // Products with a + b > S + 1 (36 of 64 kept) are dropped: below 2^-63 relative.
 //
 // Kernel layout: one CTA of 6 warps per 128 x 64 output tile, warp-specialised:
-// warp 4 streams 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles (64 x 16),
-// 32-byte swizzle, by TMA into a 4-stage mbarrier ring; warp 5 issues 12
+// warp 4 streams the 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles
+// (64 x 16) of one k block, stored pre-tiled and pre-swizzled (32-byte swizzle)
+// by the slicing pass, as two contiguous bulk copies into a 4-stage mbarrier ring; warp 5 issues 12
 // tcgen05.mma kind::f16 (M=128, N=64..256, K=16) per stage, which cover the 36
 // slice products, into 8 accumulators of 64 TMEM columns and frees each stage
 // with tcgen05.commit; warps 0-3 (TMEM lanes 0-127) flush the accumulators
 // every 512 terms while the producer keeps
 // prefetching, then signal the MMA warp that the accumulators are free.
 // Every mbarrier wait is bounded (error flag, TMEM freed, return).
-#include <cuda.h>
 #include <cuda_bf16.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <climits>
-#include <mutex>
 
 #include "pssd_internal.h"
 
@@ -64,7 +62,10 @@ constexpr int OZ_THREADS = 192;            // warps 0-3 flush, warp 4 TMA produc
 constexpr int OZ_GROUP_M = 8;              // row blocks per group of the tile order
 
 struct OzArgs {
-    CUtensorMap ta, tb;                    // slices stacked: row = (slice * batch + z) * pad + i
+    // slices, tiled: block (z, row tile, k block) = 8 slices x tile rows x 16 k,
+    // 32-byte-swizzled rows, contiguous (32 KB for A, 16 KB for B)
+    const __nv_bfloat16 *sa, *sb;
+    int kblocks;                           // k_pad / 16
     int m, n, k, batch, m_pad, n_pad;
     int triA, triB, lowerC;
     const int *ea, *eb;                    // exponents per row of op(A) (batch*m_pad), per column of op(B)
@@ -102,12 +103,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"((unsigned long long)src), "r"(bytes), "r"(bar)
         : "memory");
 }
 
@@ -225,7 +225,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     if (warp == 4) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            const int ya = z * g.m_pad + i0, yb = z * g.n_pad + j0;
+            const __nv_bfloat16 *srca = g.sa + (((long long)z * (g.m_pad / OZ_BM) + tm) * g.kblocks + kb0) *
+                                                   (OZ_S * OZ_BM * OZ_BK);
+            const __nv_bfloat16 *srcb = g.sb + (((long long)z * (g.n_pad / OZ_BN) + tn) * g.kblocks + kb0) *
+                                                   (OZ_S * OZ_BN * OZ_BK);
             for (int q = 0; q < nkb; ++q) {
                 const int s = q % OZ_STAGES;
                 if (q >= OZ_STAGES &&
@@ -234,14 +237,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                 }
                 if (s_abort) break;
                 const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
-                const int x = (kb0 + q) * OZ_BK;
                 mbar_expect_tx(b_full + 8 * s, OZ_STAGE_BYTES);
-#pragma unroll
-                for (int t = 0; t < OZ_S; ++t) {
-                    tma_load_2d(st + t * OZ_A_TILE, &g.ta, x, (t * g.batch) * g.m_pad + ya, b_full + 8 * s);
-                    tma_load_2d(st + OZ_S * OZ_A_TILE + t * OZ_B_TILE, &g.tb, x, (t * g.batch) * g.n_pad + yb,
-                                b_full + 8 * s);
-                }
+                bulk_load(st, srca + (long long)q * (OZ_S * OZ_BM * OZ_BK), OZ_S * OZ_A_TILE, b_full + 8 * s);
+                bulk_load(st + OZ_S * OZ_A_TILE, srcb + (long long)q * (OZ_S * OZ_BN * OZ_BK), OZ_S * OZ_B_TILE,
+                          b_full + 8 * s);
             }
         }
     } else if (warp == 5) {
@@ -390,12 +389,17 @@ __global__ void __launch_bounds__(256) oz_exp_kernel(const double *X, long long 
     }
 }
 
-// eight BF16 slices, K-major: out[((t * batch + z) * rows_pad + r) * k_pad + p].
+// eight BF16 slices in the tiled layout the GEMM streams: for row r of tile
+// rr = r % tile_rows and column p (k block p / 16, kk = p % 16) of slice t the
+// element sits in block ((z * rows_pad / tile_rows + r / tile_rows) * kblocks + p / 16)
+// of 8 * tile_rows * 16 elements, at t * tile_rows * 16 + rr * 16 + kk with the
+// 16-byte half of the 32-byte row flipped when bit 2 of rr is set (the 32-byte
+// shared-memory swizzle the MMA descriptors expect).
 // F = round(x 2^{56-e}) is cut into balanced base-128 digits d_8 .. d_2 in
 // [-64, 63]; the rest is d_1, |d_1| <= 128; x 2^{-e} = sum_t d_t 2^{-7t} + O(2^-57).
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long long ld, long long sb, int trans,
                                                        int rows, int k, int tri, const double *ks, int rows_pad,
-                                                       int k_pad, int batch, const int *e, __nv_bfloat16 *out)
+                                                       int k_pad, int tile_rows, const int *e, __nv_bfloat16 *out)
 {
     __shared__ double T[32][33];
     const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
@@ -406,6 +410,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long lon
         else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = oz_load(X, ld, 0, rows, k, tri, ks, r, p); }
     }
     __syncthreads();
+    const int kblocks = k_pad / 16, tiles = rows_pad / tile_rows;
     for (int yy = ty; yy < 32; yy += 8) {
         const int r = r0 + yy, p = p0 + tx;
         if (r >= rows_pad || p >= k_pad) continue;
@@ -414,8 +419,11 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long lon
             const int ex = e[z * rows_pad + r];
             if (ex > -2000) f = oz_fixed56(T[yy][tx], ex);
         }
-        __nv_bfloat16 *o = out + ((long long)z * rows_pad + r) * k_pad + p;
-        const long long sstride = (long long)batch * rows_pad * k_pad;
+        const int rr = r % tile_rows, kk = p & 15;
+        const long long blk = ((long long)z * tiles + r / tile_rows) * kblocks + (p >> 4);
+        __nv_bfloat16 *o = out + blk * (OZ_S * tile_rows * 16) + rr * 16 + ((((kk >> 3) ^ (rr >> 2)) & 1) << 3) +
+                           (kk & 7);
+        const int sstride = tile_rows * 16;
 #pragma unroll
         for (int t = OZ_S; t >= 2; --t) {
             const int d = (int)((f + 64) & 127) - 64;
@@ -432,38 +440,11 @@ __global__ void fill_int_kernel(int *x, long long n, int v)
         x[i] = v;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
-std::once_flag g_enc_once;
-
-bool get_enc()
-{
-    std::call_once(g_enc_once, []() {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            g_enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    });
-    return g_enc != nullptr;
-}
-
-bool make_map_bf16(CUtensorMap *m, const void *base, long long rows_total, int k_pad, int box_rows)
-{
-    cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows_total};
-    cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-    cuuint32_t box[2] = {OZ_BK, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 size_t oz_gemm_workspace_bytes(const GemmArgs &g)
 {
-    const long long kp = (g.k + 7) / 8 * 8;
+    const long long kp = (g.k + 15) / 16 * 16;
     const long long mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
     return (size_t)(OZ_S * (mp + np) * kp * g.batch) * 2 + (size_t)(mp + np) * g.batch * sizeof(int) + 2048;
 }
@@ -471,7 +452,6 @@ size_t oz_gemm_workspace_bytes(const GemmArgs &g)
 int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
-    if (!get_enc()) return -1;
     static bool attr_done = false;
     if (!attr_done) {
         if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES) !=
@@ -479,7 +459,7 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
             return -2;
         attr_done = true;
     }
-    const int kp = (g.k + 7) / 8 * 8;
+    const int kp = (g.k + 15) / 16 * 16;
     const int mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
     unsigned char *base = (unsigned char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     __nv_bfloat16 *sa = (__nv_bfloat16 *)base;
@@ -493,19 +473,17 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
         oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
                                          (const double *)g.kscale, mp, ea);
         oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                           (const double *)g.kscale, mp, kp, g.batch, ea, sa);
+                                           (const double *)g.kscale, mp, kp, OZ_BM, ea, sa);
     }
     {
         dim3 gr((kp + 31) / 32, (np + 31) / 32, g.batch);
         oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
                                          np, eb);
         oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                           np, kp, g.batch, eb, sb);
+                                           np, kp, OZ_BN, eb, sb);
     }
     OzArgs a;
-    if (!make_map_bf16(&a.ta, sa, (long long)OZ_S * mp * g.batch, kp, OZ_BM) ||
-        !make_map_bf16(&a.tb, sb, (long long)OZ_S * np * g.batch, kp, OZ_BN))
-        return -3;
+    a.sa = sa; a.sb = sb; a.kblocks = kp / 16;
     a.m = g.m; a.n = g.n; a.k = g.k; a.batch = g.batch; a.m_pad = mp; a.n_pad = np;
     a.triA = g.triA; a.triB = g.triB; a.lowerC = g.lowerC;
     a.ea = ea; a.eb = eb;
