@@ -312,7 +312,7 @@ def main():
     last = infos[-1]
     rs = [x for x in last["r_used"][:last["passes"]]]
     # algorithmic FLOPs: the library's exact structural count of every contraction it launched
-    fl = sum(kinds[kk]["flops"] for kk in ("dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm", "potrf_diag")) / args.steps
+    fl = sum(kinds[kk]["flops"] for kk in ("dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm", "chol_leaf")) / args.steps
     solves = args.steps * ws
     s_per_solve = t / solves
     # accuracy of the split, measured outside the timed region: S = Q Q^T Sigma,

@@ -23,7 +23,7 @@ FLAG_RESIDUALS = 1
 
 # kinds reported by profile_read
 K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM, K_OZGEMM = range(9)
-KIND_NAMES = ["dgemm", "potrf_diag", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm", "ozgemm"]
+KIND_NAMES = ["dgemm", "chol_leaf", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm", "ozgemm"]
 FLAG_NO_TENSOR_CORES = 2
 FLAG_EMU_SIMT = 4
 

@@ -209,82 +209,95 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s)
 // Cholesky of one diagonal block (<= 64) and its triangular inverse
 // --------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) potrf_diag_kernel(T *A, long long lda, long long sA, int k0, int kb,
-                                                         T *Dinv, long long sD, T *Rinv, long long ldr,
-                                                         long long sR, int *info, int info_off)
+__global__ void __launch_bounds__(512) chol_leaf_kernel(T *A, long long lda, long long sA, T *Rinv, long long ldr,
+                                                        long long sR, int off, int s, int *info)
 {
-    // kb <= PB.  Right-looking Cholesky of the diagonal block in shared memory
-    // (one reciprocal per column), then its triangular inverse column by column.
-    __shared__ T S[PB][PB + 1];
-    __shared__ T Tm[PB][PB + 1];
-    __shared__ T rinv[PB];
+    // The s x s diagonal block at (off, off) of batch matrix blockIdx.x, held in
+    // shared memory (row stride s + 1): right-looking Cholesky, one square root
+    // and one reciprocal per column, then X = L^{-1} by row-oriented forward
+    // substitution (row j of X is final once divided by L_jj, and is then
+    // eliminated from the rows below).  blockDim = (32, 16).
+    extern __shared__ unsigned char leaf_smem[];
+    T *L = (T *)leaf_smem;
+    T *X = L + (size_t)s * (s + 1);
+    T *rv = X + (size_t)s * (s + 1);
     __shared__ int bad;
-    const int z = blockIdx.x, tid = threadIdx.x;
-    A += (long long)z * sA;
+    const int ls = s + 1, z = blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    A += (long long)z * sA + (long long)off * lda + off;
+    Rinv += (long long)z * sR + (long long)off * ldr + off;
     if (tid == 0) bad = 0;
-    for (int e = tid; e < PB * PB; e += 256) {
-        int i = e / PB, j = e % PB;
-        T v = 0;
-        if (i < kb && j <= i) v = A[(long long)(k0 + i) * lda + (k0 + j)];
-        S[i][j] = v;
-        Tm[i][j] = 0;
-    }
+    for (int i = ty; i < s; i += 16)
+        for (int j = tx; j < s; j += 32) {
+            L[i * ls + j] = (j <= i) ? A[(long long)i * lda + j] : (T)0;
+            X[i * ls + j] = (i == j) ? (T)1 : (T)0;
+        }
     __syncthreads();
-    for (int j = 0; j < kb; ++j) {
+    for (int j = 0; j < s; ++j) {
         if (tid == 0) {
-            T d = S[j][j];
+            T d = L[j * ls + j];
             if (!(d > 0) || !isfinite((double)d)) {
-                if (!bad) { bad = 1; if (info[z] == 0) info[z] = info_off + k0 + j + 1; }
+                if (!bad) { bad = 1; if (info[z] == 0) info[z] = off + j + 1; }
                 d = 1;
             }
             d = sqrt(d);
-            S[j][j] = d;
-            rinv[j] = (T)1 / d;
+            L[j * ls + j] = d;
+            rv[j] = (T)1 / d;
         }
         __syncthreads();
-        const T r = rinv[j];
-        for (int i = j + 1 + tid; i < kb; i += 256) S[i][j] *= r;
+        const T r = rv[j];
+        for (int i = j + 1 + tid; i < s; i += 512) L[i * ls + j] *= r;
         __syncthreads();
-        const int w = kb - j - 1;
-        for (int e = tid; e < w * w; e += 256) {
-            int i = j + 1 + e / w, l = j + 1 + e % w;
-            if (l <= i) S[i][l] -= S[i][j] * S[l][j];
+        for (int i = j + 1 + ty; i < s; i += 16) {
+            const T lij = L[i * ls + j];
+            for (int l = j + 1 + tx; l <= i; l += 32) L[i * ls + l] -= lij * L[l * ls + j];
         }
         __syncthreads();
     }
-    // inverse of the lower-triangular factor: column c by forward substitution
-    if (tid < kb) {
-        const int c = tid;
-        Tm[c][c] = rinv[c];
-        for (int i = c + 1; i < kb; ++i) {
-            T t = 0;
-            for (int m = c; m < i; ++m) t = fma(S[i][m], Tm[m][c], t);
-            Tm[i][c] = -t * rinv[i];
+    for (int j = 0; j < s; ++j) {
+        const T r = rv[j];
+        for (int c = tid; c <= j; c += 512) X[j * ls + c] *= r;
+        __syncthreads();
+        for (int i = j + 1 + ty; i < s; i += 16) {
+            const T lij = L[i * ls + j];
+            for (int c = tx; c <= j; c += 32) X[i * ls + c] -= lij * X[j * ls + c];
         }
+        __syncthreads();
     }
-    __syncthreads();
-    T *D = Dinv + (long long)z * sD;
-    for (int e = tid; e < PB * PB; e += 256) {
-        int i = e / PB, j = e % PB;
-        D[e] = (i < kb && j <= i) ? Tm[i][j] : (T)0;
-        if (i < kb && j < kb) {
-            A[(long long)(k0 + i) * lda + (k0 + j)] = (j <= i) ? S[i][j] : (T)0;
-            if (Rinv) Rinv[(long long)z * sR + (long long)(k0 + i) * ldr + (k0 + j)] = (j <= i) ? Tm[i][j] : (T)0;
+    for (int i = ty; i < s; i += 16)
+        for (int j = tx; j < s; j += 32) {
+            A[(long long)i * lda + j] = (j <= i) ? L[i * ls + j] : (T)0;
+            Rinv[(long long)i * ldr + j] = (j <= i) ? X[i * ls + j] : (T)0;
         }
-    }
 }
 
 template <class T>
-void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch, T *Dinv, long long sD, T *Rinv,
-                long long ldr, long long sR, int *info, int info_off, cudaStream_t s)
+size_t chol_leaf_smem(int s)
 {
-    potrf_diag_kernel<T><<<batch, 256, 0, s>>>(A, lda, sA, k0, kb, Dinv, sD, Rinv, ldr, sR, info, info_off);
+    return (2 * (size_t)s * (s + 1) + s) * sizeof(T);
 }
 
-template void potrf_diag<double>(double *, long long, long long, int, int, int, double *, long long, double *,
-                                  long long, long long, int *, int, cudaStream_t);
-template void potrf_diag<float>(float *, long long, long long, int, int, int, float *, long long, float *,
-                                 long long, long long, int *, int, cudaStream_t);
+template <class T>
+int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long long sR, int off, int s, int batch,
+              int *info, cudaStream_t st)
+{
+    static bool attr = false;
+    const size_t sm = chol_leaf_smem<T>(CholLeaf<T>::max_s);
+    if (!attr) {
+        if (cudaFuncSetAttribute(chol_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    if (s <= 0 || s > CholLeaf<T>::max_s) return -2;
+    chol_leaf_kernel<T><<<batch, dim3(32, 16), chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info);
+    return 0;
+}
+
+template int chol_leaf<double>(double *, long long, long long, double *, long long, long long, int, int, int, int *,
+                               cudaStream_t);
+template int chol_leaf<float>(float *, long long, long long, float *, long long, long long, int, int, int, int *,
+                              cudaStream_t);
 
 // --------------------------------------------------------------------------
 // HBM passes with 32x32 shared-memory tiles

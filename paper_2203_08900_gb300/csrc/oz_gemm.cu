@@ -40,6 +40,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cmath>
 
 #include "pssd_internal.h"
 
@@ -72,6 +73,7 @@ struct OzArgs {
     double *C; long long ldc, sC;
     const double *Cin; long long ldcin, sCin;
     double alpha, beta;
+    int alpha_e, alpha_e_valid, alpha_neg;   // alpha = (-1)^neg 2^alpha_e when valid
     int *err;
 };
 
@@ -162,6 +164,22 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x)
     float s2 = __fadd_rn(s, l);              // Fast2Sum renormalisation (|s| >= |l|)
     lo = __fsub_rn(l, __fsub_rn(s2, s));
     hi = s2;
+}
+
+// f 2^E as a double from the bit fields (exact); false when f is not a normal
+// float or the result leaves the normal double range
+__device__ __forceinline__ bool f2d_scaled(float f, int E, double &out)
+{
+    const uint32_t u = __float_as_uint(f);
+    if ((u & 0x7FFFFFFFu) == 0) { out = 0.0; return true; }
+    const int ef = (int)((u >> 23) & 0xFF);
+    if (ef == 0 || ef == 255) return false;
+    const int ed = ef - 127 + 1023 + E;
+    if (ed < 1 || ed > 2046) return false;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    out = __longlong_as_double((long long)b);
+    return true;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
@@ -296,6 +314,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
                 for (int q = 0; q < OZ_BN; ++q) df_add(hi[q], lo[q], __fmul_rn(__uint_as_float(r[q]), sc));
             }
+
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(b_free);
         }
@@ -303,16 +322,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         if (ok && !s_abort && i < g.m) {
             double *C = g.C + (long long)z * g.sC;
             const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
-            const int ei = g.ea[z * g.m_pad + i];
+            // exponents of all-zero rows / columns are very negative; their pairs are 0
+            const int ei = max(g.ea[z * g.m_pad + i], -4000) + g.alpha_e;
+            const double *eCin = Cin ? Cin + (long long)i * g.ldcin : nullptr;
+            double *eC = C + (long long)i * g.ldc;
 #pragma unroll
             for (int q = 0; q < OZ_BN; ++q) {
                 const int j = j0 + q;
                 if (j >= g.n || (g.lowerC && j > i)) continue;
-                double v = ((double)hi[q] + (double)lo[q]);
-                v = ldexp(v, ei + g.eb[z * g.n_pad + j]);
-                double o = g.alpha * v;
-                if (g.beta != 0.0) o += g.beta * Cin[(long long)i * g.ldcin + j];
-                C[(long long)i * g.ldc + j] = o;
+                const int E = ei + max(g.eb[z * g.n_pad + j], -4000);
+                double dh, dl, v;
+                if (f2d_scaled(hi[q], E, dh) && f2d_scaled(lo[q], E, dl)) {
+                    v = dh + dl;                  // a power-of-two alpha is folded into E and the sign
+                    if (g.alpha_neg) v = -v;
+                    if (!g.alpha_e_valid) v *= g.alpha;
+                } else {
+                    v = ldexp((double)hi[q] + (double)lo[q], E - g.alpha_e) * g.alpha;
+                }
+                if (g.beta != 0.0) v = fma(g.beta, eCin[j], v);
+                eC[j] = v;
             }
         }
     }
@@ -490,6 +518,13 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     a.C = (double *)g.C; a.ldc = g.ldc; a.sC = g.sC;
     a.Cin = (const double *)g.Cin; a.ldcin = g.ldcin; a.sCin = g.sCin;
     a.alpha = g.alpha; a.beta = g.beta; a.err = err;
+    {
+        int ex = 0;
+        const double fr = std::frexp(std::fabs(g.alpha), &ex);
+        a.alpha_e_valid = (fr == 0.5) ? 1 : 0;            // |alpha| = 2^(ex-1)
+        a.alpha_e = a.alpha_e_valid ? ex - 1 : 0;
+        a.alpha_neg = (a.alpha_e_valid && g.alpha < 0) ? 1 : 0;
+    }
     dim3 grid(((g.n + OZ_BN - 1) / OZ_BN) * ((g.m + OZ_BM - 1) / OZ_BM), 1, g.batch);
     oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(a);
     return 0;

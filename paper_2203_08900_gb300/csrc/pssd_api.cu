@@ -218,8 +218,9 @@ void gemm(pssd_handle h, const GemmArgs &g0)
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
     Mark mk = mark(h);
     if (g.mode == GM_OZ && !h->derr) g.mode = GM_DF;   // (no error flag outside a guarded call)
-    // thin or small products: the slicing passes would dominate; use float pairs
-    if (g.mode == GM_OZ && !h->force_engine && (g.k < 128 || (double)g.m * g.n * g.k * g.batch < 33554432.0))
+    // very thin or tiny products: the slicing passes would dominate; use float pairs
+    // (the slices are FP64-accurate, the float pairs carry ~2^-47 per product)
+    if (g.mode == GM_OZ && !h->force_engine && (g.k < 16 || (double)g.m * g.n * g.k * g.batch < 262144.0))
         g.mode = GM_DF;
     if (g.mode == GM_DF) {
         // split each FP64 operand into compact float pairs once (stream-ordered temporaries)
@@ -294,37 +295,6 @@ void frob_pair(pssd_handle h, const double *X, long long ldx, const double *Y, l
 template <class T>
 T *talloc(pssd_handle h, size_t count) { return (T *)walloc(h, count * sizeof(T)); }
 
-template <class T>
-void potrf(pssd_handle h, T *A, int n, long long lda, long long sA, int batch, T *Rinv, long long ldr,
-           long long sR, T *Dinv, int *dinfo, int info_off = 0)
-{
-    for (int k0 = 0; k0 < n; k0 += PB) {
-        int kb = std::min(PB, n - k0);
-        {
-            Timed t(h, K_POTRF, batch * (kb * (double)kb * kb / 3.0 * 2.0));
-            potrf_diag<T>(A, lda, sA, k0, kb, batch, Dinv, PB * PB, Rinv, ldr, sR, dinfo, info_off, h->stream);
-        }
-        int rest = n - k0 - kb;
-        if (rest <= 0) continue;
-        GemmArgs p;                       // L21 = A21 L11^{-T}
-        p.mode = gm_of<T>();
-        p.m = rest; p.n = kb; p.k = kb; p.batch = batch;
-        p.A = A + (long long)(k0 + kb) * lda + k0; p.lda = lda; p.sA = sA;
-        p.B = Dinv; p.ldb = PB; p.sB = PB * PB; p.tb = 1; p.triB = TRI_UPPER;
-        p.C = A + (long long)(k0 + kb) * lda + k0; p.ldc = lda; p.sC = sA;
-        gemm(h, p);
-        GemmArgs t;                       // A22 -= L21 L21^T (lower)
-        t.mode = gm_of<T>();
-        t.m = rest; t.n = rest; t.k = kb; t.batch = batch;
-        t.A = p.C; t.lda = lda; t.sA = sA;
-        t.B = p.C; t.ldb = lda; t.sB = sA; t.tb = 1;
-        t.Cin = A + (long long)(k0 + kb) * lda + (k0 + kb); t.ldcin = lda; t.sCin = sA;
-        t.C = A + (long long)(k0 + kb) * lda + (k0 + kb); t.ldc = lda; t.sC = sA;
-        t.alpha = -1.0; t.beta = 1.0; t.lowerC = 1;
-        gemm(h, t);
-    }
-}
-
 int check_info(pssd_handle h, const int *dinfo, int batch, int *fail_index)
 {
     std::vector<int> hi(batch);
@@ -334,53 +304,27 @@ int check_info(pssd_handle h, const int *dinfo, int batch, int *fail_index)
     return 0;
 }
 
-// recursive triangular inverse; diagonal PB-blocks must already hold their inverses
-template <class T>
-void trtri_rec(pssd_handle h, const T *L, T *Rinv, int off, int s, long long ld, long long sL, long long sR,
-               int batch, T *tmp, long long sT)
-{
-    if (s <= PB) return;
-    int nbk = (s + PB - 1) / PB;
-    int hh = ((nbk + 1) / 2) * PB;
-    trtri_rec<T>(h, L, Rinv, off, hh, ld, sL, sR, batch, tmp, sT);
-    trtri_rec<T>(h, L, Rinv, off + hh, s - hh, ld, sL, sR, batch, tmp, sT);
-    GemmArgs a;   // T = L21 * inv(L11)
-    a.mode = gm_of<T>();
-    a.m = s - hh; a.n = hh; a.k = hh; a.batch = batch;
-    a.A = L + (long long)(off + hh) * ld + off; a.lda = ld; a.sA = sL;
-    a.B = Rinv + (long long)off * ld + off; a.ldb = ld; a.sB = sR; a.triB = TRI_LOWER;
-    a.C = tmp; a.ldc = hh; a.sC = sT;
-    gemm(h, a);
-    GemmArgs b;   // inv21 = -inv(L22) T
-    b.mode = gm_of<T>();
-    b.m = s - hh; b.n = hh; b.k = s - hh; b.batch = batch;
-    b.A = Rinv + (long long)(off + hh) * ld + (off + hh); b.lda = ld; b.sA = sR; b.triA = TRI_LOWER;
-    b.B = tmp; b.ldb = hh; b.sB = sT;
-    b.C = Rinv + (long long)(off + hh) * ld + off; b.ldc = ld; b.sC = sR;
-    b.alpha = -1.0;
-    gemm(h, b);
-}
-
 // Recursive Cholesky with inverse, in place on the diagonal block (off, s):
 //   L11 = chol(A11), L21 = A21 L11^{-T}, A22 <- A22 - L21 L21^T, L22 = chol(A22),
 //   L^{-1}_21 = -L22^{-1} L21 L11^{-1};
 // the work sits in GEMMs of order s/2, which the tensor-core engines take;
-// blocks of at most CHOL_LEAF use the right-looking blocked factorisation.
-constexpr int CHOL_LEAF = 256;
-
+// diagonal blocks of at most CholLeaf<T>::max_s are factorised and inverted
+// by one fused kernel (one CTA per batch matrix).
 template <class T>
 void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, int batch, T *Rinv, long long sR,
-              T *Dinv, int *dinfo, T *tmp, long long sT)
+              int *dinfo, T *tmp, long long sT)
 {
-    if (s <= CHOL_LEAF) {
-        potrf<T>(h, A + (long long)off * lda + off, s, lda, sA, batch,
-                 Rinv ? Rinv + (long long)off * lda + off : nullptr, lda, sR, Dinv, dinfo, off);
-        if (Rinv) trtri_rec<T>(h, A, Rinv, off, s, lda, sA, sR, batch, tmp, sT);
+    if (s <= CholLeaf<T>::max_s) {
+        Timed t(h, K_POTRF, batch * (double)s * s * s);
+        if (chol_leaf<T>(A, lda, sA, Rinv, lda, sR, off, s, batch, dinfo, h->stream)) {
+            h->last_err = "Cholesky leaf launch configuration failed";
+            throw Fail{PSSD_ERR_CUDA};
+        }
         return;
     }
     const int nbk = (s + PB - 1) / PB;
     const int hh = ((nbk + 1) / 2) * PB, q = s - hh;
-    chol_rec<T>(h, A, off, hh, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, sT);
+    chol_rec<T>(h, A, off, hh, lda, sA, batch, Rinv, sR, dinfo, tmp, sT);
     T *A21 = A + (long long)(off + hh) * lda + off;
     T *A22 = A + (long long)(off + hh) * lda + (off + hh);
     {   // L21 = A21 L11^{-T} into tmp (the product reads whole rows of A21), then back
@@ -400,7 +344,7 @@ void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, 
         g.alpha = -1.0; g.beta = 1.0; g.lowerC = 1;
         gemm(h, g);
     }
-    chol_rec<T>(h, A, off + hh, q, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, sT);
+    chol_rec<T>(h, A, off + hh, q, lda, sA, batch, Rinv, sR, dinfo, tmp, sT);
     if (Rinv) {   // L^{-1}_21 = -L22^{-1} (L21 L11^{-1})
         GemmArgs a; a.mode = gm_of<T>(); a.m = q; a.n = hh; a.k = hh; a.batch = batch;
         a.A = A21; a.lda = lda; a.sA = sA;
@@ -422,7 +366,6 @@ int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch,
              int *fail_index)
 {
     Mark mk = mark(h);
-    T *Dinv = talloc<T>(h, (size_t)PB * PB * batch);
     int *dinfo = ialloc(h, batch);
     cuda_check(h, cudaMemsetAsync(dinfo, 0, sizeof(int) * batch, h->stream), "memset");
     size_t tsz = (size_t)((n + 1) / 2 + PB) * ((n + 1) / 2 + PB);
@@ -431,7 +374,7 @@ int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch,
         Rinv = talloc<T>(h, (size_t)lda * n * batch);
         sR = lda * (long long)n;
     }
-    chol_rec<T>(h, A, 0, n, lda, sA, batch, Rinv, sR, Dinv, dinfo, tmp, (long long)tsz);
+    chol_rec<T>(h, A, 0, n, lda, sA, batch, Rinv, sR, dinfo, tmp, (long long)tsz);
     int bad = check_info(h, dinfo, batch, fail_index);
     release(h, mk);
     return bad;

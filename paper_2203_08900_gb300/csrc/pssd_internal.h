@@ -47,14 +47,18 @@ int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
 size_t oz_gemm_workspace_bytes(const GemmArgs &g);
 int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
 
-// Cholesky of the kb x kb (kb <= PB) diagonal block at (k0,k0) of each batch
-// matrix (lower, in place); its triangular inverse goes to Dinv (PB x PB per
-// batch, ld PB) and, if Rinv != nullptr, into the same diagonal block of Rinv.
-// info[z] receives (first failing global pivot + 1) if a pivot is not positive.
-template <class T>   // info[z] = info_off + first failing pivot (block-relative) + 1
-void potrf_diag(T *A, long long lda, long long sA, int k0, int kb, int batch,
-                T *Dinv, long long sD, T *Rinv, long long ldr, long long sR,
-                int *info, int info_off, cudaStream_t s);
+// Cholesky and triangular inverse of the s x s diagonal block at (off, off)
+// of each batch matrix, in one launch: L (lower) in place in A with zeros
+// above the diagonal inside the block, L^{-1} (lower) in the same block of
+// Rinv.  info[z] = (first failing global pivot + 1) if a pivot is not
+// positive or finite (the factorisation then continues with pivot 1).
+// s <= CholLeaf<T>::max_s; returns nonzero on a launch-configuration error.
+template <class T> struct CholLeaf;
+template <> struct CholLeaf<float> { static constexpr int max_s = 128; };
+template <> struct CholLeaf<double> { static constexpr int max_s = 64; };
+template <class T>
+int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long long sR, int off, int s, int batch,
+              int *info, cudaStream_t st);
 
 // Elementwise / HBM passes
 void sym_prepare(const double *H, long long ldh, const double *sig, int n, double *M, long long ldm,
