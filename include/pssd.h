@@ -28,6 +28,8 @@
  *    is invalid (LAPACK style), or one of the positive PSSD_ERR_* codes.  On
  *    error the outputs are unspecified; `info` (if not NULL) is filled as far
  *    as the run got.
+ *  - Orders are limited to 1 <= n <= PSSD_MAX_N (some passes put one matrix
+ *    row per grid row); larger n is rejected as an invalid argument.
  *  - Workspace is allocated by the handle on first use and grown as needed
  *    (cudaMalloc outside any stream capture); pssd_destroy frees it.
  */
@@ -39,6 +41,9 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* largest supported order n (one grid row per matrix row in some passes) */
+#define PSSD_MAX_N 65535
 
 /* status codes */
 #define PSSD_OK 0

@@ -66,6 +66,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64"]
 NOALLOC_MAX_N = 128
+MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
 
 def lib():

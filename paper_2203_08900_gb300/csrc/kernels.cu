@@ -641,20 +641,22 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 
 __global__ void fill_gaussian_kernel(double *X, long long ldx, int m, int n, uint64_t seed)
 {
-    const int i = blockIdx.y;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        uint64_t idx = (uint64_t)i * (uint64_t)n + (uint64_t)j;
-        uint64_t h1 = splitmix64(seed ^ (idx * 2 + 1)), h2 = splitmix64(seed + idx * 2 + 0x1234567ull);
-        double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-        double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
-        X[(long long)i * ldx + j] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-    }
+    for (int i = blockIdx.y; i < m; i += gridDim.y)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+            uint64_t idx = (uint64_t)i * (uint64_t)n + (uint64_t)j;
+            uint64_t h1 = splitmix64(seed ^ (idx * 2 + 1)), h2 = splitmix64(seed + idx * 2 + 0x1234567ull);
+            double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+            double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+            X[(long long)i * ldx + j] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        }
 }
 
 void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    fill_gaussian_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, seed);
+    const int gy = m < 65535 ? m : 65535;
+    if (gy <= 0) return;
+    fill_gaussian_kernel<<<dim3(gx, gy), 256, 0, s>>>(X, ldx, m, n, seed);
 }
 
 __global__ void trace_kernel(const double *X, long long ldx, int n, double *out)

@@ -524,6 +524,35 @@ int zolo_sign_fp32(pssd_handle h, float *X0, int m, double ell, double tau32, do
 // Newton-Schulz refinement of a symmetric Y ~ sign(.):  Y <- Y + Y (I - Y^2) / 2
 // (the FP64 half of the mixed path; contractions in the handle's FP64 mode).
 // Stops when ||I - Y^2||_F <= tol or stops decreasing.
+// ||I - Y^2||_F estimated from a Gaussian probe: for Omega (m x s) with
+// independent N(0,1) entries E ||(I - Y^2) Omega||_F^2 = s ||I - Y^2||_F^2.
+double ns_probe(pssd_handle h, const double *Y, long long ldy, int m, uint64_t seed)
+{
+    constexpr int s = 16;
+    Mark mk = mark(h);
+    double *Om = dalloc(h, (size_t)m * s), *T1 = dalloc(h, (size_t)m * s), *Z = dalloc(h, (size_t)m * s);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, s));
+    {
+        Timed t(h, K_HBM, 0);
+        fill_gaussian(Om, s, m, s, seed, h->stream);
+    }
+    GemmArgs a; a.m = m; a.n = s; a.k = m; a.A = Y; a.lda = ldy; a.B = Om; a.ldb = s; a.C = T1; a.ldc = s;
+    gemm(h, a);                                                          // T1 = Y Omega
+    GemmArgs b; b.m = m; b.n = s; b.k = m; b.A = Y; b.lda = ldy; b.B = T1; b.ldb = s;
+    b.Cin = Om; b.ldcin = s; b.beta = -1.0; b.C = Z; b.ldc = s;
+    gemm(h, b);                                                          // Z = Y^2 Omega - Omega
+    double d2, z2;
+    frob_pair(h, nullptr, s, Z, s, m, s, part, &d2, &z2);
+    release(h, mk);
+    return std::sqrt(z2 / s);
+}
+
+// Newton-Schulz refinement Y <- Y + Y (I - Y^2)/2 until ||I - Y^2||_F <= tol.
+// E = I - Y^2 commutes with Y, so one step maps E to (3/4) E^2 + (1/4) E^3 and
+// ||E_new||_F <= (3/4) r^2 + (1/4) r^3 for r = ||E||_F (up to rounding).  When
+// that prediction is far below tol, the residual after the step is checked by
+// ns_probe instead of forming I - Y^2 (the full product is formed if the probe
+// does not confirm it).
 int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *resid_out, int *its_out,
               bool symmetric = true, long long ldy = 0)
 {
@@ -532,11 +561,16 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
     if (ldy == 0) ldy = ld;
     double *G = dalloc(h, msz), *Yn = dalloc(h, msz);
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
-    double prev = INFINITY, res = INFINITY;
+    double prev = INFINITY, res = INFINITY, predicted = INFINITY;
     int it = 0;
     double *cur = Y;
     long long ldc = ldy;
     for (; it <= max_it; ++it) {
+        if (it > 0 && predicted <= tol / 16) {
+            const double est = ns_probe(h, cur, ldc, m, 0x9e3779b97f4a7c15ull + (uint64_t)it);
+            if (!std::isfinite(est)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+            if (est <= tol / 2) { res = est; break; }
+        }
         GemmArgs g; g.m = g.n = g.k = m; g.A = cur; g.lda = ldc; g.B = cur; g.ldb = ldc; g.C = G; g.ldc = ld;
         g.alpha = -1.0; g.lowerC = symmetric ? 1 : 0;                   // G = -Y^2
         gemm(h, g);
@@ -551,6 +585,7 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
         if (!std::isfinite(res)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (res <= tol || res > 0.5 * prev || it == max_it) break;
         prev = res;
+        predicted = 0.75 * res * res + 0.25 * res * res * res;
         GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ldc; u.B = G; u.ldb = ld; u.Cin = cur; u.ldcin = ldc;
         u.C = Yn; u.ldc = ld; u.alpha = 0.5; u.beta = 1.0; u.lowerC = symmetric ? 1 : 0;   // Y + Y (I - Y^2)/2
         gemm(h, u);
@@ -780,7 +815,7 @@ struct Front {
 
 int validate(int n, const signed char *sigma, const double *H, int ldh)
 {
-    if (n < 1) return -2;
+    if (n < 1 || n > PSSD_MAX_N) return -2;
     if (!sigma && (n % 2)) return -3;
     if (sigma)
         for (int i = 0; i < n; ++i) if (sigma[i] != 1 && sigma[i] != -1) return -3;

@@ -175,3 +175,17 @@ def test_errors_are_status_codes(P):
     # the context is still usable afterwards
     S, _ = P.sign(_dev(H))
     assert torch.isfinite(S).all()
+
+
+def test_order_limit_is_an_argument_error(P):
+    """n above PSSD_MAX_N is rejected by argument validation (-2) before any
+    device work; the pointers are never dereferenced."""
+    import ctypes
+    h = P.Handle()
+    H = torch.zeros(2, 2, dtype=torch.float64, device="cuda")
+    S = torch.empty_like(H)
+    o = P._opts()
+    info = P.Info()
+    st = P.lib().pssd_sign(h._h, P.MAX_N + 1, None, ctypes.c_void_p(H.data_ptr()), P.MAX_N + 1,
+                           ctypes.c_void_p(S.data_ptr()), P.MAX_N + 1, ctypes.byref(o), ctypes.byref(info))
+    assert st == -2
