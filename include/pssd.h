@@ -260,6 +260,33 @@ int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch
                        long long ldcin, long long sCin, double *C, long long ldc, long long sC,
                        const double *kscale);
 
+/* ---------------------------------------------------------------------------
+ * Profiling hooks (no counterpart in the paper; for measurement only).
+ * With profiling on, each library kernel region on the handle's stream is
+ * bracketed by CUDA events and its time, launch count and algorithmic FLOPs
+ * are added to one of the kinds below when the call returns.
+ * ------------------------------------------------------------------------- */
+#define PSSD_KIND_DGEMM 0       /* FP64 DFMA contraction */
+#define PSSD_KIND_CHOL_LEAF 1   /* fused Cholesky + inverse of a diagonal block */
+#define PSSD_KIND_HBM 2         /* elementwise / copy / reduction passes */
+#define PSSD_KIND_GEMV 3        /* matrix-vector products (bound estimation) */
+#define PSSD_KIND_JACOBI 4      /* Jacobi leaf eigensolver */
+#define PSSD_KIND_SGEMM 5       /* FP32 FFMA contraction */
+#define PSSD_KIND_DFGEMM 6      /* FP64 contraction in float pairs */
+#define PSSD_KIND_TCGEMM 7      /* FP32 contraction, 3xTF32 on tcgen05 */
+#define PSSD_KIND_OZGEMM 8      /* FP64 contraction, integer slices on tcgen05 (incl. slicing passes) */
+#define PSSD_NKIND 9
+/* on != 0 enables event timing on the handle (adds two events per region). */
+int pssd_profile_enable(pssd_handle h, int on);
+/* Zero the per-kind totals of the handle. */
+int pssd_profile_reset(pssd_handle h);
+/* Totals of one kind since the last reset: milliseconds, timed regions,
+ * algorithmic FLOPs (any pointer may be NULL).  -2 if kind is out of range. */
+int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops);
+/* Number of kernels the library has launched in this process (all handles;
+ * one count per launch).  -1 if h is NULL. */
+long long pssd_launch_count(pssd_handle h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,9 @@
 
 namespace pssd {
 
+std::atomic<long long> g_launches{0};
+
+
 // --------------------------------------------------------------------------
 // GEMM with triangular operands, lower-only output and inner scaling, in
 // three arithmetic modes:
@@ -199,14 +202,15 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s)
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return;
     dim3 grid((g.n + GBN - 1) / GBN, (g.m + GBM - 1) / GBM, g.batch);
     switch (g.mode) {
-    case GM_F32: gemm_kernel<GM_F32><<<grid, 256, 0, s>>>(g); break;
-    case GM_DF: gemm_kernel<GM_DF><<<grid, 256, 0, s>>>(g); break;
-    default: gemm_kernel<GM_F64><<<grid, 256, 0, s>>>(g); break;
+    case GM_F32: gemm_kernel<GM_F32><<<grid, 256, 0, s>>>(g); count_launch(); break;
+    case GM_DF: gemm_kernel<GM_DF><<<grid, 256, 0, s>>>(g); count_launch(); break;
+    default: gemm_kernel<GM_F64><<<grid, 256, 0, s>>>(g); count_launch(); break;
     }
 }
 
 // --------------------------------------------------------------------------
-// Cholesky of one diagonal block (<= 64) and its triangular inverse
+// Cholesky of one diagonal block (<= 128 in FP32, <= 64 in FP64) and its
+// triangular inverse
 // --------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(512) chol_leaf_kernel(T *A, long long lda, long long sA, T *Rinv, long long ldr,
@@ -290,7 +294,7 @@ int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long lo
         attr = true;
     }
     if (s <= 0 || s > CholLeaf<T>::max_s) return -2;
-    chol_leaf_kernel<T><<<batch, dim3(32, 16), chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info);
+    chol_leaf_kernel<T><<<batch, dim3(32, 16), chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info); count_launch();
     return 0;
 }
 
@@ -356,7 +360,7 @@ void sym_prepare(const double *H, long long ldh, const double *sig, int n, doubl
                  double *partials, cudaStream_t s)
 {
     int t = (n + TT - 1) / TT;
-    sym_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(H, ldh, sig, n, M, ldm, partials);
+    sym_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(H, ldh, sig, n, M, ldm, partials); count_launch();
 }
 
 // S <- (S + Sigma S^T Sigma) / 2: the nearest Sigma-symmetric matrix (Sigma S symmetric), in
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(256) j_resym_kernel(double *S, long long lds, 
 void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s)
 {
     int t = (n + TT - 1) / TT;
-    j_resym_kernel<<<dim3(t, t), 256, 0, s>>>(S, lds, sig, n);
+    j_resym_kernel<<<dim3(t, t), 256, 0, s>>>(S, lds, sig, n); count_launch();
 }
 
 // Daleckii-Krein weights of the sign function:
@@ -411,7 +415,7 @@ void dk_combine(const double *W, long long ldw, const double *lam, const double 
                 long long ldx, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    dk_combine_kernel<<<dim3(gx, n), 256, 0, s>>>(W, ldw, lam, lambar, n, X, ldx);
+    dk_combine_kernel<<<dim3(gx, n), 256, 0, s>>>(W, ldw, lam, lambar, n, X, ldx); count_launch();
 }
 
 // X[i][j] *= r[i] (row scaling)
@@ -426,7 +430,7 @@ __global__ void scale_rows_kernel(double *X, long long ldx, int m, int n, const 
 void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    scale_rows_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, r);
+    scale_rows_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, r); count_launch();
 }
 
 // (hi, lo) = (fl32(x), fl32(x - hi)) for a batch of rows x cols blocks (source
@@ -449,7 +453,7 @@ void split_pairs(const double *x, long long ld, long long sb, int rows, int cols
                  cudaStream_t s)
 {
     int gx = (cols + 255) / 256; if (gx > 16) gx = 16;
-    split_pairs_kernel<<<dim3(gx, rows, batch), 256, 0, s>>>(x, ld, sb, rows, cols, hi, lo);
+    split_pairs_kernel<<<dim3(gx, rows, batch), 256, 0, s>>>(x, ld, sb, rows, cols, hi, lo); count_launch();
 }
 
 // fixed-order single-block sum (deterministic)
@@ -469,7 +473,7 @@ __global__ void reduce_sum_kernel(const double *x, int count, int stride, double
 
 void reduce_sum(const double *x, int count, double *out, cudaStream_t s)
 {
-    reduce_sum_kernel<<<1, 1024, 0, s>>>(x, count, 1, out);
+    reduce_sum_kernel<<<1, 1024, 0, s>>>(x, count, 1, out); count_launch();
 }
 
 // copy the strictly lower triangle onto the upper one
@@ -496,7 +500,7 @@ template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s)
 {
     int t = (n + TT - 1) / TT;
-    mirror_lower_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, lda, sA, n);
+    mirror_lower_kernel<T><<<dim3(t, t, batch), 256, 0, s>>>(A, lda, sA, n); count_launch();
 }
 template void mirror_lower<double>(double *, long long, long long, int, int, cudaStream_t);
 template void mirror_lower<float>(float *, long long, long long, int, int, cudaStream_t);
@@ -519,7 +523,7 @@ void shift_copy_lower(const T *G, long long ldg, T *Z, long long ldz, long long 
                       int batch, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 8) gx = 8;
-    shift_copy_lower_kernel<T><<<dim3(gx, n, batch), 256, 0, s>>>(G, ldg, Z, ldz, sZ, n, shifts);
+    shift_copy_lower_kernel<T><<<dim3(gx, n, batch), 256, 0, s>>>(G, ldg, Z, ldz, sZ, n, shifts); count_launch();
 }
 template void shift_copy_lower<double>(const double *, long long, double *, long long, long long, int,
                                        const double *, int, cudaStream_t);
@@ -543,7 +547,7 @@ void combine_lower(const T *Zinv, long long ldz, long long sZ, const double *a, 
                    cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 8) gx = 8;
-    combine_lower_kernel<T><<<dim3(gx, n), 256, 0, s>>>(Zinv, ldz, sZ, a, r, n, Tm, ldt);
+    combine_lower_kernel<T><<<dim3(gx, n), 256, 0, s>>>(Zinv, ldz, sZ, a, r, n, Tm, ldt); count_launch();
 }
 template void combine_lower<double>(const double *, long long, long long, const double *, int, int, double *,
                                     long long, cudaStream_t);
@@ -564,7 +568,7 @@ void scale_copy(const TI *X, long long ldx, TO *Y, long long ldy, int m, int n, 
 {
     if (m <= 0 || n <= 0) return;
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    scale_copy_kernel<TI, TO><<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, alpha);
+    scale_copy_kernel<TI, TO><<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, alpha); count_launch();
 }
 template void scale_copy<double, double>(const double *, long long, double *, long long, int, int, double, cudaStream_t);
 template void scale_copy<double, float>(const double *, long long, float *, long long, int, int, double, cudaStream_t);
@@ -586,7 +590,7 @@ __global__ void add_diag_kernel(T *X, long long ldx, int n, double v)
 template <class T>
 void add_diag(T *X, long long ldx, int n, double v, cudaStream_t s)
 {
-    add_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, v);
+    add_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, v); count_launch();
 }
 template void add_diag<double>(double *, long long, int, double, cudaStream_t);
 template void add_diag<float>(float *, long long, int, double, cudaStream_t);
@@ -624,7 +628,7 @@ int frob_blocks(int m, int n) { (void)n; return m < FROB_BLOCKS ? (m > 0 ? m : 1
 template <class T>
 void frob_diff(const T *X, long long ldx, const T *Y, long long ldy, int m, int n, double *partials, cudaStream_t s)
 {
-    frob_diff_kernel<T><<<frob_blocks(m, n), 256, 0, s>>>(X, ldx, Y, ldy, m, n, partials);
+    frob_diff_kernel<T><<<frob_blocks(m, n), 256, 0, s>>>(X, ldx, Y, ldy, m, n, partials); count_launch();
 }
 template void frob_diff<double>(const double *, long long, const double *, long long, int, int, double *, cudaStream_t);
 template void frob_diff<float>(const float *, long long, const float *, long long, int, int, double *, cudaStream_t);
@@ -656,7 +660,7 @@ void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaSt
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
     const int gy = m < 65535 ? m : 65535;
     if (gy <= 0) return;
-    fill_gaussian_kernel<<<dim3(gx, gy), 256, 0, s>>>(X, ldx, m, n, seed);
+    fill_gaussian_kernel<<<dim3(gx, gy), 256, 0, s>>>(X, ldx, m, n, seed); count_launch();
 }
 
 __global__ void trace_kernel(const double *X, long long ldx, int n, double *out)
@@ -675,7 +679,7 @@ __global__ void trace_kernel(const double *X, long long ldx, int n, double *out)
 
 void trace_partial(const double *X, long long ldx, int n, double *out, cudaStream_t s)
 {
-    trace_kernel<<<1, 1024, 0, s>>>(X, ldx, n, out);
+    trace_kernel<<<1, 1024, 0, s>>>(X, ldx, n, out); count_launch();
 }
 
 __global__ void get_diag_kernel(const double *X, long long ldx, int n, double *d)
@@ -686,7 +690,7 @@ __global__ void get_diag_kernel(const double *X, long long ldx, int n, double *d
 
 void get_diag(const double *X, long long ldx, int n, double *d, cudaStream_t s)
 {
-    get_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, d);
+    get_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(X, ldx, n, d); count_launch();
 }
 
 // max over rows of sum_j |X[i][j]| (the infinity norm, an upper bound on
@@ -717,8 +721,8 @@ __global__ void reduce_max_kernel(const double *x, int n, double *out)
 
 void row_abs_sum_max(const double *X, long long ldx, int n, double *tmp, double *out, cudaStream_t s)
 {
-    row_abs_sums_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(X, ldx, n, tmp);
-    reduce_max_kernel<<<1, 1024, 0, s>>>(tmp, n, out);
+    row_abs_sums_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(X, ldx, n, tmp); count_launch();
+    reduce_max_kernel<<<1, 1024, 0, s>>>(tmp, n, out); count_launch();
 }
 
 // y = op(A) x for square n, op(A) optionally triangular (masked)
@@ -769,10 +773,10 @@ void gemv(const double *A, long long lda, int ta, int tri, int n, const double *
           cudaStream_t s)
 {
     if (ta == 0) {
-        gemv_n_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, tri, n, x, y);
+        gemv_n_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(A, lda, tri, n, x, y); count_launch();
     } else {
-        gemv_t_partial_kernel<<<dim3((n + 127) / 128, GEMV_CHUNKS), 128, 0, s>>>(A, lda, tri, n, x, tmp);
-        gemv_t_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, n, y);
+        gemv_t_partial_kernel<<<dim3((n + 127) / 128, GEMV_CHUNKS), 128, 0, s>>>(A, lda, tri, n, x, tmp); count_launch();
+        gemv_t_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, n, y); count_launch();
     }
 }
 
@@ -795,7 +799,7 @@ __global__ void normalize_kernel(double *y, double *x, int n, double *norm_out)
 
 void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s)
 {
-    normalize_kernel<<<1, 1024, 0, s>>>(y, x, n, norm_out);
+    normalize_kernel<<<1, 1024, 0, s>>>(y, x, n, norm_out); count_launch();
 }
 
 __global__ void dot_kernel(const double *x, const double *y, int n, double *out)
@@ -814,7 +818,7 @@ __global__ void dot_kernel(const double *x, const double *y, int n, double *out)
 
 void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s)
 {
-    dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out);
+    dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out); count_launch();
 }
 
 __global__ void scale_columns_kernel(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs)
@@ -829,7 +833,7 @@ __global__ void scale_columns_kernel(double *X, long long ldx, int m, int n, con
 void scale_columns(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs, cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    scale_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, d, use_sqrt_abs);
+    scale_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, m, n, d, use_sqrt_abs); count_launch();
 }
 
 // make the largest-magnitude entry of each column positive (ties: lowest row)
@@ -848,7 +852,7 @@ __global__ void sign_fix_columns_kernel(double *X, long long ldx, int m, int n)
 
 void sign_fix_columns(double *X, long long ldx, int m, int n, cudaStream_t s)
 {
-    sign_fix_columns_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, ldx, m, n);
+    sign_fix_columns_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, ldx, m, n); count_launch();
 }
 
 __global__ void gather_columns_kernel(const double *X, long long ldx, double *Y, long long ldy, int m, int n,
@@ -863,7 +867,7 @@ void gather_columns(const double *X, long long ldx, double *Y, long long ldy, in
                     cudaStream_t s)
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
-    gather_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, perm);
+    gather_columns_kernel<<<dim3(gx, m), 256, 0, s>>>(X, ldx, Y, ldy, m, n, perm); count_launch();
 }
 
 // --------------------------------------------------------------------------
@@ -969,7 +973,7 @@ __global__ void __launch_bounds__(256) jacobi_leaf_kernel(double *Ag, long long 
 void jacobi_leaf(double *A, long long lda, int m, double *W, long long ldw, double *w, int *sweeps_out,
                  cudaStream_t s)
 {
-    jacobi_leaf_kernel<<<1, 256, 0, s>>>(A, lda, m, W, ldw, w, sweeps_out);
+    jacobi_leaf_kernel<<<1, 256, 0, s>>>(A, lda, m, W, ldw, w, sweeps_out); count_launch();
 }
 
 }  // namespace pssd

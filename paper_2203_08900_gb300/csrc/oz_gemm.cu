@@ -495,20 +495,20 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     int *ea = (int *)(sb + (size_t)OZ_S * np * kp * g.batch);
     int *eb = ea + (size_t)mp * g.batch;
     const int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
-    fill_int_kernel<<<64, 256, 0, s>>>(ea, (long long)(mp + np) * g.batch, INT_MIN / 2);
+    fill_int_kernel<<<64, 256, 0, s>>>(ea, (long long)(mp + np) * g.batch, INT_MIN / 2); count_launch();
     {
         dim3 gr((kp + 31) / 32, (mp + 31) / 32, g.batch);
         oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                         (const double *)g.kscale, mp, ea);
+                                         (const double *)g.kscale, mp, ea); count_launch();
         oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                           (const double *)g.kscale, mp, kp, OZ_BM, ea, sa);
+                                           (const double *)g.kscale, mp, kp, OZ_BM, ea, sa); count_launch();
     }
     {
         dim3 gr((kp + 31) / 32, (np + 31) / 32, g.batch);
         oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                         np, eb);
+                                         np, eb); count_launch();
         oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                           np, kp, OZ_BN, eb, sb);
+                                           np, kp, OZ_BN, eb, sb); count_launch();
     }
     OzArgs a;
     a.sa = sa; a.sb = sb; a.kblocks = kp / 16;
@@ -526,7 +526,7 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
         a.alpha_neg = (a.alpha_e_valid && g.alpha < 0) ? 1 : 0;
     }
     dim3 grid(((g.n + OZ_BN - 1) / OZ_BN) * ((g.m + OZ_BM - 1) / OZ_BM), 1, g.batch);
-    oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(a);
+    oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(a); count_launch();
     return 0;
 }
 

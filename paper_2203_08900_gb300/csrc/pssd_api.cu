@@ -56,7 +56,6 @@ struct pssd_handle_s {
     std::vector<cudaEvent_t> free_events;
     double prof_ms[16] = {0}, prof_flops[16] = {0};
     long long prof_count[16] = {0};
-    long long launches = 0;
     int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
     std::vector<pssd_handle_s *> workers;   // pssd_eig_batched: one handle (own stream, workspace) per worker
     int *derr = nullptr;    // device error flag of the current call (bounded waits in the tensor-core kernel)
@@ -131,6 +130,11 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // ---------------------------------------------------------------------------
 enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
             K_OZGEMM = 8, K_NKIND = 9 };
+static_assert(K_DGEMM == PSSD_KIND_DGEMM && K_POTRF == PSSD_KIND_CHOL_LEAF && K_HBM == PSSD_KIND_HBM &&
+                  K_GEMV == PSSD_KIND_GEMV && K_JACOBI == PSSD_KIND_JACOBI && K_SGEMM == PSSD_KIND_SGEMM &&
+                  K_DFGEMM == PSSD_KIND_DFGEMM && K_TCGEMM == PSSD_KIND_TCGEMM && K_OZGEMM == PSSD_KIND_OZGEMM &&
+                  K_NKIND == PSSD_NKIND,
+              "profiling kinds match the public header");
 
 cudaEvent_t get_event(pssd_handle h)
 {
@@ -142,9 +146,8 @@ cudaEvent_t get_event(pssd_handle h)
 
 struct Timed {
     pssd_handle h; int kind; double flops; cudaEvent_t a = nullptr, b = nullptr;
-    Timed(pssd_handle h_, int kind_, double flops_, int nlaunch = 1) : h(h_), kind(kind_), flops(flops_)
+    Timed(pssd_handle h_, int kind_, double flops_, int = 1) : h(h_), kind(kind_), flops(flops_)
     {
-        h->launches += nlaunch;
         if (h->prof) { a = get_event(h); b = get_event(h); cudaEventRecord(a, h->stream); }
     }
     ~Timed()
@@ -1307,7 +1310,6 @@ int pssd_profile_reset(pssd_handle h)
 {
     if (!h) return -1;
     for (int i = 0; i < 16; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_count[i] = 0; }
-    h->launches = 0;
     return PSSD_OK;
 }
 
@@ -1321,7 +1323,8 @@ int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *laun
     return PSSD_OK;
 }
 
-long long pssd_launch_count(pssd_handle h) { return h ? h->launches : -1; }
+// process-wide number of kernels the library has launched (all handles)
+long long pssd_launch_count(pssd_handle h) { return h ? g_launches.load() : -1; }
 
 }  // extern "C"
 
@@ -1389,7 +1392,6 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
         if (st == PSSD_OK) st = PSSD_ERR_NOALLOC_TOO_LARGE;
     }
     local.chunks.clear();   // the scratch array is not owned by the local handle
-    h->launches += local.launches;
     if (st == PSSD_ERR_CUDA) h->last_err = local.last_err;
     return st;
 }
@@ -1529,8 +1531,6 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
             cuda_check(h, cudaEventRecord(done, h->workers[w]->stream), "cudaEventRecord");
             cuda_check(h, cudaStreamWaitEvent(h->stream, done, 0), "cudaStreamWaitEvent");
             cudaEventDestroy(done);
-            h->launches += h->workers[w]->launches;
-            h->workers[w]->launches = 0;
         }
         cudaEventDestroy(start);
         for (int i = 0; i < count; ++i)

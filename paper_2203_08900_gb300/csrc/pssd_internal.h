@@ -4,12 +4,19 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace pssd {
+
+// process-wide count of kernels launched by the library (one increment per
+// launch statement, after the launch)
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2, GM_OZ = 3 };
 
-// order of the diagonal blocks of the blocked Cholesky / triangular inverse
+// granularity of the recursive Cholesky's splits
 constexpr int PB = 32;
 
 // C[z] = alpha * op(A[z]) * diag(kscale) * op(B[z]) + beta * Cin[z]

@@ -368,13 +368,13 @@ int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     {   // A: rows i of op(A), K-major
         dim3 grid((kp + 31) / 32, (mp + 31) / 32, g.batch);
         tf32_split_kernel<<<grid, 256, 0, s>>>((const float *)g.A, g.lda, g.sA, g.ta, g.m, g.k, kp, mp, g.triA,
-                                               (const float *)g.kscale, ah, al);
+                                               (const float *)g.kscale, ah, al); count_launch();
     }
     {   // B: rows j of op(B)^T, K-major (op(B)[p][j] = B[p][j] or B[j][p])
         int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
         dim3 grid((kp + 31) / 32, (np + 31) / 32, g.batch);
         tf32_split_kernel<<<grid, 256, 0, s>>>((const float *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, kp, np, triB,
-                                               nullptr, bh, bl);
+                                               nullptr, bh, bl); count_launch();
     }
     TcArgs a;
     if (!make_map(&a.ta_hi, ah, (long long)mp * g.batch, kp) || !make_map(&a.ta_lo, al, (long long)mp * g.batch, kp) ||
@@ -387,7 +387,7 @@ int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     a.alpha = (float)g.alpha; a.beta = (float)g.beta;
     a.err = err;
     dim3 grid((g.n + TC_BN - 1) / TC_BN, (g.m + TC_BM - 1) / TC_BM, g.batch);
-    tc_gemm_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(a);
+    tc_gemm_kernel<<<grid, 128, TC_SMEM_BYTES, s>>>(a); count_launch();
     return 0;
 }
 
