@@ -26,14 +26,15 @@
 //    C = alpha 2^{e_i + f_j} (hi + lo) + beta Cin in FP64.
 // Products with a + b > S + 1 (36 of 64 kept) are dropped: below 2^-63 relative.
 //
-// Kernel layout: one CTA of 6 warps per 128 x 64 output tile, warp-specialised:
-// warp 4 streams the 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles
+// Kernel layout: one CTA of 18 warps per 128 x 64 output tile, warp-specialised:
+// warp 16 streams the 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles
 // (64 x 16) of one k block, stored pre-tiled and pre-swizzled (32-byte swizzle)
-// by the slicing pass, as two contiguous bulk copies into a 4-stage mbarrier ring; warp 5 issues 12
+// by the slicing pass, as two contiguous bulk copies into a 4-stage mbarrier ring; warp 17 issues 12
 // tcgen05.mma kind::f16 (M=128, N=64..256, K=16) per stage, which cover the 36
 // slice products, into 8 accumulators of 64 TMEM columns and frees each stage
-// with tcgen05.commit; warps 0-3 (TMEM lanes 0-127) flush the accumulators
-// every 512 terms while the producer keeps
+// with tcgen05.commit; warps 0-15 flush the accumulators every 512 terms
+// (warp w reads TMEM lanes 32 (w % 4) .. and 16 columns per level, so four
+// warps per SM sub-partition hide the TwoSum latency) while the producer keeps
 // prefetching, then signal the MMA warp that the accumulators are free.
 // Every mbarrier wait is bounded (error flag, TMEM freed, return).
 #include <cuda_bf16.h>
@@ -59,7 +60,10 @@ constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 48 KB
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;
 constexpr int OZ_TMEM_COLS = 512;
-constexpr int OZ_THREADS = 192;            // warps 0-3 flush, warp 4 TMA producer, warp 5 MMA issuer
+constexpr int OZ_FLUSH_WARPS = 16;         // warp w: TMEM lanes 32 (w % 4) .., columns 16 (w / 4) ..
+constexpr int OZ_FCOLS = OZ_BN / (OZ_FLUSH_WARPS / 4);   // 16 output columns per flush thread
+constexpr int OZ_PRODUCER_WARP = OZ_FLUSH_WARPS, OZ_MMA_WARP = OZ_FLUSH_WARPS + 1;
+constexpr int OZ_THREADS = 32 * (OZ_FLUSH_WARPS + 2);
 constexpr int OZ_GROUP_M = 8;              // row blocks per group of the tile order
 
 struct OzArgs {
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             mbar_init(b_empty + 8 * s, 1);
         }
         mbar_init(b_done, 1);
-        mbar_init(b_free, 128);
+        mbar_init(b_free, 32 * OZ_FLUSH_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -240,8 +244,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
-        // ---------------- TMA producer ----------------
+    if (warp == OZ_PRODUCER_WARP) {
+        // ---------------- bulk-copy producer ----------------
         if (lane == 0) {
             const __nv_bfloat16 *srca = g.sa + (((long long)z * (g.m_pad / OZ_BM) + tm) * g.kblocks + kb0) *
                                                    (OZ_S * OZ_BM * OZ_BK);
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                           b_full + 8 * s);
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == OZ_MMA_WARP) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             for (int c = 0; c < nchunks && !s_abort; ++c) {
@@ -295,10 +299,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             }
         }
     } else {
-        // ---------------- flush warps 0-3 (TMEM lanes 32w .. 32w+31) ----------------
-        float hi[OZ_BN], lo[OZ_BN];
+        // ---------------- flush warps: lanes 32 (w % 4) .., columns c0 .. c0 + 15 ----------------
+        const int quad = warp & 3, c0 = (warp >> 2) * OZ_FCOLS;
+        float hi[OZ_FCOLS], lo[OZ_FCOLS];
 #pragma unroll
-        for (int q = 0; q < OZ_BN; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+        for (int q = 0; q < OZ_FCOLS; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             if (!mbar_wait(b_done, (uint32_t)(c & 1))) { ok = false; atomicExch(g.err, 4); break; }
@@ -306,19 +311,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
             for (int L = 0; L < OZ_LEVELS; ++L) {
                 const float sc = __int_as_float((127 - 7 * (L + 2)) << 23);   // 2^{-7(L+2)}
-                uint32_t r[OZ_BN];
-#pragma unroll
-                for (int c0 = 0; c0 < OZ_BN; c0 += 16)
-                    tmem_ld16_nowait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * OZ_BN + c0), r + c0);
+                uint32_t r[OZ_FCOLS];
+                tmem_ld16_nowait(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_BN + c0), r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < OZ_BN; ++q) df_add(hi[q], lo[q], __fmul_rn(__uint_as_float(r[q]), sc));
+                for (int q = 0; q < OZ_FCOLS; ++q) df_add(hi[q], lo[q], __fmul_rn(__uint_as_float(r[q]), sc));
             }
-
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(b_free);
         }
-        const int i = i0 + warp * 32 + lane;
+        const int i = i0 + quad * 32 + lane;
         if (ok && !s_abort && i < g.m) {
             double *C = g.C + (long long)z * g.sC;
             const double *Cin = g.Cin ? g.Cin + (long long)z * g.sCin : nullptr;
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             const double *eCin = Cin ? Cin + (long long)i * g.ldcin : nullptr;
             double *eC = C + (long long)i * g.ldc;
 #pragma unroll
-            for (int q = 0; q < OZ_BN; ++q) {
-                const int j = j0 + q;
+            for (int q = 0; q < OZ_FCOLS; ++q) {
+                const int j = j0 + c0 + q;
                 if (j >= g.n || (g.lowerC && j > i)) continue;
                 const int E = ei + max(g.eb[z * g.n_pad + j], -4000);
                 double dh, dl, v;
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (s_abort && tid == OZ_THREADS - 64) {   // producer lane: let copies in flight land before exit
+    if (s_abort && tid == 32 * OZ_PRODUCER_WARP) {   // producer lane: let copies in flight land before exit
         for (int q = 0; q < min(nkb, OZ_STAGES); ++q) mbar_wait(b_full + 8 * (q % OZ_STAGES), 0u);
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
