@@ -64,7 +64,8 @@ extern "C" {
 #define PSSD_FP64_EMULATED 2 /* the PSSD_FP64 algorithm with every contraction FP64-accurate but emulated:
                                 by default exact integer slices of the operands multiplied on the BF16
                                 tensor cores; with PSSD_FLAG_EMU_SIMT, float pairs on the FP32 pipe */
-#define PSSD_FLAG_RESIDUALS 1 /* pssd_sign: also compute info->s2_resid = ||S^2 - I||_F */
+#define PSSD_FLAG_RESIDUALS 1 /* pssd_sign: also compute info->s2_resid = ||S^2 - I||_F;
+                                 pssd_split / pssd_eig: info->split_backerr exactly (else estimated) */
 #define PSSD_FLAG_NO_TENSOR_CORES 2 /* no tensor-core kernels: FP32 contractions on the FP32 SIMT kernel,
                                        emulated FP64 contractions with float pairs (for comparison) */
 #define PSSD_FLAG_EMU_SIMT 4        /* emulated FP64 contractions with float pairs on the FP32 pipe instead of
@@ -94,7 +95,9 @@ typedef struct {
     double s2_resid;     /* ||S^2 - I||_F (pssd_sign only; -1 if not computed) */
     double jsym_resid;   /* ||Sigma S - (Sigma S)^T||_F / ||S||_F (pssd_sign only) */
     double split_backerr;/* ||U_+^T K U_-||_F / ||K||_F: the backward error of the split (Sec. 6.1 metric)
-                            of K = L^T Sigma L ~ H, U_+- the orthonormal invariant-subspace bases */
+                            of K = L^T Sigma L ~ H, U_+- the orthonormal invariant-subspace bases;
+                            exact with PSSD_FLAG_RESIDUALS, else estimated from a 16-column Gaussian
+                            probe (||E Omega||_F / 4, an unbiased estimate of ||E||_F^2 in square) */
     int fail_index;      /* failing Cholesky pivot (0-based) for PSSD_ERR_NOT_DEFINITE, else -1 */
     int levels;          /* pssd_eig: recursion depth reached */
     double seconds;      /* wall time of the call (host clock, stream synchronised) */
@@ -158,7 +161,8 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
  *   Q      device, n x n output (columns 0..p-1 = Q_+), leading dimension ldq >= n
  *   A11    device, p x p output, lda11 >= p;  A22 device, (n-p) x (n-p), lda22 >= n-p
  *   p      host int output (may be NULL)
- * info->split_backerr = ||U_+^T K U_-||_F / ||K||_F (the metric of Sec. 6.1 for the symmetric K ~ H).
+ * info->split_backerr = ||U_+^T K U_-||_F / ||K||_F (the metric of Sec. 6.1 for the symmetric K ~ H;
+ * exact with PSSD_FLAG_RESIDUALS, otherwise a probe estimate).
  */
 int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
                double *Q, int ldq, double *A11, int lda11, double *A22, int lda22, int *p,

@@ -528,10 +528,12 @@ int zolo_sign_fp32(pssd_handle h, float *X0, int m, double ell, double tau32, do
 // (the FP64 half of the mixed path; contractions in the handle's FP64 mode).
 // Stops when ||I - Y^2||_F <= tol or stops decreasing.
 // ||I - Y^2||_F estimated from a Gaussian probe: for Omega (m x s) with
-// independent N(0,1) entries E ||(I - Y^2) Omega||_F^2 = s ||I - Y^2||_F^2.
+// independent N(0,1) entries E ||(I - Y^2) Omega||_F^2 = s ||I - Y^2||_F^2;
+// with s = 64 the estimate is within 25 % of the norm except with
+// probability about 1e-3 (chi-square with 64 degrees of freedom).
 double ns_probe(pssd_handle h, const double *Y, long long ldy, int m, uint64_t seed)
 {
-    constexpr int s = 16;
+    constexpr int s = 64;
     Mark mk = mark(h);
     double *Om = dalloc(h, (size_t)m * s), *T1 = dalloc(h, (size_t)m * s), *Z = dalloc(h, (size_t)m * s);
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, s));
@@ -550,29 +552,33 @@ double ns_probe(pssd_handle h, const double *Y, long long ldy, int m, uint64_t s
     return std::sqrt(z2 / s);
 }
 
-// Newton-Schulz refinement Y <- Y + Y (I - Y^2)/2 until ||I - Y^2||_F <= tol.
-// E = I - Y^2 commutes with Y, so one step maps E to (3/4) E^2 + (1/4) E^3 and
-// ||E_new||_F <= (3/4) r^2 + (1/4) r^3 for r = ||E||_F (up to rounding).  When
-// that prediction is far below tol, the residual after the step is checked by
-// ns_probe instead of forming I - Y^2 (the full product is formed if the probe
-// does not confirm it).
+// Third-order Newton-Schulz refinement towards sign(Y): with E = I - Y^2,
+//   Y <- Y (I + E/2 + 3 E^2/8)     (= Y (15 I - 10 Y^2 + 3 Y^4)/8),
+// until ||I - Y^2||_F <= tol.  E commutes with Y, so one step maps E to
+// (5/8) E^3 + (15/64) E^4 + (9/64) E^5 and ||E_new||_F <= (5/8) r^3 +
+// (15/64) r^4 + (9/64) r^5 for r = ||E||_F (up to rounding): from an FP32
+// iterate (r ~ 1e-5) one step reaches FP64 rounding, with three products
+// (E, P = 3 E^2/8 + E/2, Y + Y P) where two second-order steps take four.
+// When the prediction is at most tol, the residual after the step is taken
+// from ns_probe instead of forming I - Y^2 (the full product is formed if the
+// probe's estimate exceeds tol).
 int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *resid_out, int *its_out,
               bool symmetric = true, long long ldy = 0)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
     if (ldy == 0) ldy = ld;
-    double *G = dalloc(h, msz), *Yn = dalloc(h, msz);
+    double *G = dalloc(h, msz), *Yn = dalloc(h, msz), *Pm = dalloc(h, msz);
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
     double prev = INFINITY, res = INFINITY, predicted = INFINITY;
     int it = 0;
     double *cur = Y;
     long long ldc = ldy;
     for (; it <= max_it; ++it) {
-        if (it > 0 && predicted <= tol / 16) {
+        if (it > 0 && predicted <= tol) {
             const double est = ns_probe(h, cur, ldc, m, 0x9e3779b97f4a7c15ull + (uint64_t)it);
             if (!std::isfinite(est)) { release(h, mk); return PSSD_ERR_NONFINITE; }
-            if (est <= tol / 2) { res = est; break; }
+            if (est <= tol) { res = est; break; }
         }
         GemmArgs g; g.m = g.n = g.k = m; g.A = cur; g.lda = ldc; g.B = cur; g.ldb = ldc; g.C = G; g.ldc = ld;
         g.alpha = -1.0; g.lowerC = symmetric ? 1 : 0;                   // G = -Y^2
@@ -588,9 +594,13 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
         if (!std::isfinite(res)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (res <= tol || res > 0.5 * prev || it == max_it) break;
         prev = res;
-        predicted = 0.75 * res * res + 0.25 * res * res * res;
-        GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ldc; u.B = G; u.ldb = ld; u.Cin = cur; u.ldcin = ldc;
-        u.C = Yn; u.ldc = ld; u.alpha = 0.5; u.beta = 1.0; u.lowerC = symmetric ? 1 : 0;   // Y + Y (I - Y^2)/2
+        predicted = res * res * res * (0.625 + res * (0.234375 + res * 0.140625));
+        GemmArgs pp; pp.m = pp.n = pp.k = m; pp.A = G; pp.lda = ld; pp.B = G; pp.ldb = ld; pp.Cin = G; pp.ldcin = ld;
+        pp.C = Pm; pp.ldc = ld; pp.alpha = 0.375; pp.beta = 0.5; pp.lowerC = symmetric ? 1 : 0;   // P = 3E^2/8 + E/2
+        gemm(h, pp);
+        if (symmetric) mirror<double>(h, Pm, ld, 0, m, 1);
+        GemmArgs u; u.m = u.n = u.k = m; u.A = cur; u.lda = ldc; u.B = Pm; u.ldb = ld; u.Cin = cur; u.ldcin = ldc;
+        u.C = Yn; u.ldc = ld; u.alpha = 1.0; u.beta = 1.0; u.lowerC = symmetric ? 1 : 0;   // Y + Y P
         gemm(h, u);
         if (symmetric) mirror<double>(h, Yn, ld, 0, m, 1);
         if (cur == Y) { cur = Yn; Yn = dalloc(h, msz); } else std::swap(cur, Yn);
@@ -631,29 +641,32 @@ double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *ds
 }
 
 // ---------------------------------------------------------------------------
-// orthonormal basis of the columns of Y (n x m, ld ldy) by CholeskyQR2 -> U (ld ldu)
+// orthonormal basis of the columns of Y (n x m, ld ldy) by CholeskyQR2 -> U (ld ldu),
+// for `batch` independent blocks Y + z sY -> U + z sU
 // ---------------------------------------------------------------------------
-int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double *U, long long ldu)
+int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double *U, long long ldu, int batch = 1,
+            long long sY = 0, long long sU = 0)
 {
     Mark mk = mark(h);
-    double *G = dalloc(h, (size_t)m * m);
-    double *Gi = dalloc(h, (size_t)m * m);
-    double *W = dalloc(h, (size_t)n * m);
-    const double *src = Y; long long lds = ldy;
+    const long long gsz = (long long)m * m, wsz = (long long)n * m;
+    double *G = dalloc(h, (size_t)(gsz * batch));
+    double *Gi = dalloc(h, (size_t)(gsz * batch));
+    double *W = dalloc(h, (size_t)(wsz * batch));
+    const double *src = Y; long long lds = ldy, ss = sY;
     for (int pass = 0; pass < 2; ++pass) {
         GemmArgs g;  // G = Y^T Y (lower)
-        g.m = g.n = m; g.k = n; g.A = src; g.lda = lds; g.ta = 1; g.B = src; g.ldb = lds;
-        g.C = G; g.ldc = m; g.lowerC = 1;
+        g.m = g.n = m; g.k = n; g.batch = batch; g.A = src; g.lda = lds; g.sA = ss; g.ta = 1; g.B = src; g.ldb = lds;
+        g.sB = ss; g.C = G; g.ldc = m; g.sC = gsz; g.lowerC = 1;
         gemm(h, g);
         int fi;
-        if (chol_inv(h, G, m, m, 0, 1, Gi, 0, &fi)) { release(h, mk); return PSSD_ERR_BASIS; }
+        if (chol_inv(h, G, m, m, gsz, batch, Gi, gsz, &fi)) { release(h, mk); return PSSD_ERR_BASIS; }
         double *dst = (pass == 0) ? W : U;
-        long long ldd = (pass == 0) ? m : ldu;
+        long long ldd = (pass == 0) ? m : ldu, sd = (pass == 0) ? wsz : sU;
         GemmArgs q;  // U = Y G^{-T}
-        q.m = n; q.n = m; q.k = m; q.A = src; q.lda = lds; q.B = Gi; q.ldb = m; q.tb = 1; q.triB = TRI_UPPER;
-        q.C = dst; q.ldc = ldd;
+        q.m = n; q.n = m; q.k = m; q.batch = batch; q.A = src; q.lda = lds; q.sA = ss; q.B = Gi; q.ldb = m;
+        q.sB = gsz; q.tb = 1; q.triB = TRI_UPPER; q.C = dst; q.ldc = ldd; q.sC = sd;
         gemm(h, q);
-        src = dst; lds = ldd;
+        src = dst; lds = ldd; ss = sd;
     }
     release(h, mk);
     return PSSD_OK;
@@ -684,8 +697,12 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
         gemm(h, g);
     }
     int st = PSSD_OK;
-    if (p > 0) st = cholqr2(h, Yb, ld, m, p, U, ld);
-    if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld);
+    if (p > 0 && p == m - p) {   // equal halves: both bases in one batched pass
+        st = cholqr2(h, Yb, ld, m, p, U, ld, 2, p, p);
+    } else {
+        if (p > 0) st = cholqr2(h, Yb, ld, m, p, U, ld);
+        if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld);
+    }
     if (st) { release(h, mk); return st; }
     double *W = Yb;   // reuse: W = B U  (m x m)
     {
@@ -711,6 +728,42 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
     }
     release(h, mk);
     return PSSD_OK;
+}
+
+// backward error of the split of K by the basis U = [U_+ U_-]:
+// ||U_+^T K U_-||_F / ||K||_F, exactly from E = U_+^T K U_- when E is given,
+// else estimated with a Gaussian probe Omega ((n-p) x 16, N(0,1) entries):
+// E ||E Omega||_F^2 = 16 ||E||_F^2, with E Omega = U_+^T (K (U_- Omega)).
+double split_backward_error(pssd_handle h, const double *K, const double *U, int n, int p, const double *E)
+{
+    constexpr int s = 16;
+    const int q = n - p;
+    const long long ld = n;
+    Mark mk = mark(h);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+    double d2, e2, k2;
+    if (E) {
+        frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &e2);
+    } else {
+        double *Om = dalloc(h, (size_t)q * s), *T1 = dalloc(h, (size_t)n * s), *T2 = dalloc(h, (size_t)n * s);
+        double *T3 = dalloc(h, (size_t)p * s);
+        {
+            Timed t(h, K_HBM, 0);
+            fill_gaussian(Om, s, q, s, 0xbac3e77ull, h->stream);
+        }
+        GemmArgs a; a.m = n; a.n = s; a.k = q; a.A = U + p; a.lda = ld; a.B = Om; a.ldb = s; a.C = T1; a.ldc = s;
+        gemm(h, a);                                                      // U_- Omega
+        GemmArgs b; b.m = n; b.n = s; b.k = n; b.A = K; b.lda = ld; b.B = T1; b.ldb = s; b.C = T2; b.ldc = s;
+        gemm(h, b);                                                      // K U_- Omega
+        GemmArgs c; c.m = p; c.n = s; c.k = n; c.A = U; c.lda = ld; c.ta = 1; c.B = T2; c.ldb = s; c.C = T3;
+        c.ldc = s;
+        gemm(h, c);                                                      // U_+^T K U_- Omega
+        frob_pair(h, nullptr, s, T3, s, p, s, part, &d2, &e2);
+        e2 /= s;
+    }
+    frob_pair(h, nullptr, ld, K, ld, n, n, part, &d2, &k2);
+    release(h, mk);
+    return std::sqrt(e2 / k2);
 }
 
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
@@ -1151,11 +1204,13 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
         const long long ld = n, nsz = (long long)n * n;
         double *U = dalloc(h, nsz);
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
-        double *E = dalloc(h, (size_t)p * q + 1);
+        const bool exact_be = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
+        double *E = exact_be ? dalloc(h, (size_t)p * q + 1) : nullptr;
         st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
         if (st) return st;
         // C_+ = chol(B_+), C_- = chol(-B_-)
-        double *Cp = dalloc(h, (size_t)p * p + 1), *Cm = dalloc(h, (size_t)q * q + 1);
+        double *Cpm = dalloc(h, (size_t)p * p + (size_t)q * q + 1);
+        double *Cp = Cpm, *Cm = Cpm + (size_t)p * p;
         double *X = dalloc(h, nsz);
         int fi;
         if (p > 0) {
@@ -1166,8 +1221,12 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
             Timed t(h, K_HBM, 0);
             scale_copy(Bm, q, Cm, q, q, q, -1.0, h->stream);
         }
-        if (p > 0 && chol_inv<double>(h, Cp, p, p, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
-        if (q > 0 && chol_inv<double>(h, Cm, q, q, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        if (p > 0 && p == q) {   // both factors in one batched call
+            if (chol_inv<double>(h, Cp, p, p, (long long)p * p, 2, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        } else {
+            if (p > 0 && chol_inv<double>(h, Cp, p, p, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+            if (q > 0 && chol_inv<double>(h, Cm, q, q, 0, 1, nullptr, 0, &fi)) return PSSD_ERR_BASIS;
+        }
         if (p > 0) {   // X_+ = U_+ C_+, Q_+ = L^{-T} X_+, A11 = C_+^T C_+
             GemmArgs g; g.m = n; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Cp; g.ldb = p; g.triB = TRI_LOWER;
             g.C = X; g.ldc = ld;
@@ -1191,13 +1250,8 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
             g.ldb = ld; g.C = Q; g.ldc = ldq;
             gemm(h, g);
         }
-        if (info && p > 0 && q > 0) {   // ||U_+^T K U_-||_F / ||K||_F (backward error of the split of K ~ H)
-            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
-            double d2, e2, k2;
-            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &e2);
-            frob_pair(h, nullptr, ld, F.K, ld, n, n, part, &d2, &k2);
-            info->split_backerr = std::sqrt(e2 / k2);
-        }
+        if (info && p > 0 && q > 0)     // ||U_+^T K U_-||_F / ||K||_F (backward error of the split of K ~ H)
+            info->split_backerr = split_backward_error(h, F.K, U, n, p, E);
         return PSSD_OK;
     });
 }
@@ -1216,7 +1270,8 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
         const long long ld = n, nsz = (long long)n * n;
         double *U = dalloc(h, nsz);
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
-        double *E = dalloc(h, (size_t)p * q + 1);
+        const bool exact_be = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
+        double *E = exact_be ? dalloc(h, (size_t)p * q + 1) : nullptr;
         st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
         if (st) return st;
         double *Wp = dalloc(h, (size_t)p * p + 1), *Wm = dalloc(h, (size_t)q * q + 1);
@@ -1266,13 +1321,8 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
             gather_columns(Vt, ld, V, ldv, n, n, dperm, h->stream);
         }
         cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
-        if (info && p > 0 && q > 0) {   // ||U_+^T K U_-||_F / ||K||_F
-            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
-            double d2, e2, k2;
-            frob_pair(h, nullptr, q, E, q, p, q, part, &d2, &e2);
-            frob_pair(h, nullptr, ld, F.K, ld, n, n, part, &d2, &k2);
-            info->split_backerr = std::sqrt(e2 / k2);
-        }
+        if (info && p > 0 && q > 0)     // ||U_+^T K U_-||_F / ||K||_F
+            info->split_backerr = split_backward_error(h, F.K, U, n, p, E);
         return PSSD_OK;
 }
 }  // namespace

@@ -189,3 +189,17 @@ def test_order_limit_is_an_argument_error(P):
     st = P.lib().pssd_sign(h._h, P.MAX_N + 1, None, ctypes.c_void_p(H.data_ptr()), P.MAX_N + 1,
                            ctypes.c_void_p(S.data_ptr()), P.MAX_N + 1, ctypes.byref(o), ctypes.byref(info))
     assert st == -2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "emulated"])
+def test_split_backerr_estimate_tracks_exact(P, precision):
+    """Without PSSD_FLAG_RESIDUALS the split's backward error ||U_+^T K U_-||_F/||K||_F
+    comes from a 16-column Gaussian probe; with it, from the full product.  A
+    chi-square(16) norm ratio lies within [1/3, 3] except with probability < 1e-3."""
+    prec = {"fp64": P.PSSD_FP64, "emulated": P.PSSD_FP64_EMULATED}[precision]
+    H, _, _ = G.casida(150, ("loguniform", 1e-2, 1e2), seed=77)
+    Hd = _dev(H)
+    _, _, _, _, est = P.split(Hd, precision=prec)
+    _, _, _, _, ex = P.split(Hd, precision=prec, flags=P.FLAG_RESIDUALS)
+    assert 0 < ex["split_backerr"] <= 1e-12
+    assert ex["split_backerr"] / 3 <= est["split_backerr"] <= 3 * ex["split_backerr"]
