@@ -1,0 +1,178 @@
+"""GPU checks at the sizes of the workload configurations.
+
+* n = 128 (k = 64), d ~ U[1, 10], r = 8, plain FP64: full diagonalisation
+  against the oracle's definition-level eigendecomposition (scalar Cholesky +
+  Jacobi), eigenvalue by eigenvalue.
+* n = 4096 (k = 2048), d ~ U[0.1, 100], plain FP64 GPU path: full
+  diagonalisation, every eigenvalue against the definition lambda(H) =
+  lambda(L^T Sigma L) with Sigma H = L L^T (the oracle's scalar Jacobi would
+  take hours at this size, so the symmetric eigenvalues come from LAPACK),
+  plus ||HV - VD||_F / ||H||_F, V^T Sigma V = diag(I, -I) and the +- pairing.
+* n = 16384 (k = 8192), d log-uniform in [1e-2, 1e2], the benchmark's input
+  and precision modes: properties that hold at any size -- S^2 = I (the
+  library's exact residual), Sigma S symmetric, S H = H S on random probes,
+  tr S = 0, and for the split Q^T Sigma Q = diag(I, -I) on probes, A11 SPD,
+  A22 SND (Cholesky), and the spectral moments tr A11 = -tr A22 (pairing)
+  and tr A11^2 + tr A22^2 = tr H^2 (decoupling: the two blocks carry exactly
+  the spectrum of H).
+
+Tolerances: the FP64 and FP64-emulated paths meet the targets of the method
+(|lambda - lambda_ref| <= 1e-10 ||H||_2, ||S^2 - I||_F <= 1e-12 n, Sigma-
+symmetry <= 1e-12, ||HV - VD||_F / ||H||_F <= 1e-11; defects of non-normal S
+and Q scaled by ||S||_2^2, ||Q||_2^2 as in the parity tests).  The mixed path
+meets ||S^2 - I||_F <= 1e-12 n and the Sigma-symmetry after its FP64-accurate
+refinement, but Newton-Schulz converges to the involution nearest the FP32
+iterate, whose invariant subspaces keep the FP32 Zolotarev error, about
+u_32 kappa(K) = 6e-8 x 1e4 = 6e-4 for this input.  Its first-order subspace
+quantities (S H - H S, Q_+^T Sigma Q_-) are checked against
+delta = 1e-2 (that bound with a 15x margin), its Ritz-value moments against
+delta^2 = 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+import casida_inputs as G
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2203_08900_gb300 import build as b
+    b.build()
+    import paper_2203_08900_gb300 as P
+    P.lib()
+    return P
+
+
+def _J(n):
+    return np.r_[np.ones(n // 2), -np.ones(n // 2)]
+
+
+def _order(lam):
+    """Output convention: positive eigenvalues ascending, then negative ones by ascending magnitude."""
+    pos = np.sort(lam[lam > 0])
+    neg = lam[lam < 0][np.argsort(np.abs(lam[lam < 0]))]
+    return np.r_[pos, neg]
+
+
+def test_config_n128_r8_fp64_eig(P):
+    H, _, _ = G.casida(64, ("uniform", 1.0, 10.0), seed=0)
+    n = 128
+    D, V, info = P.eig(torch.from_numpy(H).cuda(), r=8)
+    D = D.cpu().numpy(); V = V.cpu().numpy()
+    lam, _ = O.eig_def(H)
+    nrm = np.max(np.abs(lam))
+    assert info["r_used"][0] == 8
+    assert np.max(np.abs(D - lam)) <= 1e-10 * nrm
+    assert np.linalg.norm(H @ V - V * D) <= 1e-11 * np.linalg.norm(H)
+    J = _J(n)
+    assert np.linalg.norm(V.T @ (J[:, None] * V) - np.diag(J)) <= 1e-12 * n * np.linalg.norm(V, 2) ** 2
+
+
+def test_config_n4096_fp64_eig_every_eigenvalue(P):
+    k = 2048
+    n = 2 * k
+    H, _, _ = G.casida(k, ("uniform", 0.1, 100.0), seed=11)
+    J = _J(n)
+    D, V, info = P.eig(torch.from_numpy(H).cuda())
+    D = D.cpu().numpy(); V = V.cpu().numpy()
+    # definition: Sigma H = L L^T, lambda(H) = lambda(L^T Sigma L)
+    M = J[:, None] * H
+    L = np.linalg.cholesky(0.5 * (M + M.T))
+    K = L.T @ (J[:, None] * L)
+    lam = _order(np.linalg.eigvalsh(0.5 * (K + K.T)))
+    nrm = np.max(np.abs(lam))
+    assert np.max(np.abs(D - lam)) <= 1e-10 * nrm
+    assert np.linalg.norm(H @ V - V * D) <= 1e-11 * np.linalg.norm(H)
+    assert np.linalg.norm(V.T @ (J[:, None] * V) - np.diag(J)) <= 1e-12 * n * np.linalg.norm(V, 2) ** 2
+    assert np.max(np.abs(D[k:] + D[:k])) <= 1e-10 * nrm      # +-omega pairs of the Casida form
+    assert info["levels"] >= 2
+
+
+@pytest.fixture(scope="module")
+def H16k():
+    H, _, _ = G.casida_torch(8192, ("loguniform", 1e-2, 1e2), seed=1234, device="cuda")
+    return H.contiguous()
+
+
+def _norm2(A, iters=30, seed=9):
+    """||A||_2 estimated by power iteration on A^T A (from below; enough to scale tolerances)."""
+    g = torch.Generator(device=A.device); g.manual_seed(seed)
+    x = torch.randn(A.shape[1], 1, device=A.device, dtype=A.dtype, generator=g)
+    for _ in range(iters):
+        x = A.T @ (A @ x)
+        x = x / torch.linalg.norm(x)
+    return float(torch.linalg.norm(A @ x))
+
+
+def _Jt(n):
+    return torch.cat([torch.ones(n // 2, device="cuda", dtype=torch.float64),
+                      -torch.ones(n // 2, device="cuda", dtype=torch.float64)])
+
+
+@pytest.mark.parametrize("prec_name,ctol", [("mixed", 1e-2), ("fp64e", None)])
+def test_config_n16384_sign_invariants(P, H16k, prec_name, ctol):
+    prec = {"mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}[prec_name]
+    n = H16k.shape[0]
+    S, info = P.sign(H16k, precision=prec, flags=P.FLAG_RESIDUALS)
+    J = _Jt(n)
+    s2 = max(1.0, _norm2(S)) ** 2
+    g = torch.Generator(device="cuda"); g.manual_seed(3)
+    X = torch.randn(n, 16, device="cuda", dtype=torch.float64, generator=g)
+    Y = torch.randn(n, 16, device="cuda", dtype=torch.float64, generator=g)
+    # S^2 = I: the library's exact ||S^2 - I||_F (the metric's condition)
+    assert info["s2_resid"] <= 1e-12 * n
+    # Sigma S symmetric: Y^T (Sigma S - (Sigma S)^T) X on probes, relative to ||S||_F
+    d = Y.T @ (J[:, None] * (S @ X)) - (X.T @ (J[:, None] * (S @ Y))).T
+    jsym = float(torch.linalg.norm(d) / (torch.linalg.norm(X) * torch.linalg.norm(Y) / n) / torch.linalg.norm(S))
+    # S H = H S on probes, relative to ||S||_2 ||H X||
+    c = S @ (H16k @ X) - H16k @ (S @ X)
+    comm = float(torch.linalg.norm(c) / (s2 ** 0.5 * torch.linalg.norm(H16k @ X)))
+    tr = abs(float(torch.trace(S)))
+    print(f"\n{prec_name}: s2_resid {info['s2_resid']:.3e}  jsym {jsym:.3e}  comm {comm:.3e}  "
+          f"|tr S| {tr:.3e}  ||S||_2^2 {s2:.3e}")
+    assert jsym <= 1e-12 * s2
+    assert comm <= (1e-11 * s2 if ctol is None else ctol)
+    assert tr <= 1e-10 * n * s2
+    del S, c
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec_name,tol,qtol", [("mixed", 1e-4, 1e-2), ("fp64e", 1e-11, None)])
+def test_config_n16384_split_decouples(P, H16k, prec_name, tol, qtol):
+    """qtol: the mixed path's Q_+^T Sigma Q_- carries its FP32 invariant-subspace
+    error (delta = 1e-2, first order; its moments delta^2); the FP64-emulated
+    path meets 1e-12 n ||Q||_2^2 and 1e-11."""
+    prec = {"mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}[prec_name]
+    n = H16k.shape[0]
+    k = n // 2
+    Q, A11, A22, p, info = P.split(H16k, precision=prec)
+    assert p == k
+    J = _Jt(n)
+    g = torch.Generator(device="cuda"); g.manual_seed(5)
+    X = torch.randn(n, 16, device="cuda", dtype=torch.float64, generator=g)
+    q2 = _norm2(Q) ** 2
+    r = Q.T @ (J[:, None] * (Q @ X)) - J[:, None] * X
+    qjq = float(torch.linalg.norm(r) / torch.linalg.norm(X))
+    spd = int(torch.linalg.cholesky_ex(A11)[1]) == 0
+    snd = int(torch.linalg.cholesky_ex(-A22)[1]) == 0
+    t1, t2 = torch.trace(A11), torch.trace(A22)
+    pair = float(torch.abs(t1 + t2) / torch.abs(t1))
+    trH2 = torch.sum(H16k * H16k.T)
+    mom2 = float(torch.abs(torch.sum(A11 * A11) + torch.sum(A22 * A22) - trH2) / trH2)
+    print(f"\n{prec_name}: QJQ {qjq:.3e} (||Q||_2^2 {q2:.3e})  pair {pair:.3e}  mom2 {mom2:.3e}  "
+          f"backerr {info['split_backerr']:.3e}")
+    assert spd and snd
+    if qtol is None:
+        assert qjq <= 1e-12 * n * q2
+    else:
+        assert qjq <= qtol * q2
+    assert pair <= tol
+    assert mom2 <= tol
+    if prec_name == "fp64e":
+        assert info["split_backerr"] <= 1e-11
+    del Q, A11, A22, r
+    torch.cuda.empty_cache()
