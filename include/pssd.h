@@ -119,6 +119,29 @@ int pssd_set_stream(pssd_handle h, void *stream);
 const char *pssd_last_cuda_error(pssd_handle h);
 const char *pssd_status_string(int status);
 
+/* ---------------------------------------------------------------------------
+ * Workspace.  By default a handle allocates device workspace on first use and
+ * keeps it (grown as needed) until pssd_destroy.  A caller that manages its own
+ * device memory can hand the handle one buffer instead; the handle then never
+ * allocates, and a call that needs more returns PSSD_ERR_ALLOC (the handle
+ * stays usable).  The worker handles of pssd_eig_batched keep library-managed
+ * workspaces.
+ * ------------------------------------------------------------------------- */
+/* Upper bound on the workspace bytes of one pssd_sign / pssd_split / pssd_eig
+ * call of order n with these options (r = 0 counts r = 8): (20 + 3 r) n^2
+ * doubles + 256 MiB.  Returns -2 for n outside [1, PSSD_MAX_N]. */
+int pssd_workspace_bytes(pssd_handle h, int n, const pssd_opts *opts, size_t *bytes);
+/* Use [dptr, dptr + bytes) (device memory, at least 4096 bytes, owned by the
+ * caller, kept alive until the handle is destroyed or the workspace replaced)
+ * as the handle's only workspace; dptr = NULL returns to library-managed
+ * workspace.  Synchronises the handle's stream and frees any workspace the
+ * library had allocated; resets the peak. */
+int pssd_set_workspace(pssd_handle h, void *dptr, size_t bytes);
+/* Largest workspace (bytes) a call on this handle has needed since it was
+ * created or since pssd_set_workspace: the exact size a caller-owned buffer
+ * needs for the same calls. */
+int pssd_workspace_peak(pssd_handle h, size_t *bytes);
+
 /*
  * Zolotarev coefficients (host only, FP64; Sec. 5.3).
  *   c_i = l^2 sn^2(i K'/(2r+1); l') / cn^2(i K'/(2r+1); l'), i = 1..2r  (Eq. Compcis,

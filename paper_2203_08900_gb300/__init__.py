@@ -64,7 +64,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
-           "pssd_test_gemm_f64"]
+           "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -108,6 +108,9 @@ def lib():
     L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
     L.pssd_launch_count.argtypes = [vp]
     L.pssd_launch_count.restype = ctypes.c_longlong
+    L.pssd_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
+    L.pssd_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.pssd_workspace_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     _lib = L
     return L
 
@@ -170,11 +173,35 @@ class Handle:
     def launch_count(self) -> int:
         return int(lib().pssd_launch_count(self._h))
 
+    # ---- workspace
+    def workspace_bytes(self, n: int, **kw) -> int:
+        """pssd_workspace_bytes: upper bound for one sign/split/eig call of order n."""
+        b = ctypes.c_size_t(0)
+        o = _opts(**kw)
+        self._check(lib().pssd_workspace_bytes(self._h, int(n), ctypes.byref(o), ctypes.byref(b)))
+        return int(b.value)
+
+    def set_workspace(self, buf: torch.Tensor | None):
+        """pssd_set_workspace: use a caller-owned CUDA tensor's memory as the only
+        workspace (None: back to library-managed).  The tensor is kept alive here."""
+        if buf is None:
+            self._check(lib().pssd_set_workspace(self._h, None, 0))
+            self._ws = None
+            return
+        nbytes = buf.numel() * buf.element_size()
+        self._check(lib().pssd_set_workspace(self._h, ctypes.c_void_p(buf.data_ptr()), nbytes))
+        self._ws = buf
+
+    def workspace_peak(self) -> int:
+        b = ctypes.c_size_t(0)
+        self._check(lib().pssd_workspace_peak(self._h, ctypes.byref(b)))
+        return int(b.value)
+
     def _check(self, st):
         if st:
             L = lib()
             msg = L.pssd_status_string(st).decode()
-            if st == 6:
+            if st in (6, 7):
                 msg += " (" + L.pssd_last_cuda_error(self._h).decode() + ")"
             raise PssdError(st, msg)
 

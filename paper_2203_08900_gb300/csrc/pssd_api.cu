@@ -41,7 +41,7 @@ namespace {
 
 constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 
-struct Chunk { char *base; size_t cap; size_t off; };
+struct Chunk { char *base; size_t cap; size_t off; bool owned; };   // owned: allocated by the library
 
 struct ProfEvent { cudaEvent_t a, b; int kind; double flops; };
 
@@ -61,6 +61,9 @@ struct pssd_handle_s {
     int *derr = nullptr;    // device error flag of the current call (bounded waits in the tensor-core kernel)
     int use_tc = 1;         // FP32 contractions on tcgen05 tensor cores (0: FP32 SIMT kernel)
     int force_engine = 0;   // test hooks: no size-based engine selection
+    bool user_ws = false;   // chunks[0] is caller-owned memory (pssd_set_workspace); never allocate
+    size_t depth = 0;       // bytes of workspace live in the current call (stack discipline)
+    size_t peak = 0;        // largest depth reached since creation or pssd_set_workspace
 };
 
 namespace {
@@ -81,15 +84,15 @@ inline void cuda_check(pssd_handle h, cudaError_t e, const char *what)
 // ---------------------------------------------------------------------------
 // workspace: chunked bump allocator with stack marks; chunks are kept for reuse
 // ---------------------------------------------------------------------------
-struct Mark { size_t chunk; size_t off; };
+struct Mark { size_t chunk; size_t off; size_t depth; };
 
 Mark mark(pssd_handle h)
 {
-    if (h->chunks.empty()) return {0, 0};
+    if (h->chunks.empty()) return {0, 0, h->depth};
     // the active chunk is the last one with off > 0, or 0
     size_t c = 0;
     for (size_t i = 0; i < h->chunks.size(); ++i) if (h->chunks[i].off > 0) c = i;
-    return {c, h->chunks.empty() ? 0 : h->chunks[c].off};
+    return {c, h->chunks[c].off, h->depth};
 }
 
 void release(pssd_handle h, Mark m)
@@ -98,12 +101,27 @@ void release(pssd_handle h, Mark m)
         if (i > m.chunk) h->chunks[i].off = 0;
         else if (i == m.chunk) h->chunks[i].off = m.off;
     }
+    h->depth = m.depth;
 }
 
 void *walloc(pssd_handle h, size_t bytes)
 {
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes == 0) bytes = 256;
+    h->depth += bytes;
+    h->peak = std::max(h->peak, h->depth);
+    if (h->user_ws) {   // caller-owned workspace: one chunk, no allocation
+        Chunk &c = h->chunks[0];
+        if (c.off + bytes > c.cap) {
+            h->depth -= bytes;
+            h->last_err = "workspace set by pssd_set_workspace is too small (" + std::to_string(c.cap) +
+                          " bytes; this call needs more than " + std::to_string(c.off + bytes) + ")";
+            throw Fail{PSSD_ERR_ALLOC};
+        }
+        void *p = c.base + c.off;
+        c.off += bytes;
+        return p;
+    }
     Mark m = mark(h);
     for (size_t i = m.chunk; i < h->chunks.size(); ++i) {
         Chunk &c = h->chunks[i];
@@ -118,7 +136,7 @@ void *walloc(pssd_handle h, size_t bytes)
         h->last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         throw Fail{PSSD_ERR_ALLOC};
     }
-    h->chunks.push_back({(char *)p, cap, bytes});
+    h->chunks.push_back({(char *)p, cap, bytes, true});
     return p;
 }
 
@@ -1076,12 +1094,12 @@ int pssd_destroy(pssd_handle h)
     cudaStreamSynchronize(h->stream);
     for (auto *w : h->workers) {
         cudaStreamSynchronize(w->stream);
-        for (auto &c : w->chunks) cudaFree(c.base);
+        for (auto &c : w->chunks) if (c.owned) cudaFree(c.base);
         for (auto &e : w->free_events) cudaEventDestroy(e);
         cudaStreamDestroy(w->stream);
         delete w;
     }
-    for (auto &c : h->chunks) cudaFree(c.base);
+    for (auto &c : h->chunks) if (c.owned) cudaFree(c.base);
     for (auto &e : h->free_events) cudaEventDestroy(e);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     delete h;
@@ -1373,6 +1391,48 @@ int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *laun
     return PSSD_OK;
 }
 
+int pssd_set_workspace(pssd_handle h, void *dptr, size_t bytes)
+{
+    if (!h) return -1;
+    if (dptr && bytes < 4096) return -3;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->last_err = "cudaStreamSynchronize before replacing the workspace failed";
+        return PSSD_ERR_CUDA;
+    }
+    for (auto &c : h->chunks) if (c.owned) cudaFree(c.base);
+    h->chunks.clear();
+    h->user_ws = false;
+    h->depth = 0;
+    h->peak = 0;
+    if (dptr) {   // align the start to 256 bytes inside the caller's buffer
+        const uintptr_t a = ((uintptr_t)dptr + 255) & ~(uintptr_t)255;
+        const size_t lost = (size_t)(a - (uintptr_t)dptr);
+        h->chunks.push_back({(char *)a, bytes - lost, 0, false});
+        h->user_ws = true;
+    }
+    return PSSD_OK;
+}
+
+int pssd_workspace_peak(pssd_handle h, size_t *bytes)
+{
+    if (!h) return -1;
+    if (!bytes) return -2;
+    *bytes = h->peak;
+    return PSSD_OK;
+}
+
+int pssd_workspace_bytes(pssd_handle h, int n, const pssd_opts *opts, size_t *bytes)
+{
+    if (!h) return -1;
+    if (n < 1 || n > PSSD_MAX_N) return -2;
+    if (!bytes) return -4;
+    pssd_opts o = opts ? *opts : defaults();
+    const double rmax = o.r > 0 ? o.r : 8;
+    const double nn = (double)n * (double)n * sizeof(double);
+    *bytes = (size_t)((20.0 + 3.0 * rmax) * nn) + ((size_t)256 << 20);
+    return PSSD_OK;
+}
+
 // process-wide number of kernels the library has launched (all handles)
 long long pssd_launch_count(pssd_handle h) { return h ? g_launches.load() : -1; }
 
@@ -1433,7 +1493,7 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
     // temporary of pssd_sign is carved from it, nothing is allocated
     pssd_handle_s local;
     local.stream = h->stream;
-    local.chunks.push_back({(char *)scratch, NOALLOC_SCRATCH_BYTES, 0});
+    local.chunks.push_back({(char *)scratch, NOALLOC_SCRATCH_BYTES, 0, false});
     int st = pssd_sign(&local, n, sigma, H, ldh, S, lds, opts, info);
     if (local.chunks.size() != 1) {   // cannot happen for n <= NOALLOC_MAX_N (bounded workspace)
         cudaStreamSynchronize(local.stream);
