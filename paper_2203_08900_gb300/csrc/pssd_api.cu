@@ -146,9 +146,9 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // ---------------------------------------------------------------------------
 // launch accounting and optional per-launch CUDA-event timing
 // ---------------------------------------------------------------------------
-enum Kind { K_DGEMM = 0, K_POTRF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
+enum Kind { K_DGEMM = 0, K_CHOL_LEAF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
             K_OZGEMM = 8, K_NKIND = 9 };
-static_assert(K_DGEMM == PSSD_KIND_DGEMM && K_POTRF == PSSD_KIND_CHOL_LEAF && K_HBM == PSSD_KIND_HBM &&
+static_assert(K_DGEMM == PSSD_KIND_DGEMM && K_CHOL_LEAF == PSSD_KIND_CHOL_LEAF && K_HBM == PSSD_KIND_HBM &&
                   K_GEMV == PSSD_KIND_GEMV && K_JACOBI == PSSD_KIND_JACOBI && K_SGEMM == PSSD_KIND_SGEMM &&
                   K_DFGEMM == PSSD_KIND_DFGEMM && K_TCGEMM == PSSD_KIND_TCGEMM && K_OZGEMM == PSSD_KIND_OZGEMM &&
                   K_NKIND == PSSD_NKIND,
@@ -336,7 +336,7 @@ void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, 
               int *dinfo, T *tmp, long long sT)
 {
     if (s <= CholLeaf<T>::max_s) {
-        Timed t(h, K_POTRF, batch * (double)s * s * s);
+        Timed t(h, K_CHOL_LEAF, batch * (double)s * s * s);
         if (chol_leaf<T>(A, lda, sA, Rinv, lda, sR, off, s, batch, dinfo, h->stream)) {
             h->last_err = "Cholesky leaf launch configuration failed";
             throw Fail{PSSD_ERR_CUDA};
