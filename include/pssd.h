@@ -31,7 +31,8 @@
  *  - Orders are limited to 1 <= n <= PSSD_MAX_N (some passes put one matrix
  *    row per grid row); larger n is rejected as an invalid argument.
  *  - Workspace is allocated by the handle on first use and grown as needed
- *    (cudaMalloc outside any stream capture); pssd_destroy frees it.
+ *    (cudaMalloc outside any stream capture); pssd_destroy frees it.  A
+ *    caller can supply the workspace instead (pssd_set_workspace).
  */
 #ifndef PSSD_H
 #define PSSD_H
@@ -53,7 +54,7 @@ extern "C" {
 #define PSSD_ERR_NONFINITE 4           /* NaN/Inf in the input or an iterate */
 #define PSSD_ERR_TIMEOUT 5             /* a bounded device wait gave up (tensor-core pipeline) */
 #define PSSD_ERR_CUDA 6                /* a CUDA call failed; see pssd_last_cuda_error */
-#define PSSD_ERR_ALLOC 7               /* workspace allocation failed */
+#define PSSD_ERR_ALLOC 7               /* workspace allocation failed, or the caller's workspace is too small */
 #define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
 #define PSSD_ERR_NOALLOC_TOO_LARGE 9   /* pssd_sign_noalloc: n exceeds PSSD_NOALLOC_MAX_N */
 
@@ -80,7 +81,7 @@ typedef struct {
     int precision;      /* PSSD_FP64, PSSD_MIXED or PSSD_FP64_EMULATED */
     int max_restarts;   /* restarts allowed after a failed stopping test (Alg. 8); < 0 = default (2) */
     int leaf;           /* pssd_eig: subproblems of at most this order are solved by Jacobi; 0 = 64 */
-    int flags;          /* PSSD_FLAG_RESIDUALS or 0 */
+    int flags;          /* bitwise OR of PSSD_FLAG_* (0: none) */
 } pssd_opts;
 
 typedef struct {
@@ -103,8 +104,9 @@ typedef struct {
     double seconds;      /* wall time of the call (host clock, stream synchronised) */
     int precision;       /* precision mode used */
     int fp32_steps;      /* PSSD_MIXED: FP32 Zolotarev steps taken (r of the first four in r_used, l in ell) */
-    int ns_steps;        /* PSSD_MIXED: Newton-Schulz updates applied */
-    double ns_resid;     /* PSSD_MIXED: ||I - sign(K)^2||_F after refinement, K = L^T Sigma L */
+    int ns_steps;        /* PSSD_MIXED: third-order Newton-Schulz steps applied */
+    double ns_resid;     /* PSSD_MIXED: ||I - sign(K)^2||_F after refinement, K = L^T Sigma L (from a
+                            64-column Gaussian probe when the step's prediction was within tolerance) */
 } pssd_info;
 
 /* Fill `o` with the defaults (r = 0, alpha = beta = 0, FP64, 2 restarts, leaf 64). */
@@ -115,7 +117,7 @@ void pssd_opts_init(pssd_opts *o);
 int pssd_create(pssd_handle *h, void *stream);
 int pssd_destroy(pssd_handle h);
 int pssd_set_stream(pssd_handle h, void *stream);
-/* Last CUDA error string recorded by the handle (never NULL). */
+/* Last CUDA error or failure message recorded by the handle (never NULL). */
 const char *pssd_last_cuda_error(pssd_handle h);
 const char *pssd_status_string(int status);
 
