@@ -8,6 +8,10 @@
 // The HBM-bound passes (symmetrisation, mirror, shift, combine, norms) use
 // 32x32 shared-memory transposes so that both the row and the column access
 // are coalesced.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "pssd_internal.h"
 
 #include <math.h>
@@ -17,6 +21,19 @@
 namespace pssd {
 
 std::atomic<long long> g_launches{0};
+
+bool ensure_dynamic_smem(const void *func, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, func})) return true;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    done.insert({dev, func});
+    return true;
+}
 
 
 // --------------------------------------------------------------------------
@@ -285,14 +302,8 @@ template <class T>
 int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long long sR, int off, int s, int batch,
               int *info, cudaStream_t st)
 {
-    static bool attr = false;
     const size_t sm = chol_leaf_smem<T>(CholLeaf<T>::max_s);
-    if (!attr) {
-        if (cudaFuncSetAttribute(chol_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-            cudaSuccess)
-            return -1;
-        attr = true;
-    }
+    if (!ensure_dynamic_smem((const void *)chol_leaf_kernel<T>, (int)sm)) return -1;
     if (s <= 0 || s > CholLeaf<T>::max_s) return -2;
     chol_leaf_kernel<T><<<batch, dim3(32, 16), chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info); count_launch();
     return 0;

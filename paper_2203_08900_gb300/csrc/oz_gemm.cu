@@ -482,13 +482,7 @@ size_t oz_gemm_workspace_bytes(const GemmArgs &g)
 int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM_BYTES) !=
-            cudaSuccess)
-            return -2;
-        attr_done = true;
-    }
+    if (!ensure_dynamic_smem((const void *)oz_gemm_kernel, OZ_SMEM_BYTES)) return -2;
     const int kp = (g.k + 15) / 16 * 16;
     const int mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
     unsigned char *base = (unsigned char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);

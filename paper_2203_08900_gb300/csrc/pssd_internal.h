@@ -13,6 +13,11 @@ namespace pssd {
 extern std::atomic<long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Allow `func` (a __global__ function) `bytes` of dynamic shared memory on the
+// current device: set once per (device, function), thread-safe.  False if the
+// attribute call failed.
+bool ensure_dynamic_smem(const void *func, int bytes);
+
 enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 enum GemmMode { GM_F64 = 0, GM_F32 = 1, GM_DF = 2, GM_OZ = 3 };
 

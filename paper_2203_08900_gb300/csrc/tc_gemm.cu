@@ -338,13 +338,7 @@ size_t tc_gemm_workspace_bytes(const GemmArgs &g)
 int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
-    static bool attr_done = false;
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES) !=
-            cudaSuccess)
-            return -2;
-        attr_done = true;
-    }
+    if (!ensure_dynamic_smem((const void *)tc_gemm_kernel, TC_SMEM_BYTES)) return -2;
     const int kp = (g.k + 15) / 16 * 16;
     const int mp = (g.m + TC_BM - 1) / TC_BM * TC_BM, np = (g.n + TC_BN - 1) / TC_BN * TC_BN;
     float *base = (float *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
