@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     unsigned long long *bars = (unsigned long long *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
     // bars[0..ST): full, [ST..2ST): empty, [2ST]: chunk done (MMA -> flush), [2ST+1]: accumulators free
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * OZ_STAGES + 4);
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_issued;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -222,15 +222,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     const int nchunks = (nkb + OZ_CHUNK_STAGES - 1) / OZ_CHUNK_STAGES;
     const uint32_t b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[OZ_STAGES]);
     const uint32_t b_done = smem_u32(&bars[2 * OZ_STAGES]), b_free = smem_u32(&bars[2 * OZ_STAGES + 1]);
+    const uint32_t b_drain = smem_u32(&bars[2 * OZ_STAGES + 2]);   // MMA drain after an abort
 
     if (tid == 0) {
         s_abort = 0;
+        s_issued = 0;
         for (int s = 0; s < OZ_STAGES; ++s) {
             mbar_init(b_full + 8 * s, 1);
             mbar_init(b_empty + 8 * s, 1);
         }
         mbar_init(b_done, 1);
         mbar_init(b_free, 32 * OZ_FLUSH_WARPS);
+        mbar_init(b_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -263,6 +266,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                 bulk_load(st, srca + (long long)q * (OZ_S * OZ_BM * OZ_BK), OZ_S * OZ_A_TILE, b_full + 8 * s);
                 bulk_load(st + OZ_S * OZ_A_TILE, srcb + (long long)q * (OZ_S * OZ_BN * OZ_BK), OZ_S * OZ_B_TILE,
                           b_full + 8 * s);
+                s_issued = q + 1;
             }
         }
     } else if (warp == OZ_MMA_WARP) {
@@ -296,6 +300,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                 }
                 if (!ok) { s_abort = 1; atomicExch(g.err, 3); break; }
                 mma_commit(b_done);
+            }
+            if (s_abort) {   // let the MMAs already issued retire before TMEM and the stages go away
+                mma_commit(b_drain);
+                mbar_wait(b_drain, 0u);
             }
         }
     } else {
@@ -348,8 +356,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (s_abort && tid == 32 * OZ_PRODUCER_WARP) {   // producer lane: let copies in flight land before exit
-        for (int q = 0; q < min(nkb, OZ_STAGES); ++q) mbar_wait(b_full + 8 * (q % OZ_STAGES), 0u);
+    if (s_abort && tid == 32 * OZ_PRODUCER_WARP) {   // producer lane: let the last copies issued land
+        for (int q = max(0, s_issued - OZ_STAGES); q < s_issued; ++q)
+            mbar_wait(b_full + 8 * (q % OZ_STAGES), (uint32_t)((q / OZ_STAGES) & 1));
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
 }

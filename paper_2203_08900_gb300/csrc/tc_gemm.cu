@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     unsigned long long *bars = (unsigned long long *)(smem + TC_STAGES * TC_STAGE_BYTES);
     // bars[0..ST): full, [ST..2ST): empty, [2ST]: accumulator done
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * TC_STAGES + 2);
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_issued;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -157,14 +157,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int nkb = (kend > kbeg) ? (kend + TC_BK - 1) / TC_BK - kb0 : 0;
     const uint32_t b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[TC_STAGES]);
     const uint32_t b_done = smem_u32(&bars[2 * TC_STAGES]);
+    const uint32_t b_drain = smem_u32(&bars[2 * TC_STAGES + 1]);   // MMA drain after an abort
 
     if (tid == 0) {
         s_abort = 0;
+        s_issued = 0;
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(b_full + 8 * s, 1);
             mbar_init(b_empty + 8 * s, 1);
         }
         mbar_init(b_done, 1);
+        mbar_init(b_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 mbar_expect_tx(b_full + 8 * s, TC_STAGE_BYTES);
                 bulk_load(st, srca + (long long)q * (TC_A_BYTES / 4), TC_A_BYTES, b_full + 8 * s);
                 bulk_load(st + TC_A_BYTES, srcb + (long long)q * (TC_B_BYTES / 4), TC_B_BYTES, b_full + 8 * s);
+                s_issued = q + 1;
             }
         }
     } else if (warp == TC_MMA_WARP) {
@@ -217,6 +221,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
             if (ok) mma_commit(b_done);
             else { s_abort = 1; atomicExch(g.err, 2); }
+            if (s_abort) {   // let the MMAs already issued retire before TMEM and the stages go away
+                mma_commit(b_drain);
+                mbar_wait(b_drain, 0u);
+            }
         }
     } else {
         // ---------------- epilogue warps ----------------
@@ -262,8 +270,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (s_abort && tid == 32 * TC_PRODUCER_WARP) {   // producer lane: let copies in flight land before exit
-        for (int q = 0; q < min(nkb, TC_STAGES); ++q) mbar_wait(b_full + 8 * (q % TC_STAGES), 0u);
+    if (s_abort && tid == 32 * TC_PRODUCER_WARP) {   // producer lane: let the last copies issued land
+        for (int q = max(0, s_issued - TC_STAGES); q < s_issued; ++q)
+            mbar_wait(b_full + 8 * (q % TC_STAGES), (uint32_t)((q / TC_STAGES) & 1));
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
