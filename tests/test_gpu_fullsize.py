@@ -176,3 +176,19 @@ def test_config_n16384_split_decouples(P, H16k, prec_name, tol, qtol):
         assert info["split_backerr"] <= 1e-11
     del Q, A11, A22, r
     torch.cuda.empty_cache()
+
+
+def test_config_n16384_same_q_exact_spectrum_fp64e(P):
+    """Q1 = Q2 at the benchmark's size and distribution: lambda(H) = +-sqrt(d1_i d2_i)
+    exactly, so every eigenvalue of the FP64-emulated full diagonalisation is
+    checked against a closed form (|lambda - lambda_ref| <= 1e-10 ||H||_2)."""
+    H, d1, d2 = G.casida_torch(8192, ("loguniform", 1e-2, 1e2), seed=4321, device="cuda", same_q=True)
+    H = H.contiguous()
+    om = torch.sort(torch.sqrt(d1 * d2)).values
+    ref = torch.cat([om, -om])
+    D, V, info = P.eig(H, precision=P.PSSD_FP64_EMULATED)
+    err = float(torch.max(torch.abs(D - ref)) / om[-1])
+    print(f"\nsame-Q n=16384 fp64e: max |lambda - lambda_ref| / ||H||_2 = {err:.3e}, levels {info['levels']}")
+    assert err <= 1e-10
+    del D, V, H
+    torch.cuda.empty_cache()
