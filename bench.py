@@ -37,6 +37,16 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(t, device="cpu"):
+    """The job's time: the largest of the ranks' times (needs an initialised
+    process group; NCCL on the GPU machine, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -174,11 +184,17 @@ def run_batch(args):
     import paper_2203_08900_gb300 as P
     from paper_2203_08900_gb300 import build as B
     B.build()
-    dev = torch.device("cuda", 0)
+    ws, rank, local = dist_env()
+    if ws > 1:   # independent batches per rank (weak scaling), no data-path collective
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
     ks = G.batch_sizes(args.batch_count, 16, 1024, seed=0)
     Hs = []
     for i, k in enumerate(ks):
-        H, _, _ = G.casida_torch(int(k), ("uniform", 0.5, 50.0), seed=10000 + i, device=dev)
+        H, _, _ = G.casida_torch(int(k), ("uniform", 0.5, 50.0), seed=10000 + rank * args.batch_count + i,
+                                 device=dev)
         Hs.append(H.contiguous())
     torch.cuda.synchronize()
     prec = {"fp64": P.PSSD_FP64, "mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}[args.precision]
@@ -187,7 +203,9 @@ def run_batch(args):
     for _ in range(args.warmup):
         P.eig_batched(Hs, handle=h, precision=prec)
     torch.cuda.synchronize()
-    clocks = Clocks(0)
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     h.profile_reset()
     l0 = h.launch_count()
@@ -197,22 +215,29 @@ def run_batch(args):
         Ds, Vs, infos = P.eig_batched(Hs, handle=h, precision=prec)
     e1.record(stream)
     torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     ck = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        t = max_over_ranks(t, dev)
     # accuracy over the batch (untimed): max relative eigen-residual
     res = 0.0
     with torch.no_grad():
         for H, D, V in zip(Hs, Ds, Vs):
             res = max(res, float(torch.linalg.norm(H @ V - V * D) / torch.linalg.norm(H)))
     n3 = float(sum((2.0 * k) ** 3 for k in ks))
-    line = {"metric": "batched diagonalisation: instances/s", "value": args.batch_count * args.steps / t,
-            "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    line = {"metric": "batched diagonalisation: instances/s", "value": ws * args.batch_count * args.steps / t,
+            "unit": "instances/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": "batch of %d Casida matrices, k log-uniform [16,1024], d ~ U[0.5,50]"
                        % args.batch_count, "sum_n3": n3, "precision": args.precision},
             "max_rel_residual": res, "gpu_launches": h.launch_count() - l0, "clocks": ck}
-    print(json.dumps(line))
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -302,9 +327,7 @@ def main():
     launches = h.launch_count() - l0
     t = e0.elapsed_time(e1) / 1e3
     if ws > 1:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+        t = max_over_ranks(t, dev)
     kinds = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
     # dominant kernel of this precision mode
     dom = max(["dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm"], key=lambda kk: kinds[kk]["ms"])
