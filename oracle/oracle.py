@@ -370,6 +370,71 @@ def sign_alg(H, sigma=None, r: int | None = None, alpha: float | None = None,
     raise RuntimeError("Zolo-PD: stopping test failed after %d restarts" % max_restarts)
 
 
+def dwh_sign_alg(H, sigma=None, alpha: float | None = None, beta: float | None = None, max_iter: int = 30):
+    """The Sigma-DWH iteration Sec. 6 compares against: the Zolotarev step of
+    Eq. (ZoloIt2) with degree r = 1 (the dynamically weighted Halley step;
+    Sec. 5.3 identifies the two) repeated with the l-update of Alg. 8 after
+    every step, until ||X_{k+1} - X_k||_F / ||X_{k+1}||_F <= u^{1/3} (the step
+    converges cubically).  Bounds as in Alg. 8 (reading R5).
+    Returns (S, info) with info["iterations"] and the l sequence."""
+    n = H.shape[0]
+    s = signature(n, sigma)
+    A = np.array(H, dtype=np.float64)
+    al, be = (float(alpha), float(beta)) if (alpha is not None and beta is not None) else estimate_bounds(A, s)
+    X = A / al
+    ell = min(be / al, 1.0)
+    info = {"ell": [ell], "iterations": 0}
+    for it in range(max_iter):
+        c, a, chat, ell1 = zolo_coeffs(ell, 1)
+        Xn = zolo_step(X, s, c, a, chat)
+        crit = np.linalg.norm(Xn - X) / np.linalg.norm(Xn)
+        X = Xn
+        ell = min(ell1, 1.0)
+        info["ell"].append(ell)
+        info["iterations"] = it + 1
+        if crit <= U_FP64 ** (1.0 / 3.0):
+            return X, info
+    raise RuntimeError("Sigma-DWH did not converge in %d steps" % max_iter)
+
+
+def byers_xu_scalings(a: float, b: float, count: int):
+    """The suboptimal scaling factors of Byers and Xu for Newton's iteration
+    (the comparison method of Sec. 6) for a spectrum whose magnitudes lie in
+    [b, a]: z_0 = 1/sqrt(ab), z_1 = sqrt(2 sqrt(ab)/(a+b)),
+    z_{k+1} = 1/sqrt((z_k + 1/z_k)/2)."""
+    z = [1.0 / math.sqrt(a * b)]
+    if count > 1:
+        z.append(math.sqrt(2.0 * math.sqrt(a * b) / (a + b)))
+    while len(z) < count:
+        z.append(1.0 / math.sqrt(0.5 * (z[-1] + 1.0 / z[-1])))
+    return z[:count]
+
+
+def newton_sign_scaled(H, sigma=None, alpha: float | None = None, beta: float | None = None, max_iter: int = 60):
+    """Scaled Newton iteration for sign(H) (Eq. NewtonSign with the scaling of
+    Byers and Xu, the comparison method of Sec. 6):
+    X_{k+1} = (z_k X_k + (z_k X_k)^{-1}) / 2, X_0 = H/alpha, spectral bounds
+    a = 1, b = beta/alpha; the inverse by Gaussian elimination with partial
+    pivoting.  Stops when ||X_{k+1} - X_k||_F / ||X_{k+1}||_F <= u^{1/2}
+    (quadratic convergence), never after the first step.
+    Returns (S, info) with info["iterations"]."""
+    n = H.shape[0]
+    s = signature(n, sigma)
+    A = np.array(H, dtype=np.float64)
+    al, be = (float(alpha), float(beta)) if (alpha is not None and beta is not None) else estimate_bounds(A, s)
+    X = A / al
+    zs = byers_xu_scalings(1.0, min(be / al, 1.0), max_iter)
+    I = np.eye(n)
+    for it in range(max_iter):
+        z = zs[it]
+        Xn = 0.5 * (z * X + lu_solve(z * X, I))
+        crit = np.linalg.norm(Xn - X) / np.linalg.norm(Xn)
+        X = Xn
+        if it > 0 and crit <= math.sqrt(U_FP64):
+            return X, {"iterations": it + 1}
+    raise RuntimeError("scaled Newton did not converge in %d steps" % max_iter)
+
+
 def split_alg(H, sigma=None, S=None):
     """Alg. 7 (robust (Sigma, Sigma_hat)-orthogonal basis via pivoted,
     truncated LDL^T) and the projections of Thm. DefDivConq.

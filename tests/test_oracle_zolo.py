@@ -133,6 +133,33 @@ def test_choose_r_rule():
     assert O.choose_r(1e-4, tau=2.0 ** -24) <= O.choose_r(1e-4)
 
 
+_KAPPAS = [10, 1e2, 1e3, 1e4, 1e8, 1e12, 1e16]
+_TAUS = [1e-15, 1e-6]   # the FP64 steps and the FP32 steps of the mixed path
+
+
+def _ell2_product_form(ell, r):
+    """l_2 of two steps, evaluated with the product form of Eq. (hatZ) at the
+    interval's end point (independent of the coefficient routine's own
+    l-update): l_1 = Zhat(l; l), l_2 = Zhat(l_1; l_1)."""
+    l1 = min(float(O.zolo_eval(ell, ell, r)), 1.0)
+    return min(float(O.zolo_eval(l1, l1, r)), 1.0)
+
+
+@pytest.mark.parametrize("tau", _TAUS)
+@pytest.mark.parametrize("kappa", _KAPPAS)
+def test_choose_r_is_minimal(kappa, tau):
+    """Reading R3 of the choice of r (Sec. 5.3, "two steps suffice"): r is the
+    SMALLEST degree for which two steps map [1/kappa, 1] into [1 - tau, 1].
+    Pins both halves of the rule: the criterion holds at r and fails at r - 1,
+    so an off-by-one or a wrong tau fails here."""
+    ell = 1.0 / kappa
+    r = O.choose_r(ell, tau)
+    assert 1 <= r <= 8
+    assert 1.0 - _ell2_product_form(ell, r) <= tau
+    if r > 1:
+        assert 1.0 - _ell2_product_form(ell, r - 1) > tau
+
+
 def test_sc_comp_against_real_argument_landen():
     """Two independent routes to sc(u) agree to within the real-argument
     route's own error, which grows like u_fp64/cn (cos of an angle near pi/2)."""
