@@ -18,10 +18,12 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -51,8 +53,8 @@ class Clocks:
     """nvidia-smi sampling during the timed region."""
 
     def __init__(self, gpu_index):
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        fd, self.path = tempfile.mkstemp(prefix="pssd_clocks_", suffix=".csv")
+        os.close(fd)
         self.proc = None
         self.gpu = gpu_index
 
@@ -91,47 +93,83 @@ class Clocks:
             for nm, val in zip(names, v[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if sm:
             out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                    "samples": len(sm)}
         return out
 
 
-def cpu_baseline_sample(seconds_target=20.0):
-    """The oracle (Alg. 8 + Alg. 7 in scalar-loop FP64 C) on a bounded sample
-    of the same workload: the same generator at n = 512 (k = 256), timed on the
-    host cores, scaled to n = 16384 by n^3."""
+ORACLE_SIZES = (256, 384, 512)
+
+
+def _oracle_solve(n_s, seed=0):
+    """One oracle sign (Alg. 8, scalar-loop pivoted elimination of Eq. ZoloIt2,
+    the r shifted systems in r threads) + split (Alg. 7) of an order-n_s input
+    of the workload's distribution; returns (seconds, threads used)."""
     import casida_inputs as G
     import oracle as O
-    n_s = 512
-    H, _, _ = G.casida(n_s // 2, ("loguniform", 1e-2, 1e2), seed=0)
+    H, _, _ = G.casida(n_s // 2, ("loguniform", 1e-2, 1e2), seed=seed)
     t0 = time.perf_counter()
     S, info = O.sign_alg(H)
     O.split_alg(H, None, S)
-    t = time.perf_counter() - t0
-    scale = (16384 / n_s) ** 3
-    return {"value": t * scale, "unit": "s/solve", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle sign (Alg. 8, scalar-loop pivoted elimination) + split (Alg. 7) of one n=%d "
-                      "Casida input of the same distribution: %.2f s measured, scaled by (16384/%d)^3 = %d "
-                      "to s/solve at n=16384 (extrapolated)" % (n_s, t, n_s, int(scale)),
-            "measured_s": t, "measured_n": n_s}
+    return time.perf_counter() - t0, max(info["r"])
+
+
+def cpu_baseline_sample(n_target=16384):
+    """The oracle on a bounded sample of the same workload (about 12 s of host
+    work): one solve at each of n = 256, 384, 512, a least-squares fit of
+    t = c n^3 through them, and the fit evaluated at n_target (extrapolated;
+    the oracle's dense steps are O(n^3))."""
+    ts, thr = [], 1
+    for n_s in ORACLE_SIZES:
+        t, r = _oracle_solve(n_s)
+        ts.append(t); thr = max(thr, r)
+    x = [float(n) ** 3 for n in ORACLE_SIZES]
+    c = sum(a * b for a, b in zip(x, ts)) / sum(a * a for a in x)
+    # log-log slope of the measurements, to show how close to n^3 they are
+    lx = [math.log(n) for n in ORACLE_SIZES]; ly = [math.log(t) for t in ts]
+    mx, my = sum(lx) / 3, sum(ly) / 3
+    slope = sum((a - mx) * (b - my) for a, b in zip(lx, ly)) / sum((a - mx) ** 2 for a in lx)
+    return {"value": c * n_target ** 3, "unit": "s/solve", "cores": thr, "kind": "oracle",
+            "sample": "oracle sign (Alg. 8: scalar-loop pivoted elimination of Eq. ZoloIt2, r shifted systems in "
+                      "r threads) + split (Alg. 7) of one Casida input of the workload's distribution at each of "
+                      "n = %s: %s s; t = c n^3 fitted (measured log-log slope %.2f) and evaluated at n = %d "
+                      "(extrapolated); cores = threads the shifted solves used (max r); numpy matmuls use the "
+                      "host BLAS" % (", ".join(map(str, ORACLE_SIZES)), ", ".join("%.2f" % t for t in ts),
+                                     slope, n_target),
+            "measured_s": dict(zip(map(str, ORACLE_SIZES), ts)), "loglog_slope": slope}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is one bounded
+    sample of the workload (one oracle sign + split at n = 384, about 3 s),
+    reported in the metric's unit by n^3 scaling to n = 16384 (extrapolated);
+    ms_per_step is the measured time of a step."""
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return 0
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline_sample()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline_sample())
-    v = statistics.median([x["value"] for x in vals])
-    cb = dict(vals[-1]); cb["value"] = v
+    n_s = 384
+    for i in range(args.warmup):
+        _oracle_solve(n_s, seed=i)
+    ts, thr = [], 1
+    for i in range(args.steps):
+        t, r = _oracle_solve(n_s, seed=100 + i)
+        ts.append(t); thr = max(thr, r)
+    tm = statistics.median(ts)
+    v = tm * (args.n / n_s) ** 3
+    cb = {"value": v, "unit": "s/solve", "cores": thr, "kind": "oracle",
+          "sample": "each step: oracle sign (Alg. 8) + split (Alg. 7) of one n=%d Casida input of the workload's "
+                    "distribution (median %.2f s), scaled by (%d/%d)^3 to s/solve at n=%d (extrapolated)"
+                    % (n_s, tm, args.n, n_s, args.n)}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/solve", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tm * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "casida_n16384_log1e-2_1e2 split (oracle sample n=512, n^3-scaled)"},
+            "config": {"workload": "casida_n%d_log1e-2_1e2 split" % args.n, "n": args.n,
+                       "sample_n": n_s, "note": "value extrapolated by n^3 from the sample; ms_per_step measured"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "s/solve", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -252,8 +290,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp64e"],
                     help="fp64: native FP64; mixed: FP32 Zolotarev + FP64-accurate refinement; "
-                         "fp64e: the FP64 algorithm with FP64 emulated on the FP32 pipe")
-    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison solve")
+                         "fp64e: the FP64 algorithm with every contraction FP64-accurate on the BF16 tensor cores")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64-emulated and plain-FP64 solves on the same input")
     ap.add_argument("--workload", default="split", choices=["split", "batch"],
                     help="split: one n x n sign + split per step (headline); batch: full diagonalisation of "
                          "512 Casida matrices with k log-uniform in [16, 1024], d ~ U[0.5, 50]")
@@ -282,6 +321,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_2203_08900_gb300 import build as B
     B.build()
+    peaks = measured_peaks()
     n = args.n
     k = n // 2
     dist_d = ("loguniform", 1e-2, 1e2)
@@ -296,7 +336,8 @@ def main():
     h = P.Handle(stream)
     p = n // 2
 
-    prec = {"fp64": P.PSSD_FP64, "mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}[args.precision]
+    PREC = {"fp64": P.PSSD_FP64, "mixed": P.PSSD_MIXED, "fp64e": P.PSSD_FP64_EMULATED}
+    prec = PREC[args.precision]
 
     def step(pr=prec):
         return P.split(H, handle=h, precision=pr)
@@ -329,78 +370,38 @@ def main():
     if ws > 1:
         t = max_over_ranks(t, dev)
     kinds = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
-    # dominant kernel of this precision mode
-    dom = max(["dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm"], key=lambda kk: kinds[kk]["ms"])
-    gemm = kinds[dom]
     last = infos[-1]
     rs = [x for x in last["r_used"][:last["passes"]]]
     # algorithmic FLOPs: the library's exact structural count of every contraction it launched
     fl = sum(kinds[kk]["flops"] for kk in ("dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm", "chol_leaf")) / args.steps
     solves = args.steps * ws
     s_per_solve = t / solves
-    # accuracy of the split, measured outside the timed region: S = Q Q^T Sigma,
-    # randomized estimates of ||S^2 - I||_F and ||S H - H S||_F / ||H||_F
-    with torch.no_grad():
-        J = torch.cat([torch.ones(p, device=dev, dtype=torch.float64), -torch.ones(n - p, device=dev, dtype=torch.float64)])
-        g = torch.Generator(device=dev); g.manual_seed(7)
-        X = torch.randn(n, 16, device=dev, dtype=torch.float64, generator=g)
-        Sx = lambda Y: Q @ (Q.T @ (J[:, None] * Y))
-        R = Sx(Sx(X)) - X
-        s2 = float(torch.linalg.norm(R) / 4.0)                     # E||(S^2-I)x||^2 = ||S^2-I||_F^2
-        C = Sx(H @ X) - H @ Sx(X)
-        comm = float(torch.linalg.norm(C) / 4.0 / torch.linalg.norm(H))
-        QJQ = float(torch.linalg.norm(Q.T @ (J[:, None] * Q) - torch.diag(J)) / torch.linalg.norm(Q) ** 2)
+    table = kernel_table(kinds, t, args.steps, peaks)
+    dom = max(["dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm"], key=lambda kk: kinds[kk]["ms"])
+    roof = dict(table[dom])
+    roof.update({"kernel": KERNEL_NAMES[dom], "traffic": None})
+    acc = split_accuracy(P, torch, H, Q, p, dev)
     # the metric's condition on S itself: S = L^{-T} sign(K) L^T from pssd_sign in the same
-    # precision mode, ||S^2 - I||_F computed by the library (untimed)
+    # precision mode, ||S^2 - I||_F and ||SH - HS||_F / ||H||_F computed by the library (untimed)
     S_chk, info_s = P.sign(H, handle=h, precision=prec, flags=P.FLAG_RESIDUALS)
-    s2_sign = info_s["s2_resid"]
     del S_chk
-    peak_fp64 = 152 * 2 * 2 * 2.07e9 / 1e12        # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12      # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
-    achieved = (gemm["flops"] / gemm["launches"]) / (gemm["ms"] / gemm["launches"] / 1e3) / 1e12 if gemm["launches"] else None
-    # the FP64-emulating kernel spends 13 FP32 instructions per multiply-add (see the design notes):
-    # its ALU roof is the FP32 issue rate / 6.5 in FP64-equivalent FLOP/s
-    bf16_meas = 1901.5    # measured cuBLAS BF16 dense TFLOP/s on this machine's GB300 (burst)
-    try:
-        bf16_meas = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
-    except Exception:
-        pass
-    # tensor-core kernels are reported in the tensor pipe's own operations:
-    #   tcgemm: 3 TF32 products per FP32 product; TF32 peak = BF16 peak x (1.1 / 2.25) nominal ratio
-    #   ozgemm: 36 BF16 slice products per FP64 product; peak = measured BF16
-    tensor_factor = {"tcgemm": 3.0, "ozgemm": 36.0}.get(dom, 1.0)
-    if achieved is not None:
-        achieved *= tensor_factor
-    peak_dom = {"dgemm": peak_fp64, "sgemm": peak_fp32, "dfgemm": peak_fp32 / 13.0,
-                "tcgemm": bf16_meas * 1.1 / 2.25, "ozgemm": bf16_meas}[dom]
+    acc.update({"s2_resid_sign": info_s["s2_resid"], "s2_bound": 1e-12 * n,
+                "s2_ok": bool(info_s["s2_resid"] <= 1e-12 * n), "comm_rel_sign": info_s["comm_resid"],
+                "split_backerr_K": last["split_backerr"], "comm_rel_split_lib": last["comm_resid"]})
     line = {
         "metric": METRIC, "value": s_per_solve, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp64e": "f64 (emulated on f32)"}[args.precision],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp64e": "f64 (emulated on bf16 tensor cores)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "casida_n%d_log1e-2_1e2 split (sign+split), %s path" % (n, args.precision), "n": n,
                    "k": k, "precision": args.precision, "l2": "inputs larger than L2 (2.1 GB per H), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "tflops": fl * solves / t / 1e12, "algorithmic_flops_per_solve": fl,
         "r_per_pass": rs, "restarts": last["restarts"], "alpha": last["alpha"], "beta": last["beta"],
-        "accuracy": {"s2_resid_sign": s2_sign, "s2_bound": 1e-12 * n, "s2_ok": bool(s2_sign <= 1e-12 * n),
-                     "s2_resid_est_from_Q": s2, "comm_rel_est_from_Q": comm, "qjq_rel_defect": QJQ,
-                     "split_backerr_K": last["split_backerr"]},
-        "roofline": {"kernel": {"dgemm": "gemm_kernel<GM_F64> (FP64 DFMA, 64x64x16 tiles)",
-                                "sgemm": "gemm_kernel<GM_F32> (FP32 FFMA)",
-                                "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated on the FP32 pipe)",
-                                "tcgemm": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
-                                "ozgemm": "oz_gemm_kernel (tcgen05 kind::f16 BF16, 36 integer-slice products)"}[dom],
-                     "bound": "tensor" if dom in ("tcgemm", "ozgemm") else "alu",
-                     "achieved": achieved, "peak": peak_dom, "unit": "TFLOP/s",
-                     "frac": (achieved / peak_dom) if achieved else None, "traffic": None,
-                     "peak_note": {"dgemm": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (cuBLAS DGEMM measured 1.09)",
-                                   "sgemm": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz",
-                                   "dfgemm": "derived: FP32 issue rate (152 SM x 128/clk x 2.07 GHz) / 13 instructions per multiply-add x 2 flop",
-                                   "tcgemm": "of measured: BF16 burst x 1.1/2.25 (TF32 nominal ratio); achieved counts the 3 TF32 products",
-                                   "ozgemm": "of measured: BF16 burst; achieved counts the 36 BF16 slice products (FP64-equivalent = achieved/36)"}[dom],
-                     "share_of_step": gemm["ms"] / 1e3 / t if t > 0 else None},
-        "kernels": kinds,
+        "accuracy": acc,
+        "roofline": roof,
+        "kernels": table,
         "gpu_launches": launches,
         "clocks": ck,
     }
@@ -414,39 +415,149 @@ def main():
         A22h = torch.empty((n - p, n - p), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True); f1 = torch.cuda.Event(enable_timing=True)
+        fa = torch.cuda.Event(enable_timing=True); fb = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         Hd = Hh.to(dev, non_blocking=True)
+        fa.record(stream)
         Q2, B11, B22, _, _ = P.split(Hd, handle=h, precision=prec)
+        fb.record(stream)
         Qh.copy_(Q2, non_blocking=True); A11h.copy_(B11, non_blocking=True); A22h.copy_(B22, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
         te = f0.elapsed_time(f1) / 1e3
-        line["e2e"] = {"value": te, "unit": "s/solve", "h2d_bytes_per_step": 8 * n * n,
-                       "d2h_bytes_per_step": 8 * (n * n + p * p + (n - p) ** 2)}
-    if rank == 0 and not args.no_compare and args.precision != "fp64":
-        # plain FP64 on the same input: one untimed warm-up (allocations), one timed solve
-        step(P.PSSD_FP64)
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        Qf, A11f, A22f, _, infof = step(P.PSSD_FP64)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        tf = g0.elapsed_time(g1) / 1e3
-        with torch.no_grad():
-            dA = float(torch.linalg.norm(torch.linalg.eigvalsh(A11f) - torch.linalg.eigvalsh(A11))
-                       / torch.linalg.norm(torch.linalg.eigvalsh(A11f)))
-        line["plain_fp64"] = {"s_per_solve": tf, "speedup_of_this_path": tf / s_per_solve,
-                              "split_backerr": infof["split_backerr"],
-                              "A11_spectrum_rel_diff_vs_this_path": dA,
-                              "note": "same input, 1 warm-up + 1 timed solve"}
+        hb, db = 8 * n * n, 8 * (n * n + p * p + (n - p) ** 2)
+        line["e2e"] = {"value": te, "unit": "s/solve", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db,
+                       "h2d_GBps": hb / (f0.elapsed_time(fa) / 1e3) / 1e9,
+                       "d2h_GBps": db / (fb.elapsed_time(f1) / 1e3) / 1e9,
+                       "note": "pinned host buffers; copy rates from events around the copies"}
+        del Q2, B11, B22, Hd
+    if rank == 0 and not args.no_compare:
+        # the other precision modes on the same input, same handle (workspace already grown)
+        for name in ("fp64e", "fp64"):
+            if name == args.precision:
+                continue
+            reps = 1 if name == "fp64" else max(1, min(3, args.steps))
+            if name == "fp64e":
+                step(PREC[name])          # one warm-up (the slice engine's extra workspace)
+            torch.cuda.synchronize()
+            h.profile(True); h.profile_reset()
+            g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(reps):
+                Qf, A11f, A22f, _, infof = step(PREC[name])
+            g1.record(stream)
+            torch.cuda.synchronize()
+            h.profile(False)
+            tf = g0.elapsed_time(g1) / 1e3 / reps
+            kf = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
+            tab = kernel_table(kf, tf * reps, reps, peaks)
+            domf = max(["dgemm", "dfgemm", "ozgemm"], key=lambda kk: kf[kk]["ms"])
+            with torch.no_grad():
+                dA = float(torch.linalg.norm(torch.linalg.eigvalsh(A11f) - torch.linalg.eigvalsh(A11))
+                           / torch.linalg.norm(torch.linalg.eigvalsh(A11f)))
+            accf = split_accuracy(P, torch, H, Qf, p, dev)
+            accf.update({"split_backerr_K": infof["split_backerr"], "comm_rel_split_lib": infof["comm_resid"]})
+            line["plain_fp64" if name == "fp64" else "fp64_emulated"] = {
+                "s_per_solve": tf, "speedup_vs_this_path": tf / s_per_solve,
+                "timed_solves": reps, "accuracy": accf,
+                "A11_spectrum_rel_diff_vs_headline_path": dA,
+                "dominant_kernel": dict(tab[domf], kernel=KERNEL_NAMES[domf]),
+                "kernels": tab, "r_per_pass": infof["r_used"][:infof["passes"]],
+                "note": "same input and handle" + ("; timed after the FP64-emulated solves (workspace allocated)"
+                                                   if name == "fp64" else "; 1 warm-up")}
+            del Qf, A11f, A22f
+        if "plain_fp64" in line and "fp64_emulated" in line:
+            line["fp64_emulated"]["speedup_vs_plain_fp64"] = (line["plain_fp64"]["s_per_solve"]
+                                                              / line["fp64_emulated"]["s_per_solve"])
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_sample(n)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+KERNEL_NAMES = {"dgemm": "gemm_kernel<GM_F64> (FP64 DFMA, 64x64x16 tiles)",
+                "sgemm": "gemm_kernel<GM_F32> (FP32 FFMA)",
+                "dfgemm": "gemm_kernel<GM_DF> (FP64 emulated with float pairs on the FP32 pipe)",
+                "tcgemm": "tc_gemm_kernel (tcgen05 kind::tf32, 3xTF32)",
+                "ozgemm": "oz_gemm_kernel (tcgen05 kind::f16 BF16, 36 integer-slice products)"}
+
+
+def measured_peaks():
+    """HBM copy bandwidth and BF16 dense throughput measured on this machine type
+    (MEASURED_PEAKS.json beside this file).  Fails loudly when absent: every
+    roofline fraction is taken against these measured numbers."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    with open(path) as f:
+        d = json.load(f)
+    return {"hbm_gbs": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+            "bf16_sustained": float(d["bf16_tflops_sustained"])}
+
+
+def kernel_table(kinds, t_total_s, steps, peaks):
+    """Per kind of kernel: time per step, share of the step, launches, and the
+    achieved rate against its roof.  Contractions: algorithmic FLOPs in the
+    pipe's own operations (3 TF32 products per 3xTF32 product, 36 BF16 slice
+    products per slice product) over the kernel's event-timed duration, against
+    the SUSTAINED measured BF16 peak (x 1.1/2.25, the nominal TF32/BF16 ratio,
+    for TF32) since these kernels run inside a seconds-long step, or against the
+    derived FP64 / FP32 ALU roofs.  Memory-bound passes: algorithmic bytes over
+    duration against the measured HBM copy bandwidth."""
+    fp64_roof = 152 * 2 * 2 * 2.07e9 / 1e12        # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    fp32_roof = 152 * 128 * 2 * 2.07e9 / 1e12      # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+    tensor = {"tcgemm": (3.0, peaks["bf16_sustained"] * 1.1 / 2.25,
+                         "of measured: sustained BF16 x 1.1/2.25 (TF32 nominal ratio); 3 TF32 products counted"),
+              "ozgemm": (36.0, peaks["bf16_sustained"],
+                         "of measured: sustained BF16; 36 BF16 slice products counted (FP64-equivalent = /36)")}
+    alu = {"dgemm": (fp64_roof, "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"),
+           "sgemm": (fp32_roof, "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+           "dfgemm": (fp32_roof / 13.0, "derived: FP32 issue rate / 13 instructions per multiply-add x 2 flop"),
+           "chol_leaf": (fp64_roof, "derived FP64 roof; the leaf is latency-bound (sequential columns)")}
+    out = {}
+    for name, v in kinds.items():
+        if v["launches"] == 0:
+            continue
+        ms = v["ms"]
+        row = {"ms_per_step": ms / steps, "share_of_step": ms / 1e3 / t_total_s if t_total_s > 0 else None,
+               "launches_per_step": v["launches"] / steps}
+        if name in tensor:
+            f, pk, note = tensor[name]
+            a = v["flops"] * f / (ms / 1e3) / 1e12
+            row.update({"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                        "peak_note": note})
+        elif name in alu:
+            pk, note = alu[name]
+            a = v["flops"] / (ms / 1e3) / 1e12
+            row.update({"bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                        "peak_note": note})
+        elif v.get("bytes", 0) > 0:
+            a = v["bytes"] / (ms / 1e3) / 1e9
+            row.update({"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": a / peaks["hbm_gbs"], "bytes_per_step": v["bytes"] / steps,
+                        "peak_note": "of measured HBM copy bandwidth; algorithmic bytes of the passes that count them"})
+        out[name] = row
+    return out
+
+
+def split_accuracy(P, torch, H, Q, p, dev):
+    """Accuracy of a split, measured outside the timed region: S = Q Q^T Sigma,
+    randomized estimates of ||S^2 - I||_F and ||SH - HS||_F / ||H||_F, and the
+    (Sigma, Sigma_hat)-orthogonality defect of Q."""
+    n = H.shape[0]
+    with torch.no_grad():
+        J = torch.cat([torch.ones(p, device=dev, dtype=torch.float64),
+                       -torch.ones(n - p, device=dev, dtype=torch.float64)])
+        g = torch.Generator(device=dev); g.manual_seed(7)
+        X = torch.randn(n, 16, device=dev, dtype=torch.float64, generator=g)
+        Sx = lambda Y: Q @ (Q.T @ (J[:, None] * Y))
+        R = Sx(Sx(X)) - X
+        s2 = float(torch.linalg.norm(R) / 4.0)                     # E||(S^2-I)x||^2 = ||S^2-I||_F^2
+        C = Sx(H @ X) - H @ Sx(X)
+        comm = float(torch.linalg.norm(C) / 4.0 / torch.linalg.norm(H))
+        QJQ = float(torch.linalg.norm(Q.T @ (J[:, None] * Q) - torch.diag(J)) / torch.linalg.norm(Q) ** 2)
+    return {"s2_resid_est_from_Q": s2, "comm_rel_est_from_Q": comm, "qjq_rel_defect": QJQ}
 
 
 if __name__ == "__main__":

@@ -56,7 +56,7 @@ extern "C" {
 #define PSSD_ERR_CUDA 6                /* a CUDA call failed; see pssd_last_cuda_error */
 #define PSSD_ERR_ALLOC 7               /* workspace allocation failed, or the caller's workspace is too small */
 #define PSSD_ERR_NOT_PSEUDOSYMMETRIC 8 /* ||Sigma H - (Sigma H)^T||_F > 1e-12 ||Sigma H||_F */
-#define PSSD_ERR_NOALLOC_TOO_LARGE 9   /* pssd_sign_noalloc: n exceeds PSSD_NOALLOC_MAX_N */
+#define PSSD_ERR_NOALLOC_TOO_LARGE 9   /* pssd_sign_noalloc: n exceeds PSSD_NOALLOC_MAX_N, or the temporaries exceed the scratch array */
 
 /* precision modes */
 #define PSSD_FP64 0          /* every step in native FP64 (DFMA) */
@@ -72,6 +72,25 @@ extern "C" {
 #define PSSD_FLAG_EMU_SIMT 4        /* emulated FP64 contractions with float pairs on the FP32 pipe instead of
                                        integer slices on the tensor cores (for comparison) */
 
+/* iteration for the sign function (pssd_opts.method; PSSD_FP64 and PSSD_FP64_EMULATED).
+ * All three run on the same congruence form K = L^T Sigma L and the same kernels.
+ *  PSSD_METHOD_ZOLO    hyperbolic Zolo-PD, Alg. 8: two steps of degree r, stopping test, restarts.
+ *  PSSD_METHOD_DWH     the Sigma-DWH iteration the paper compares against in Sec. 6: the Zolotarev
+ *                      step of degree r = 1 (the dynamically weighted Halley step, Sec. 5.3) repeated
+ *                      with the l-update until ||X_{k+1} - X_k||_F / ||X_{k+1}||_F <= u^{1/3}
+ *                      (cubic convergence), at most 30 steps.
+ *  PSSD_METHOD_NEWTON  the scaled Newton iteration X <- (z X + (z X)^{-1})/2 of Eq. (NewtonSign) with
+ *                      the suboptimal scaling of Byers and Xu that Sec. 6 compares against:
+ *                      z_0 = 1/sqrt(ab), z_1 = sqrt(2 sqrt(ab)/(a+b)), z_{k+1} = 1/sqrt((z_k + 1/z_k)/2)
+ *                      for spectral bounds a = 1, b = l of X_0; stops when the relative change is
+ *                      at most u^{1/2} (quadratic convergence), at most 60 steps.  X_0^{-1} comes from
+ *                      the Cholesky factor (K^{-1} = L^{-1} Sigma L^{-T}); later inverses as
+ *                      (X^2)^{-1} X from the Cholesky factor of X^2, whose condition number is at most
+ *                      kappa/4 after the first scaled step. */
+#define PSSD_METHOD_ZOLO 0
+#define PSSD_METHOD_DWH 1
+#define PSSD_METHOD_NEWTON 2
+
 typedef struct pssd_handle_s *pssd_handle;
 
 typedef struct {
@@ -82,6 +101,11 @@ typedef struct {
     int max_restarts;   /* restarts allowed after a failed stopping test (Alg. 8); < 0 = default (2) */
     int leaf;           /* pssd_eig: subproblems of at most this order are solved by Jacobi; 0 = 64 */
     int flags;          /* bitwise OR of PSSD_FLAG_* (0: none) */
+    int method;         /* PSSD_METHOD_* (0: Zolo-PD); PSSD_MIXED accepts only PSSD_METHOD_ZOLO */
+    long long wait_cycles; /* bound on each pipeline wait inside the tensor-core kernels, in polls of the
+                              mbarrier (0 = default, 2^26); when a wait runs out the kernel stops, waits for
+                              its own copies and products in flight, frees its tensor memory and the call
+                              returns PSSD_ERR_TIMEOUT with the handle still usable */
 } pssd_opts;
 
 typedef struct {
@@ -107,9 +131,19 @@ typedef struct {
     int ns_steps;        /* PSSD_MIXED: third-order Newton-Schulz steps applied */
     double ns_resid;     /* PSSD_MIXED: ||I - sign(K)^2||_F after refinement, K = L^T Sigma L (from a
                             64-column Gaussian probe when the step's prediction was within tolerance) */
+    double comm_resid;   /* ||S H - H S||_F / ||H||_F of the returned result (pssd_sign: S; pssd_split:
+                            S = Q Sigma_hat Q^T Sigma; pssd_eig: S = V V^T Sigma): exact with
+                            PSSD_FLAG_RESIDUALS, else estimated from a 16-column Gaussian probe;
+                            -1 if not computed.  S^2 = I alone does not certify the invariant
+                            subspaces; this commutator does (Lemma SignProj) */
+    int method;          /* iteration used (PSSD_METHOD_*) */
+    int iterations;      /* sign iterations taken (Zolotarev steps of all passes, DWH or Newton steps) */
 } pssd_info;
 
-/* Fill `o` with the defaults (r = 0, alpha = beta = 0, FP64, 2 restarts, leaf 64). */
+/* Fill `o` with the defaults (r = 0, alpha = beta = 0, FP64, 2 restarts, leaf 64, Zolo-PD,
+ * default wait bound).  Every entry point rejects options outside their ranges with the
+ * invalid-argument status of its opts argument: r outside [0, 64], alpha or beta negative or
+ * not finite, beta > alpha when both are given, precision or method unknown, wait_cycles < 0. */
 void pssd_opts_init(pssd_opts *o);
 
 /* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
@@ -183,6 +217,10 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
  *   A11 = Q_+^T (Sigma H) Q_+   (p x p, symmetric positive definite),
  *   A22 = -Q_-^T (Sigma H) Q_-  ((n-p) x (n-p), symmetric negative definite),
  * so that Q^{-1} H Q = diag(A11, A22).  p = number of +1 in sigma (Thm. EVRealSigmaOrth).
+ *   S      device, n x n, leading dimension lds >= n: a precomputed sign(H) (for example from
+ *          pssd_sign) from which the projectors P_+- = (I +- S)/2 of Lemma SignProj are taken;
+ *          NULL computes it (Alg. 8, as pssd_sign).  A given S is used as it is (its defect
+ *          shows in info->split_backerr and info->comm_resid); it is not modified.
  *   Q      device, n x n output (columns 0..p-1 = Q_+), leading dimension ldq >= n
  *   A11    device, p x p output, lda11 >= p;  A22 device, (n-p) x (n-p), lda22 >= n-p
  *   p      host int output (may be NULL)
@@ -190,8 +228,8 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
  * exact with PSSD_FLAG_RESIDUALS, otherwise a probe estimate).
  */
 int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
-               double *Q, int ldq, double *A11, int lda11, double *A22, int lda22, int *p,
-               const pssd_opts *opts, pssd_info *info);
+               const double *S, int lds, double *Q, int ldq, double *A11, int lda11, double *A22,
+               int lda22, int *p, const pssd_opts *opts, pssd_info *info);
 
 /*
  * Full diagonalisation V^{-1} H V = D (Alg. 3; after one split the
@@ -242,26 +280,33 @@ int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *
 
 /*
  * Allocation-free pssd_sign for small problems (the paper has no counterpart;
- * this exists for callers of the library).
+ * this entry point exists for callers of the library).
  *
- * Some callers cannot call cudaMalloc: code running while a CUDA graph is
- * being captured, applications whose device memory belongs to their own pool,
- * and latency-critical loops that cannot afford a first-call allocation.
- * pssd_sign_noalloc computes exactly what pssd_sign computes (same arguments,
- * same results) but takes every temporary from one fixed scratch array of
- * PSSD_NOALLOC_SCRATCH_BYTES in the library's device memory, which every GPU
- * that loads the library holds until the process exits.  It calls no
- * cudaMalloc or cudaFree, and the handle's own workspace is not touched.
+ * Some callers cannot let a library call cudaMalloc: applications whose device
+ * memory is owned by their own pool or caching allocator (a stray allocation
+ * outside it can fail once the pool has reserved the device, or fragments it),
+ * and latency-critical loops for which the device-wide synchronisation that
+ * cudaMalloc and cudaFree can cause is not acceptable.  pssd_sign_noalloc
+ * computes what pssd_sign computes (same arguments, same results) but takes
+ * every temporary from one fixed scratch array of PSSD_NOALLOC_SCRATCH_BYTES in
+ * the library's device memory, which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc or cudaFree (nor any
+ * allocating library routine), and the handle's own workspace is not touched.
  *   - n must be at most PSSD_NOALLOC_MAX_N; larger n returns
- *     PSSD_ERR_NOALLOC_TOO_LARGE without doing any work.
+ *     PSSD_ERR_NOALLOC_TOO_LARGE without doing any work.  A call whose
+ *     temporaries do not fit the scratch array (for example a large explicit
+ *     opts->r) stops with PSSD_ERR_NOALLOC_TOO_LARGE as soon as a temporary
+ *     would overflow it, also without allocating.
  *   - The first call on each device looks up the scratch array's device
- *     address (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture begins.
+ *     address (cudaGetSymbolAddress, with that device current); make that
+ *     first call before any stream capture begins.
  *   - All calls on a device share the one array and it keeps the previous
  *     call's contents (every value the computation reads is written first in
  *     the same call).  Calls that can overlap on the GPU -- on different
  *     streams, or from several host threads -- race on the array: serialise
  *     them.
+ *   - Like pssd_sign, the call synchronises the handle's stream where it needs
+ *     a host scalar (bounds, stopping test, residuals).
  */
 #define PSSD_NOALLOC_MAX_N 128
 #define PSSD_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -301,20 +346,29 @@ int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch
 #define PSSD_KIND_GEMV 3        /* matrix-vector products (bound estimation) */
 #define PSSD_KIND_JACOBI 4      /* Jacobi leaf eigensolver */
 #define PSSD_KIND_SGEMM 5       /* FP32 FFMA contraction */
-#define PSSD_KIND_DFGEMM 6      /* FP64 contraction in float pairs */
-#define PSSD_KIND_TCGEMM 7      /* FP32 contraction, 3xTF32 on tcgen05 */
-#define PSSD_KIND_OZGEMM 8      /* FP64 contraction, integer slices on tcgen05 (incl. slicing passes) */
-#define PSSD_NKIND 9
+#define PSSD_KIND_DFGEMM 6      /* FP64 contraction in float pairs (its operand split counts under PSSD_KIND_HBM) */
+#define PSSD_KIND_TCGEMM 7      /* FP32 contraction, 3xTF32 on tcgen05: the tensor-core kernel alone */
+#define PSSD_KIND_OZGEMM 8      /* FP64 contraction, integer slices on tcgen05: the tensor-core kernel alone */
+#define PSSD_KIND_OZPREP 9      /* exponent and slicing passes feeding PSSD_KIND_OZGEMM */
+#define PSSD_KIND_TCPREP 10     /* tf32 split passes feeding PSSD_KIND_TCGEMM */
+#define PSSD_NKIND 11
 /* on != 0 enables event timing on the handle (adds two events per region). */
 int pssd_profile_enable(pssd_handle h, int on);
 /* Zero the per-kind totals of the handle. */
 int pssd_profile_reset(pssd_handle h);
 /* Totals of one kind since the last reset: milliseconds, timed regions,
- * algorithmic FLOPs (any pointer may be NULL).  -2 if kind is out of range. */
-int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops);
+ * algorithmic FLOPs (contractions: the exact structural multiply-add count x 2)
+ * and algorithmic HBM bytes (memory-bound passes: the bytes each pass must read
+ * and write; 0 where not counted).  Any pointer may be NULL; -2 if kind is out
+ * of range. */
+int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops,
+                      double *bytes);
 /* Number of kernels the library has launched in this process (all handles;
  * one count per launch).  -1 if h is NULL. */
 long long pssd_launch_count(pssd_handle h);
+/* Number of device allocations (cudaMalloc calls) the library has made in this
+ * process (all handles, workspace growth included). */
+long long pssd_device_alloc_count(void);
 
 #ifdef __cplusplus
 }

@@ -21,17 +21,19 @@ PSSD_MIXED = 1
 PSSD_FP64_EMULATED = 2
 FLAG_RESIDUALS = 1
 
-# kinds reported by profile_read
-K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM, K_OZGEMM = range(9)
-KIND_NAMES = ["dgemm", "chol_leaf", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm", "ozgemm"]
+# kinds reported by profile_read (PSSD_KIND_* of include/pssd.h)
+K_DGEMM, K_POTRF, K_HBM, K_GEMV, K_JACOBI, K_SGEMM, K_DFGEMM, K_TCGEMM, K_OZGEMM, K_OZPREP, K_TCPREP = range(11)
+KIND_NAMES = ["dgemm", "chol_leaf", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", "dfgemm", "tcgemm", "ozgemm",
+              "ozprep", "tcprep"]
 FLAG_NO_TENSOR_CORES = 2
 FLAG_EMU_SIMT = 4
+METHOD_ZOLO, METHOD_DWH, METHOD_NEWTON = 0, 1, 2
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_restarts", ctypes.c_int), ("leaf", ctypes.c_int),
-                ("flags", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("method", ctypes.c_int), ("wait_cycles", ctypes.c_longlong)]
 
 
 class Info(ctypes.Structure):
@@ -41,7 +43,8 @@ class Info(ctypes.Structure):
                 ("s2_resid", ctypes.c_double), ("jsym_resid", ctypes.c_double),
                 ("split_backerr", ctypes.c_double), ("fail_index", ctypes.c_int), ("levels", ctypes.c_int),
                 ("seconds", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_steps", ctypes.c_int),
-                ("ns_steps", ctypes.c_int), ("ns_resid", ctypes.c_double)]
+                ("ns_steps", ctypes.c_int), ("ns_resid", ctypes.c_double), ("comm_resid", ctypes.c_double),
+                ("method", ctypes.c_int), ("iterations", ctypes.c_int)]
 
     def as_dict(self):
         d = {}
@@ -64,7 +67,8 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_status_string", "pssd_zolo_coeffs", "pssd_choose_r", "pssd_sign", "pssd_split", "pssd_eig",
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
-           "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak"]
+           "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
+           "pssd_device_alloc_count"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -91,7 +95,7 @@ def lib():
     L.pssd_choose_r.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
     sig = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.pssd_sign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
-    L.pssd_split.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ip,
+    L.pssd_split.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ip,
                                    ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_eig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
@@ -105,14 +109,21 @@ def lib():
                                    ctypes.POINTER(Info)]
     L.pssd_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pssd_profile_reset.argtypes = [vp]
-    L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
+    L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.pssd_launch_count.argtypes = [vp]
     L.pssd_launch_count.restype = ctypes.c_longlong
+    L.pssd_device_alloc_count.argtypes = []
+    L.pssd_device_alloc_count.restype = ctypes.c_longlong
     L.pssd_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
     L.pssd_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
     L.pssd_workspace_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     _lib = L
     return L
+
+
+def device_alloc_count() -> int:
+    """Device allocations (cudaMalloc calls) the library has made in this process."""
+    return int(lib().pssd_device_alloc_count())
 
 
 def zolo_coeffs(ell: float, r: int):
@@ -166,9 +177,10 @@ class Handle:
         lib().pssd_profile_reset(self._h)
 
     def profile_read(self, kind: int):
-        ms = ctypes.c_double(); cnt = ctypes.c_longlong(); fl = ctypes.c_double()
-        lib().pssd_profile_read(self._h, int(kind), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl))
-        return {"ms": ms.value, "launches": cnt.value, "flops": fl.value}
+        ms = ctypes.c_double(); cnt = ctypes.c_longlong(); fl = ctypes.c_double(); by = ctypes.c_double()
+        lib().pssd_profile_read(self._h, int(kind), ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl),
+                                ctypes.byref(by))
+        return {"ms": ms.value, "launches": cnt.value, "flops": fl.value, "bytes": by.value}
 
     def launch_count(self) -> int:
         return int(lib().pssd_launch_count(self._h))
@@ -206,11 +218,13 @@ class Handle:
             raise PssdError(st, msg)
 
 
-def _opts(r=0, alpha=0.0, beta=0.0, precision=PSSD_FP64, max_restarts=2, leaf=64, flags=0):
+def _opts(r=0, alpha=0.0, beta=0.0, precision=PSSD_FP64, max_restarts=2, leaf=64, flags=0, method=METHOD_ZOLO,
+          wait_cycles=0):
     o = Opts()
     lib().pssd_opts_init(ctypes.byref(o))
     o.r = int(r); o.alpha = float(alpha); o.beta = float(beta); o.precision = int(precision)
     o.max_restarts = int(max_restarts); o.leaf = int(leaf); o.flags = int(flags)
+    o.method = int(method); o.wait_cycles = int(wait_cycles)
     return o
 
 
@@ -277,10 +291,15 @@ def sign_noalloc(H, S=None, sigma=None, handle=None, **kw):
     return S, info.as_dict()
 
 
-def split(H, sigma=None, handle=None, **kw):
-    """One structure-preserving split.  Returns (Q, A11, A22, p, info)."""
+def split(H, sigma=None, handle=None, S=None, **kw):
+    """One structure-preserving split.  S: optional precomputed sign(H) (an n x n
+    row-major float64 CUDA tensor); None computes it.  Returns (Q, A11, A22, p, info)."""
     n, ldh = _check_H(H)
     h = _handle(handle)
+    if S is not None:
+        _check_H(S)
+        if S.shape != H.shape:
+            raise ValueError("S must match H")
     keep, sp = _sigma(n, sigma)
     p = int((keep > 0).sum()) if keep is not None else n // 2
     Q = torch.empty_like(H)
@@ -289,8 +308,9 @@ def split(H, sigma=None, handle=None, **kw):
     pp = ctypes.c_int(0)
     info = Info()
     o = _opts(**kw)
-    st = lib().pssd_split(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(Q.data_ptr()),
-                          Q.stride(0), ctypes.c_void_p(A11.data_ptr()), A11.stride(0),
+    st = lib().pssd_split(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh,
+                          ctypes.c_void_p(S.data_ptr() if S is not None else 0), S.stride(0) if S is not None else n,
+                          ctypes.c_void_p(Q.data_ptr()), Q.stride(0), ctypes.c_void_p(A11.data_ptr()), A11.stride(0),
                           ctypes.c_void_p(A22.data_ptr()), A22.stride(0), ctypes.byref(pp), ctypes.byref(o),
                           ctypes.byref(info))
     h._check(st)

@@ -24,7 +24,12 @@
 // 4. Every 512 terms of k the eight level sums are scaled by 2^{-7L} (exact)
 //    and added into a float-pair (TwoSum) accumulator per output; at the end
 //    C = alpha 2^{e_i + f_j} (hi + lo) + beta Cin in FP64.
-// Products with a + b > S + 1 (36 of 64 kept) are dropped: below 2^-63 relative.
+// Products with a + b > S + 1 (36 of 64 kept) are dropped.  Level L = a + b
+// carries weight 2^{-7L} and its terms are at most 2^12 (2^14 with a d_1 slice),
+// so the first dropped level (L = 10, seven products) contributes up to about
+// 7 * 2^12 * 2^-70 ~ 2^-55 of the row/column maxima per term, and the levels
+// beyond it less: the dropped part is ~2^-55 relative to sum_p |a_ip||b_pj| in
+// the worst case (the measured error is 0.9-1.7e-15 of that sum).
 //
 // Kernel layout: one CTA of 18 warps per 128 x 64 output tile, warp-specialised:
 // warp 16 streams the 8 A-slice tiles (128 x 16 BF16) and 8 B-slice tiles
@@ -36,7 +41,9 @@
 // (warp w reads TMEM lanes 32 (w % 4) .. and 16 columns per level, so four
 // warps per SM sub-partition hide the TwoSum latency) while the producer keeps
 // prefetching, then signal the MMA warp that the accumulators are free.
-// Every mbarrier wait is bounded (error flag, TMEM freed, return).
+// Every pipeline mbarrier wait is bounded by the caller's limit (error flag,
+// then the kernel waits -- under a fixed, longer bound -- for its own bulk
+// copies and MMAs in flight, frees TMEM and returns).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,7 +65,7 @@ constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 4 KB
 constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 2 KB
 constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_TILE + OZ_B_TILE);   // 48 KB
 constexpr int OZ_SMEM_BYTES = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
-constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;
+constexpr unsigned long long OZ_WAIT_LIMIT = 1ull << 26;   // default pipeline bound and the drain bound
 constexpr int OZ_TMEM_COLS = 512;
 constexpr int OZ_FLUSH_WARPS = 16;         // warp w: TMEM lanes 32 (w % 4) .., columns 16 (w / 4) ..
 constexpr int OZ_FCOLS = OZ_BN / (OZ_FLUSH_WARPS / 4);   // 16 output columns per flush thread
@@ -79,6 +86,7 @@ struct OzArgs {
     double alpha, beta;
     int alpha_e, alpha_e_valid, alpha_neg;   // alpha = (-1)^neg 2^alpha_e when valid
     int *err;
+    unsigned long long wait_limit;         // polls per pipeline wait before giving up
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,9 +101,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit)
 {
-    for (unsigned long long it = 0; it < OZ_WAIT_LIMIT; ++it) {
+    for (unsigned long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\n"
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             for (int q = 0; q < nkb; ++q) {
                 const int s = q % OZ_STAGES;
                 if (q >= OZ_STAGES &&
-                    !mbar_wait(b_empty + 8 * s, (uint32_t)(((q / OZ_STAGES) - 1) & 1))) {
+                    !mbar_wait(b_empty + 8 * s, (uint32_t)(((q / OZ_STAGES) - 1) & 1), g.wait_limit)) {
                     s_abort = 1; atomicExch(g.err, 1); break;
                 }
                 if (s_abort) break;
@@ -273,13 +281,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             for (int c = 0; c < nchunks && !s_abort; ++c) {
-                if (c > 0 && !mbar_wait(b_free, (uint32_t)((c - 1) & 1))) { s_abort = 1; atomicExch(g.err, 2); break; }
+                if (c > 0 && !mbar_wait(b_free, (uint32_t)((c - 1) & 1), g.wait_limit)) {
+                    s_abort = 1; atomicExch(g.err, 2); break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const int q0 = c * OZ_CHUNK_STAGES, q1 = min(nkb, q0 + OZ_CHUNK_STAGES);
                 bool ok = true;
                 for (int q = q0; q < q1; ++q) {
                     const int s = q % OZ_STAGES;
-                    if (!mbar_wait(b_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1))) { ok = false; break; }
+                    if (!mbar_wait(b_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1), g.wait_limit)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t st = smem_u32(smem + s * OZ_STAGE_BYTES);
                     // A slice a against B slices b = 1 .. S+1-a stacked along N: the product
@@ -301,10 +311,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                 if (!ok) { s_abort = 1; atomicExch(g.err, 3); break; }
                 mma_commit(b_done);
             }
-            if (s_abort) {   // let the MMAs already issued retire before TMEM and the stages go away
-                mma_commit(b_drain);
-                mbar_wait(b_drain, 0u);
-            }
+            // Every MMA issued has retired before TMEM and the stages go away, whatever
+            // the other roles did (a flush warp that gave up no longer waits for them).
+            mma_commit(b_drain);
+            mbar_wait(b_drain, 0u, OZ_WAIT_LIMIT);
         }
     } else {
         // ---------------- flush warps: lanes 32 (w % 4) .., columns c0 .. c0 + 15 ----------------
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         for (int q = 0; q < OZ_FCOLS; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(b_done, (uint32_t)(c & 1))) { ok = false; atomicExch(g.err, 4); break; }
+            if (!mbar_wait(b_done, (uint32_t)(c & 1), g.wait_limit)) { ok = false; atomicExch(g.err, 4); break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
             for (int L = 0; L < OZ_LEVELS; ++L) {
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     __syncthreads();
     if (s_abort && tid == 32 * OZ_PRODUCER_WARP) {   // producer lane: let the last copies issued land
         for (int q = max(0, s_issued - OZ_STAGES); q < s_issued; ++q)
-            mbar_wait(b_full + 8 * (q % OZ_STAGES), (uint32_t)((q / OZ_STAGES) & 1));
+            mbar_wait(b_full + 8 * (q % OZ_STAGES), (uint32_t)((q / OZ_STAGES) & 1), OZ_WAIT_LIMIT);
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
 }
@@ -488,41 +498,65 @@ size_t oz_gemm_workspace_bytes(const GemmArgs &g)
     return (size_t)(OZ_S * (mp + np) * kp * g.batch) * 2 + (size_t)(mp + np) * g.batch * sizeof(int) + 2048;
 }
 
-int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+namespace {
+struct OzLayout {
+    int kp, mp, np;
+    __nv_bfloat16 *sa, *sb;
+    int *ea, *eb;
+};
+OzLayout oz_layout(const GemmArgs &g, void *ws)
+{
+    OzLayout L;
+    L.kp = (g.k + 15) / 16 * 16;
+    L.mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM; L.np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+    unsigned char *base = (unsigned char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    L.sa = (__nv_bfloat16 *)base;
+    L.sb = L.sa + (size_t)OZ_S * L.mp * L.kp * g.batch;
+    L.ea = (int *)(L.sb + (size_t)OZ_S * L.np * L.kp * g.batch);
+    L.eb = L.ea + (size_t)L.mp * g.batch;
+    return L;
+}
+}  // namespace
+
+// operand preparation: exponents and pre-tiled slices of op(A) and op(B) into ws
+int oz_gemm_prepare(const GemmArgs &g, void *ws, cudaStream_t s)
+{
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
+    const OzLayout L = oz_layout(g, ws);
+    const int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
+    fill_int_kernel<<<64, 256, 0, s>>>(L.ea, (long long)(L.mp + L.np) * g.batch, INT_MIN / 2); count_launch();
+    {
+        dim3 gr((L.kp + 31) / 32, (L.mp + 31) / 32, g.batch);
+        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
+                                         (const double *)g.kscale, L.mp, L.ea); count_launch();
+        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
+                                           (const double *)g.kscale, L.mp, L.kp, OZ_BM, L.ea, L.sa); count_launch();
+    }
+    {
+        dim3 gr((L.kp + 31) / 32, (L.np + 31) / 32, g.batch);
+        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
+                                         L.np, L.eb); count_launch();
+        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
+                                           L.np, L.kp, OZ_BN, L.eb, L.sb); count_launch();
+    }
+    return 0;
+}
+
+// the tensor-core product on operands prepared by oz_gemm_prepare(g, ws)
+int oz_gemm_run(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
     if (!ensure_dynamic_smem((const void *)oz_gemm_kernel, OZ_SMEM_BYTES)) return -2;
-    const int kp = (g.k + 15) / 16 * 16;
-    const int mp = (g.m + OZ_BM - 1) / OZ_BM * OZ_BM, np = (g.n + OZ_BN - 1) / OZ_BN * OZ_BN;
-    unsigned char *base = (unsigned char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    __nv_bfloat16 *sa = (__nv_bfloat16 *)base;
-    __nv_bfloat16 *sb = sa + (size_t)OZ_S * mp * kp * g.batch;
-    int *ea = (int *)(sb + (size_t)OZ_S * np * kp * g.batch);
-    int *eb = ea + (size_t)mp * g.batch;
-    const int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
-    fill_int_kernel<<<64, 256, 0, s>>>(ea, (long long)(mp + np) * g.batch, INT_MIN / 2); count_launch();
-    {
-        dim3 gr((kp + 31) / 32, (mp + 31) / 32, g.batch);
-        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                         (const double *)g.kscale, mp, ea); count_launch();
-        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                           (const double *)g.kscale, mp, kp, OZ_BM, ea, sa); count_launch();
-    }
-    {
-        dim3 gr((kp + 31) / 32, (np + 31) / 32, g.batch);
-        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                         np, eb); count_launch();
-        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                           np, kp, OZ_BN, eb, sb); count_launch();
-    }
+    const OzLayout L = oz_layout(g, ws);
     OzArgs a;
-    a.sa = sa; a.sb = sb; a.kblocks = kp / 16;
-    a.m = g.m; a.n = g.n; a.k = g.k; a.batch = g.batch; a.m_pad = mp; a.n_pad = np;
+    a.sa = L.sa; a.sb = L.sb; a.kblocks = L.kp / 16;
+    a.m = g.m; a.n = g.n; a.k = g.k; a.batch = g.batch; a.m_pad = L.mp; a.n_pad = L.np;
     a.triA = g.triA; a.triB = g.triB; a.lowerC = g.lowerC;
-    a.ea = ea; a.eb = eb;
+    a.ea = L.ea; a.eb = L.eb;
     a.C = (double *)g.C; a.ldc = g.ldc; a.sC = g.sC;
     a.Cin = (const double *)g.Cin; a.ldcin = g.ldcin; a.sCin = g.sCin;
     a.alpha = g.alpha; a.beta = g.beta; a.err = err;
+    a.wait_limit = g.wait_limit > 0 ? (unsigned long long)g.wait_limit : OZ_WAIT_LIMIT;
     {
         int ex = 0;
         const double fr = std::frexp(std::fabs(g.alpha), &ex);
@@ -533,6 +567,12 @@ int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     dim3 grid(((g.n + OZ_BN - 1) / OZ_BN) * ((g.m + OZ_BM - 1) / OZ_BM), 1, g.batch);
     oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(a); count_launch();
     return 0;
+}
+
+int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+{
+    int st = oz_gemm_prepare(g, ws, s);
+    return st ? st : oz_gemm_run(g, ws, err, s);
 }
 
 }  // namespace pssd

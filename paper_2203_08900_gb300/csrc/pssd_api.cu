@@ -43,7 +43,9 @@ constexpr double U64 = 1.1102230246251565e-16;  // 2^-53
 
 struct Chunk { char *base; size_t cap; size_t off; bool owned; };   // owned: allocated by the library
 
-struct ProfEvent { cudaEvent_t a, b; int kind; double flops; };
+std::atomic<long long> g_device_allocs{0};   // device allocations (cudaMalloc) made by the library
+
+struct ProfEvent { cudaEvent_t a, b; int kind; double flops, bytes; };
 
 }  // namespace
 
@@ -54,7 +56,7 @@ struct pssd_handle_s {
     int prof = 0;
     std::vector<ProfEvent> events;
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[16] = {0}, prof_flops[16] = {0};
+    double prof_ms[16] = {0}, prof_flops[16] = {0}, prof_bytes[16] = {0};
     long long prof_count[16] = {0};
     int dmode = GM_F64;   // arithmetic of FP64 contractions in the current call (GM_F64 or GM_DF)
     std::vector<pssd_handle_s *> workers;   // pssd_eig_batched: one handle (own stream, workspace) per worker
@@ -64,6 +66,7 @@ struct pssd_handle_s {
     bool user_ws = false;   // chunks[0] is caller-owned memory (pssd_set_workspace); never allocate
     size_t depth = 0;       // bytes of workspace live in the current call (stack discipline)
     size_t peak = 0;        // largest depth reached since creation or pssd_set_workspace
+    long long wait_limit = 0;   // pipeline wait bound of the tensor-core kernels in this call (0 = default)
 };
 
 namespace {
@@ -130,6 +133,7 @@ void *walloc(pssd_handle h, size_t bytes)
     }
     size_t cap = std::max(bytes, size_t(1) << 30);
     void *p = nullptr;
+    g_device_allocs.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaMalloc(&p, cap);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -147,11 +151,11 @@ int *ialloc(pssd_handle h, size_t count) { return (int *)walloc(h, count * sizeo
 // launch accounting and optional per-launch CUDA-event timing
 // ---------------------------------------------------------------------------
 enum Kind { K_DGEMM = 0, K_CHOL_LEAF = 1, K_HBM = 2, K_GEMV = 3, K_JACOBI = 4, K_SGEMM = 5, K_DFGEMM = 6, K_TCGEMM = 7,
-            K_OZGEMM = 8, K_NKIND = 9 };
+            K_OZGEMM = 8, K_OZPREP = 9, K_TCPREP = 10, K_NKIND = 11 };
 static_assert(K_DGEMM == PSSD_KIND_DGEMM && K_CHOL_LEAF == PSSD_KIND_CHOL_LEAF && K_HBM == PSSD_KIND_HBM &&
                   K_GEMV == PSSD_KIND_GEMV && K_JACOBI == PSSD_KIND_JACOBI && K_SGEMM == PSSD_KIND_SGEMM &&
                   K_DFGEMM == PSSD_KIND_DFGEMM && K_TCGEMM == PSSD_KIND_TCGEMM && K_OZGEMM == PSSD_KIND_OZGEMM &&
-                  K_NKIND == PSSD_NKIND,
+                  K_OZPREP == PSSD_KIND_OZPREP && K_TCPREP == PSSD_KIND_TCPREP && K_NKIND == PSSD_NKIND,
               "profiling kinds match the public header");
 
 cudaEvent_t get_event(pssd_handle h)
@@ -162,15 +166,17 @@ cudaEvent_t get_event(pssd_handle h)
     return e;
 }
 
+// one timed region: algorithmic FLOPs (contractions) or algorithmic HBM bytes
+// (memory-bound passes: the bytes the pass must read and write at least)
 struct Timed {
-    pssd_handle h; int kind; double flops; cudaEvent_t a = nullptr, b = nullptr;
-    Timed(pssd_handle h_, int kind_, double flops_, int = 1) : h(h_), kind(kind_), flops(flops_)
+    pssd_handle h; int kind; double flops, bytes; cudaEvent_t a = nullptr, b = nullptr;
+    Timed(pssd_handle h_, int kind_, double flops_, double bytes_ = 0.0) : h(h_), kind(kind_), flops(flops_), bytes(bytes_)
     {
         if (h->prof) { a = get_event(h); b = get_event(h); cudaEventRecord(a, h->stream); }
     }
     ~Timed()
     {
-        if (h->prof) { cudaEventRecord(b, h->stream); h->events.push_back({a, b, kind, flops}); }
+        if (h->prof) { cudaEventRecord(b, h->stream); h->events.push_back({a, b, kind, flops, bytes}); }
     }
 };
 
@@ -183,6 +189,7 @@ void prof_collect(pssd_handle h)
         cudaEventElapsedTime(&ms, e.a, e.b);
         h->prof_ms[e.kind] += ms;
         h->prof_flops[e.kind] += e.flops;
+        h->prof_bytes[e.kind] += e.bytes;
         h->prof_count[e.kind] += 1;
         h->free_events.push_back(e.a);
         h->free_events.push_back(e.b);
@@ -236,6 +243,7 @@ void gemm(pssd_handle h, const GemmArgs &g0)
     if (g0.m <= 0 || g0.n <= 0 || g0.batch <= 0) return;
     GemmArgs g = g0;
     if (g.mode < 0) g.mode = h->dmode;
+    g.wait_limit = h->wait_limit;
     double fl = h->prof ? 2.0 * gemm_macs(g) : 0.0;
     Mark mk = mark(h);
     if (g.mode == GM_OZ && !h->derr) g.mode = GM_DF;   // (no error flag outside a guarded call)
@@ -250,29 +258,39 @@ void gemm(pssd_handle h, const GemmArgs &g0)
         const size_t na = (size_t)g.batch * ra * cla, nb = (size_t)g.batch * rb * clb;
         float *ah = (float *)walloc(h, sizeof(float) * na), *al = (float *)walloc(h, sizeof(float) * na);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * na);
             split_pairs((const double *)g.A, g.lda, g.sA, ra, cla, g.batch, ah, al, h->stream);
         }
         float *bh = ah, *bl = al;
         const bool same = g.B == g.A && rb == ra && clb == cla && g.ldb == g.lda && g.sB == g.sA;
         if (!same) {
             bh = (float *)walloc(h, sizeof(float) * nb); bl = (float *)walloc(h, sizeof(float) * nb);
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * nb);
             split_pairs((const double *)g.B, g.ldb, g.sB, rb, clb, g.batch, bh, bl, h->stream);
         }
         g.lda = cla; g.sA = (long long)ra * cla;
         g.ldb = clb; g.sB = (long long)rb * clb;
         g.A = ah; g.Alo = al; g.B = bh; g.Blo = bl;
     }
+    // operand elements read by the preparation passes (for their HBM byte count)
+    const double opA = (double)g.batch * g.m * g.k, opB = (double)g.batch * g.n * g.k;
     if (g.mode == GM_OZ) {
         void *ws = walloc(h, oz_gemm_workspace_bytes(g));
+        {   // exponent pass (8 B read) + slicing pass (8 B read, 8 slices x 2 B written) per element
+            Timed t(h, K_OZPREP, 0, 32.0 * (opA + opB));
+            oz_gemm_prepare(g, ws, h->stream);
+        }
         Timed t(h, K_OZGEMM, fl);
-        int st = oz_gemm_launch(g, ws, h->derr, h->stream);
+        int st = oz_gemm_run(g, ws, h->derr, h->stream);
         if (st) { h->last_err = "tensor-core FP64 GEMM setup failed"; throw Fail{PSSD_ERR_CUDA}; }
     } else if (g.mode == GM_F32 && h->use_tc && h->derr) {
         void *ws = walloc(h, tc_gemm_workspace_bytes(g));
+        {   // split pass: 4 B read, hi + lo (8 B) written per element
+            Timed t(h, K_TCPREP, 0, 12.0 * (opA + opB));
+            tc_gemm_prepare(g, ws, h->stream);
+        }
         Timed t(h, K_TCGEMM, fl);
-        int st = tc_gemm_launch(g, ws, h->derr, h->stream);
+        int st = tc_gemm_run(g, ws, h->derr, h->stream);
         if (st) { h->last_err = "tensor-core GEMM setup failed"; throw Fail{PSSD_ERR_CUDA}; }
     } else {
         Timed t(h, g.mode == GM_F32 ? K_SGEMM : (g.mode == GM_DF ? K_DFGEMM : K_DGEMM), fl);
@@ -299,7 +317,7 @@ void frob_pair(pssd_handle h, const double *X, long long ldx, const double *Y, l
                double *part, double *d2, double *y2)
 {
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, (X ? 16.0 : 8.0) * m * (double)n);
         frob_diff(X, ldx, Y, ldy, m, n, part, h->stream);
     }
     int nb = frob_blocks(m, n);
@@ -354,7 +372,7 @@ void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, 
         g.B = Rinv + (long long)off * lda + off; g.ldb = lda; g.sB = sR; g.tb = 1; g.triB = TRI_UPPER;
         g.C = tmp; g.ldc = hh; g.sC = sT;
         gemm(h, g);
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 2.0 * sizeof(T) * q * (double)hh * batch);
         for (int z = 0; z < batch; ++z)
             scale_copy<T, T>(tmp + (long long)z * sT, hh, A21 + (long long)z * sA, lda, q, hh, 1.0, h->stream);
     }
@@ -404,7 +422,7 @@ int chol_inv(pssd_handle h, T *A, int n, long long lda, long long sA, int batch,
 template <class T>
 void mirror(pssd_handle h, T *A, long long lda, long long sA, int n, int batch)
 {
-    Timed t(h, K_HBM, 0);
+    Timed t(h, K_HBM, 0, (double)sizeof(T) * n * (double)(n - 1) * batch);
     mirror_lower<T>(A, lda, sA, n, batch, h->stream);
 }
 
@@ -432,7 +450,7 @@ int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, c
     g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
     gemm(h, g);
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, sizeof(T) * 0.5 * m * (double)m * (1 + r));
         shift_copy_lower<T>(G, ld, Z, ld, msz, m, dsh, r, h->stream);   // Z_j = G + c_{2j-1} I
     }
     int bad = chol_inv<T>(h, Z, m, ld, msz, r, Ri, msz, fail_index);   // R_j, R_j^{-1}
@@ -445,7 +463,7 @@ int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, c
     l.C = Z; l.ldc = ld; l.sC = msz; l.lowerC = 1;
     gemm(h, l);
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, sizeof(T) * 0.5 * m * (double)m * (r + 1));
         combine_lower<T>(Z, ld, msz, dsh + r, r, m, Tm, ld, h->stream);   // T = sum a_j Z_j^{-1}
     }
     mirror<T>(h, Tm, ld, 0, m, 1);
@@ -472,14 +490,16 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
     int pass = 0;
     for (;; ++pass) {
+        if (!(ell > 0.0)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        ell = std::min(ell, 1.0);
         int r = (pass == 0 && r_opt > 0) ? r_opt : choose_r_host(ell, tau, 8);
         double c[128], a[64], chat, ell1, ell2;
-        zolo_coeffs_host(ell, r, c, a, &chat, &ell1);
+        if (zolo_coeffs_host(ell, r, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell1 > 1.0) ell1 = 1.0;
         double *X1 = (X == bufA) ? bufB : bufA;
         int st = zolo_step(h, X, X1, m, r, c, a, chat, fail_index);
         if (st) { release(h, mk); return st; }
-        zolo_coeffs_host(ell1, r, c, a, &chat, &ell2);
+        if (zolo_coeffs_host(ell1, r, c, a, &chat, &ell2)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell2 > 1.0) ell2 = 1.0;
         double *X2 = (X1 == bufA) ? bufB : bufA;   // may be X itself on a restart (no longer needed)
         st = zolo_step(h, X1, X2, m, r, c, a, chat, fail_index);
@@ -491,6 +511,7 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
             if (pass < 4) { info->r_used[pass] = r; info->stop_crit[pass] = crit; }
             if (pass < 2) { info->ell[3 * pass] = ell; info->ell[3 * pass + 1] = ell1; info->ell[3 * pass + 2] = ell2; }
             info->passes = pass + 1; info->steps = 2 * (pass + 1); info->restarts = pass;
+            info->iterations = info->steps;
         }
         if (!std::isfinite(crit)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (crit <= std::pow(U64, 1.0 / (2 * r + 1))) { *Yout = X2; release(h, mk); return PSSD_OK; }
@@ -501,11 +522,110 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
     }
 }
 
+// Sigma-DWH (the comparison method of Sec. 6): the Zolotarev step of degree 1
+// -- the dynamically weighted Halley step, Sec. 5.3 -- repeated on the
+// symmetric X0 (|lambda| in [ell, 1]) with the l-update after every step,
+// until ||X_{k+1} - X_k||_F / ||X_{k+1}||_F <= u^{1/3}: the step converges
+// cubically, so the next step's change would be at rounding level.
+int dwh_sign(pssd_handle h, double *X0, int m, double ell, double *bufA, double *bufB, double **Yout,
+             pssd_info *info, int *fail_index)
+{
+    const long long ld = m;
+    Mark mk = mark(h);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
+    double *X = X0;
+    const double tol = std::cbrt(U64);
+    for (int it = 0; it < 30; ++it) {
+        if (!(ell > 0.0)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        ell = std::min(ell, 1.0);
+        double c[2], a[1], chat, ell1;
+        if (zolo_coeffs_host(ell, 1, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        double *Xn = (X == bufA) ? bufB : bufA;
+        int st = zolo_step<double>(h, X, Xn, m, 1, c, a, chat, fail_index);
+        if (st) { release(h, mk); return st; }
+        double d2, y2;
+        frob_pair(h, X, ld, Xn, ld, m, m, part, &d2, &y2);
+        const double crit = std::sqrt(d2 / y2);
+        if (info) {
+            if (it < 6) info->ell[it] = ell;
+            if (it < 4) { info->stop_crit[it] = crit; info->r_used[it] = 1; }
+            info->iterations = info->steps = it + 1; info->passes = 1;
+        }
+        if (!std::isfinite(crit)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        ell = std::min(ell1, 1.0);
+        X = Xn;
+        if (crit <= tol) { *Yout = X; release(h, mk); return PSSD_OK; }
+    }
+    *Yout = X;
+    release(h, mk);
+    return PSSD_ERR_NO_CONVERGENCE;
+}
+
+// Scaled Newton iteration (Eq. NewtonSign) with the suboptimal scaling of Byers
+// and Xu that Sec. 6 compares against: for X0 with |lambda| in [b, a] (here
+// a = 1, b = ell), X_{k+1} = (z_k X_k + (z_k X_k)^{-1})/2 with
+//   z_0 = 1/sqrt(ab),  z_1 = sqrt(2 sqrt(ab)/(a + b)),  z_{k+1} = 1/sqrt((z_k + 1/z_k)/2);
+// after the first step |lambda| lies in [1, (a + b)/(2 sqrt(ab))] and each z_k
+// is the optimal scaling for the interval bound carried forward.  The first
+// inverse comes from the Cholesky factor of M: X0 = K/alpha with K = L^T Sigma L,
+// so X0^{-1} = alpha L^{-1} Sigma L^{-T}; later inverses are (X^2)^{-1} X with the
+// Cholesky factor of the SPD X^2 (condition number at most kappa/4 after the
+// first step).  Stops when the relative change is at most u^{1/2} (quadratic
+// convergence).
+int newton_sign(pssd_handle h, const double *Linv, const double *sig, double alpha, double *X0, int m, double ell,
+                double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index)
+{
+    const long long ld = m, msz = (long long)m * m;
+    Mark mk = mark(h);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
+    double *G = dalloc(h, msz), *Ri = dalloc(h, msz), *Gi = dalloc(h, msz);
+    const double a = 1.0, b = std::min(std::max(ell, 1e-300), 1.0);
+    double z = 1.0 / std::sqrt(a * b);
+    double *X = X0;
+    const double tol = std::sqrt(U64);
+    for (int it = 0; it < 60; ++it) {
+        double *Xn = (X == bufA) ? bufB : bufA;
+        if (it == 0) {   // X1 = (z/2) X0 + (alpha / (2 z)) L^{-1} Sigma L^{-T}   (lower, then mirrored)
+            GemmArgs g; g.m = g.n = g.k = m; g.A = Linv; g.lda = ld; g.triA = TRI_LOWER; g.kscale = sig;
+            g.B = Linv; g.ldb = ld; g.tb = 1; g.triB = TRI_UPPER; g.Cin = X; g.ldcin = ld;
+            g.C = Xn; g.ldc = ld; g.alpha = 0.5 * alpha / z; g.beta = 0.5 * z; g.lowerC = 1;
+            gemm(h, g);
+        } else {
+            GemmArgs g; g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld;
+            g.lowerC = 1;
+            gemm(h, g);                                                   // G = X^2 (lower)
+            if (chol_inv<double>(h, G, m, ld, 0, 1, Ri, 0, fail_index)) { release(h, mk); return PSSD_ERR_NOT_DEFINITE; }
+            GemmArgs l; l.m = l.n = l.k = m; l.A = Ri; l.lda = ld; l.ta = 1; l.triA = TRI_UPPER;
+            l.B = Ri; l.ldb = ld; l.triB = TRI_LOWER; l.C = Gi; l.ldc = ld; l.lowerC = 1;
+            gemm(h, l);                                                   // (X^2)^{-1} = R^{-T} R^{-1}
+            mirror<double>(h, Gi, ld, 0, m, 1);
+            GemmArgs f; f.m = f.n = f.k = m; f.A = Gi; f.lda = ld; f.B = X; f.ldb = ld; f.Cin = X; f.ldcin = ld;
+            f.C = Xn; f.ldc = ld; f.alpha = 0.5 / z; f.beta = 0.5 * z; f.lowerC = 1;
+            gemm(h, f);                                                   // (z X + (X^2)^{-1} X / z) / 2
+        }
+        mirror<double>(h, Xn, ld, 0, m, 1);
+        double d2, y2;
+        frob_pair(h, X, ld, Xn, ld, m, m, part, &d2, &y2);
+        const double crit = std::sqrt(d2 / y2);
+        if (info) {
+            if (it < 4) info->stop_crit[it] = crit;
+            info->iterations = info->steps = it + 1; info->passes = 1;
+        }
+        if (!std::isfinite(crit)) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        X = Xn;
+        if (it > 0 && crit <= tol) { *Yout = X; release(h, mk); return PSSD_OK; }
+        z = (it == 0) ? std::sqrt(2.0 * std::sqrt(a * b) / (a + b)) : 1.0 / std::sqrt(0.5 * (z + 1.0 / z));
+    }
+    *Yout = X;
+    release(h, mk);
+    return PSSD_ERR_NO_CONVERGENCE;
+}
+
 // scaled Zolotarev function (Eq. hatZ), product form, for tracking the image of l
 double zolo_eval_host(double x, double ell, int r)
 {
     double c[128], a[64], chat, l1;
-    zolo_coeffs_host(ell, r, c, a, &chat, &l1);
+    if (zolo_coeffs_host(ell, r, c, a, &chat, &l1)) return NAN;
     double y = chat * x;
     for (int j = 0; j < r; ++j) y *= (x * x + c[2 * j + 1]) / (x * x + c[2 * j]);
     return y;
@@ -522,17 +642,19 @@ int zolo_sign_fp32(pssd_handle h, float *X0, int m, double ell, double tau32, do
     float *X = X0;
     for (int step = 0; step < 8; ++step) {
         double eu = std::max(ell, ell_floor);
+        if (!(eu > 0.0) || !(eu <= 1.0)) return PSSD_ERR_NONFINITE;
         int r = choose_r_host(eu, tau32, 8);
         double c[128], a[64], chat, l1;
-        zolo_coeffs_host(eu, r, c, a, &chat, &l1);
+        if (zolo_coeffs_host(eu, r, c, a, &chat, &l1)) return PSSD_ERR_NONFINITE;
         float *Xn = (X == bufA) ? bufB : bufA;
         int st = zolo_step<float>(h, X, Xn, m, r, c, a, chat, fail_index);
         if (st) return st;
         double en = std::min(zolo_eval_host(ell, eu, r), 1.0);
+        if (!(en > 0.0)) return PSSD_ERR_NONFINITE;
         if (info) {
             if (step < 4) info->r_used[step] = r;
             if (step < 6) info->ell[step] = ell;
-            info->fp32_steps = step + 1; info->steps = step + 1; info->passes = 1;
+            info->fp32_steps = step + 1; info->steps = step + 1; info->passes = 1; info->iterations = step + 1;
         }
         ell = en;
         X = Xn;
@@ -556,7 +678,7 @@ double ns_probe(pssd_handle h, const double *Y, long long ldy, int m, uint64_t s
     double *Om = dalloc(h, (size_t)m * s), *T1 = dalloc(h, (size_t)m * s), *Z = dalloc(h, (size_t)m * s);
     double *part = dalloc(h, 2 * (size_t)frob_blocks(m, s));
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 8.0 * m * s);
         fill_gaussian(Om, s, m, s, seed, h->stream);
     }
     GemmArgs a; a.m = m; a.n = s; a.k = m; a.A = Y; a.lda = ldy; a.B = Om; a.ldb = s; a.C = T1; a.ldc = s;
@@ -603,7 +725,7 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
         gemm(h, g);
         if (symmetric) mirror<double>(h, G, ld, 0, m, 1);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * m);
             add_diag<double>(G, ld, m, 1.0, h->stream);                // G = I - Y^2
         }
         double d2, y2;
@@ -625,7 +747,7 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
         ldc = ld;
     }
     if (cur != Y) {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 16.0 * m * (double)m);
         copy_matrix(cur, ld, Y, ldy, m, m, h->stream);
     }
     if (resid_out) *resid_out = res;
@@ -639,18 +761,18 @@ template <class F>
 double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *dscal, int iters)
 {
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 24.0 * n);
         fill_gaussian(v, n, 1, n, 0x5eedull, h->stream);
         normalize_vec(v, v, n, nullptr, h->stream);
     }
     for (int it = 0; it < iters; ++it) {
         apply(v, w);
-        Timed t(h, K_GEMV, 0);
+        Timed t(h, K_GEMV, 0, 16.0 * n);
         normalize_vec(w, v, n, nullptr, h->stream);
     }
     apply(v, w);
     {
-        Timed t(h, K_GEMV, 0);
+        Timed t(h, K_GEMV, 0, 16.0 * n);
         dot_vec(v, w, n, dscal, h->stream);
     }
     double rq;
@@ -701,7 +823,7 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
     double *Om = dalloc(h, (size_t)m * m);
     double *Yb = dalloc(h, (size_t)m * m);
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 8.0 * m * (double)m);
         fill_gaussian(Om, ld, m, m, seed, h->stream);
     }
     if (p > 0) {   // Y_+ = (I + Y)/2 Omega_+
@@ -766,7 +888,7 @@ double split_backward_error(pssd_handle h, const double *K, const double *U, int
         double *Om = dalloc(h, (size_t)q * s), *T1 = dalloc(h, (size_t)n * s), *T2 = dalloc(h, (size_t)n * s);
         double *T3 = dalloc(h, (size_t)p * s);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 8.0 * q * s);
             fill_gaussian(Om, s, q, s, 0xbac3e77ull, h->stream);
         }
         GemmArgs a; a.m = n; a.n = s; a.k = q; a.A = U + p; a.lda = ld; a.B = Om; a.ldb = s; a.C = T1; a.ldc = s;
@@ -782,6 +904,72 @@ double split_backward_error(pssd_handle h, const double *K, const double *U, int
     frob_pair(h, nullptr, ld, K, ld, n, n, part, &d2, &k2);
     release(h, mk);
     return std::sqrt(e2 / k2);
+}
+
+// Relative commutator ||S H - H S||_F / ||H||_F (Lemma SignProj: the projectors
+// (I +- S)/2 are spectral exactly when S commutes with H).  S is given either
+// explicitly (S != nullptr, ld lds) or as S = A A^T Sigma with A = Q of a split
+// or V of a diagonalisation (A^{-1} = Sigma_hat A^T Sigma and Sigma_hat^2 = I, so
+// S = A Sigma_hat A^{-1} = A A^T Sigma).  exact: forms S H - H S (two n^3
+// products); otherwise a 16-column Gaussian probe, E ||C Omega||_F^2 = 16 ||C||_F^2.
+double comm_resid(pssd_handle h, int n, const double *H, long long ldh, double normH, const double *S,
+                  long long lds, const double *A, long long lda, const double *sig, bool exact)
+{
+    Mark mk = mark(h);
+    const long long nn = (long long)n * n;
+    double d2 = 0, c2 = 0;
+    if (exact) {
+        double *Sm = const_cast<double *>(S);
+        long long ldm = lds;
+        if (!S) {
+            Sm = dalloc(h, nn); ldm = n;
+            GemmArgs g; g.m = g.n = g.k = n; g.A = A; g.lda = lda; g.B = A; g.ldb = lda; g.tb = 1;
+            g.C = Sm; g.ldc = n;
+            gemm(h, g);                                                        // A A^T
+            Timed t(h, K_HBM, 0, 16.0 * nn);
+            scale_columns(Sm, n, n, n, sig, 0, h->stream);                     // (A A^T) Sigma
+        }
+        double *C = dalloc(h, nn);
+        GemmArgs a; a.m = a.n = a.k = n; a.A = Sm; a.lda = ldm; a.B = H; a.ldb = ldh; a.C = C; a.ldc = n;
+        gemm(h, a);                                                            // S H
+        GemmArgs b; b.m = b.n = b.k = n; b.A = H; b.lda = ldh; b.B = Sm; b.ldb = ldm; b.Cin = C; b.ldcin = n;
+        b.C = C; b.ldc = n; b.alpha = -1.0; b.beta = 1.0;
+        gemm(h, b);                                                            // S H - H S
+        double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+        frob_pair(h, nullptr, n, C, n, n, n, part, &d2, &c2);
+    } else {
+        constexpr int s = 16;
+        double *Om = dalloc(h, (size_t)n * s), *HO = dalloc(h, (size_t)n * s), *T = dalloc(h, (size_t)n * s);
+        double *SHO = dalloc(h, (size_t)n * s), *SO = dalloc(h, (size_t)n * s);
+        {
+            Timed t(h, K_HBM, 0, 8.0 * n * s);
+            fill_gaussian(Om, s, n, s, 0xc033e7ull, h->stream);
+        }
+        auto applyS = [&](const double *x, double *y) {   // y = S x  (n x s blocks, ld s)
+            if (S) {
+                GemmArgs g; g.m = n; g.n = s; g.k = n; g.A = S; g.lda = lds; g.B = x; g.ldb = s; g.C = y; g.ldc = s;
+                gemm(h, g);
+            } else {
+                GemmArgs g; g.m = n; g.n = s; g.k = n; g.A = A; g.lda = lda; g.ta = 1; g.B = x; g.ldb = s;
+                g.kscale = sig; g.C = T; g.ldc = s;
+                gemm(h, g);                                                    // A^T Sigma x
+                GemmArgs f; f.m = n; f.n = s; f.k = n; f.A = A; f.lda = lda; f.B = T; f.ldb = s; f.C = y; f.ldc = s;
+                gemm(h, f);                                                    // A (A^T Sigma x)
+            }
+        };
+        GemmArgs g; g.m = n; g.n = s; g.k = n; g.A = H; g.lda = ldh; g.B = Om; g.ldb = s; g.C = HO; g.ldc = s;
+        gemm(h, g);                                                            // H Omega
+        applyS(HO, SHO);                                                       // S H Omega
+        applyS(Om, SO);                                                        // S Omega
+        GemmArgs c; c.m = n; c.n = s; c.k = n; c.A = H; c.lda = ldh; c.B = SO; c.ldb = s; c.Cin = SHO; c.ldcin = s;
+        c.C = SHO; c.ldc = s; c.alpha = -1.0; c.beta = 1.0;
+        gemm(h, c);                                                            // (S H - H S) Omega
+        double *part = dalloc(h, 2 * (size_t)frob_blocks(n, s));
+        frob_pair(h, nullptr, s, SHO, s, n, s, part, &d2, &c2);
+        c2 /= s;
+    }
+    release(h, mk);
+    return normH > 0 ? std::sqrt(c2) / normH : NAN;
 }
 
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
@@ -801,7 +989,7 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
     std::vector<double> dg(m);
     double *dd = dalloc(h, m);
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 16.0 * m);
         get_diag(B, ld, m, dd, h->stream);
     }
     d2h_sync(h, dg.data(), dd, sizeof(double) * m);
@@ -818,7 +1006,7 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
         double *X0 = dalloc(h, msz), *bA = dalloc(h, msz), *bB = dalloc(h, msz);
         double *tmp = dalloc(h, m + 2);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 24.0 * m * (double)m);
             copy_matrix(B, ld, X0, ld, m, m, h->stream);
             add_diag(X0, ld, m, -sigma, h->stream);
             row_abs_sum_max(X0, ld, m, tmp, tmp + m, h->stream);
@@ -836,7 +1024,7 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
             return PSSD_OK;
         }
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * m * (double)m);
             scale_copy(X0, ld, X0, ld, m, m, 1.0 / alpha, h->stream);
         }
         double *Y = nullptr;
@@ -846,7 +1034,7 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
         if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE) { release(h, mk); continue; }
         if (st) { release(h, outer); return st; }
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 8.0 * m);
             trace_partial(Y, ld, m, tmp, h->stream);
         }
         double tr;
@@ -899,9 +1087,11 @@ int validate(int n, const signed char *sigma, const double *H, int ldh)
 }
 
 int front(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, const pssd_opts &o,
-          pssd_info *info, Front &F)
+          pssd_info *info, Front &F, const double *S_in = nullptr, long long lds_in = 0)
 {
     F.n = n;
+    h->wait_limit = o.wait_cycles;
+    if (info) info->method = o.method;
     h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
     h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
     if (info) info->precision = o.precision;
@@ -923,7 +1113,7 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         Mark mk = mark(h);
         double *part = dalloc(h, 2 * (size_t)nb);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
             sym_prepare(H, ldh, F.sig, n, F.M, ld, part, h->stream);
         }
         std::vector<double> hp(2 * (size_t)nb);
@@ -938,13 +1128,31 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
     }
     // a2: L = chol(M), L^{-1}
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
         copy_matrix(F.M, ld, F.L, ld, n, n, h->stream);
     }
     int fi = -1;
     if (chol_inv(h, F.L, n, ld, 0, 1, F.Linv, 0, &fi)) {
         if (info) info->fail_index = fi;
         return PSSD_ERR_NOT_DEFINITE;
+    }
+    if (S_in) {   // a precomputed S = sign(H): K = L^T Sigma L and sign(K) = L^T S L^{-T} (H = L^{-T} K L^T)
+        GemmArgs g; g.m = g.n = g.k = n; g.A = F.L; g.lda = ld; g.ta = 1; g.triA = TRI_UPPER; g.kscale = F.sig;
+        g.B = F.L; g.ldb = ld; g.triB = TRI_LOWER; g.C = F.K; g.ldc = ld; g.lowerC = 1;
+        gemm(h, g);
+        mirror(h, F.K, ld, 0, n, 1);
+        F.Y = dalloc(h, nsz);
+        Mark mk = mark(h);
+        double *T1 = dalloc(h, nsz);
+        GemmArgs a; a.m = a.n = a.k = n; a.A = S_in; a.lda = lds_in; a.B = F.Linv; a.ldb = ld; a.tb = 1;
+        a.triB = TRI_UPPER; a.C = T1; a.ldc = ld;
+        gemm(h, a);                                                      // S L^{-T}
+        GemmArgs b; b.m = b.n = b.k = n; b.A = F.L; b.lda = ld; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = ld;
+        b.C = F.Y; b.ldc = ld; b.lowerC = 1;
+        gemm(h, b);                                                      // L^T S L^{-T} (symmetric; lower, mirrored)
+        mirror(h, F.Y, ld, 0, n, 1);
+        release(h, mk);
+        return PSSD_OK;
     }
     // a3: bounds (reading R5: |lambda(H)| in [lambda_min(M), lambda_max(M)])
     double alpha = o.alpha, beta = o.beta;
@@ -955,14 +1163,14 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         cudaStream_t s = h->stream;
         if (!(alpha > 0.0)) {
             double rq = power_max(h, n, [&](double *x, double *y) {
-                Timed t(h, K_GEMV, 2.0 * n * (double)n);
+                Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);
                 gemv(M, ld, 0, TRI_NONE, n, x, y, tmp, s);
             }, v, w, tmp + 32 * (size_t)n, 60);
             alpha = 1.05 * rq;
         }
         if (!(beta > 0.0)) {
             double rq = power_max(h, n, [&](double *x, double *y) {
-                Timed t(h, K_GEMV, 2.0 * n * (double)n, 3);
+                Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);  // two triangular halves
                 gemv(Li, ld, 0, TRI_LOWER, n, x, u, tmp, s);     // u = L^{-1} x
                 gemv(Li, ld, 1, TRI_UPPER, n, u, y, tmp, s);     // y = L^{-T} u
             }, v, w, tmp + 32 * (size_t)n, 60);
@@ -986,14 +1194,14 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         Mark mk = mark(h);
         float *X32 = talloc<float>(h, nsz), *fA = talloc<float>(h, nsz), *fB = talloc<float>(h, nsz);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 12.0 * n * (double)n);
             scale_copy<double, float>(F.K, ld, X32, ld, n, n, 1.0 / alpha, h->stream);
         }
         float *Y32 = nullptr;
         int st = zolo_sign_fp32(h, X32, n, beta / alpha, 1e-6, 3e-3, fA, fB, &Y32, info, &fi);
         if (st) { if (info) info->fail_index = fi; release(h, mk); return st; }
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 12.0 * n * (double)n);
             scale_copy<float, double>(Y32, ld, F.Y, ld, n, n, 1.0, h->stream);
         }
         release(h, mk);
@@ -1004,11 +1212,17 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
     }
     double *X0 = dalloc(h, nsz), *bA = dalloc(h, nsz), *bB = dalloc(h, nsz);
     {
-        Timed t(h, K_HBM, 0);
+        Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
         scale_copy<double, double>(F.K, ld, X0, ld, n, n, 1.0 / alpha, h->stream);
     }
     int maxr = o.max_restarts < 0 ? 2 : o.max_restarts;
-    int st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi);
+    int st;
+    if (o.method == PSSD_METHOD_DWH)
+        st = dwh_sign(h, X0, n, beta / alpha, bA, bB, &F.Y, info, &fi);
+    else if (o.method == PSSD_METHOD_NEWTON)
+        st = newton_sign(h, F.Linv, F.sig, alpha, X0, n, beta / alpha, bA, bB, &F.Y, info, &fi);
+    else
+        st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi);
     if (st == PSSD_ERR_NOT_DEFINITE && info) info->fail_index = fi;
     return st;
 }
@@ -1028,6 +1242,20 @@ void info_init(pssd_info *info)
     info->s2_resid = -1.0;
     info->jsym_resid = -1.0;
     info->split_backerr = -1.0;
+    info->comm_resid = -1.0;
+}
+
+// options outside their documented ranges (nonzero = invalid)
+int opts_bad(const pssd_opts &o)
+{
+    if (o.r < 0 || o.r > 64) return 1;
+    if (!(o.alpha >= 0.0) || !std::isfinite(o.alpha) || !(o.beta >= 0.0) || !std::isfinite(o.beta)) return 1;
+    if (o.alpha > 0.0 && o.beta > 0.0 && o.beta > o.alpha) return 1;
+    if (o.precision < 0 || o.precision > 2) return 1;
+    if (o.method < 0 || o.method > 2) return 1;
+    if (o.precision == PSSD_MIXED && o.method != PSSD_METHOD_ZOLO) return 1;
+    if (o.wait_cycles < 0 || o.leaf < 0) return 1;
+    return 0;
 }
 
 template <class F>
@@ -1037,6 +1265,7 @@ int guarded(pssd_handle h, pssd_info *info, F body)
     auto t0 = std::chrono::steady_clock::now();
     Mark mk = mark(h);
     int st;
+    h->wait_limit = 0;   // the default bound unless the call's options set one (front())
     int *outer_err = h->derr;
     try {
         if (!outer_err) {
@@ -1051,7 +1280,9 @@ int guarded(pssd_handle h, pssd_info *info, F body)
             int herr = 0;
             cudaMemcpyAsync(&herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
             cudaStreamSynchronize(h->stream);
-            if (herr && st == PSSD_OK) st = PSSD_ERR_TIMEOUT;
+            // a tensor-core kernel that gave up leaves garbage behind it, so the later
+            // steps may fail too; the timeout is the cause that is reported
+            if (herr && st != PSSD_ERR_CUDA) st = PSSD_ERR_TIMEOUT;
         }
     } catch (Fail &f) {
         st = f.code;
@@ -1155,7 +1386,7 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
     if (lds < n) return -7;
     if (S == H) return -6;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision < 0 || o.precision > 2) return -8;
+    if (opts_bad(o)) return -8;
     info_init(info);
     return guarded(h, info, [&]() -> int {
         Front F;
@@ -1175,7 +1406,7 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
             // north star (1): J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
             // Sigma-symmetric S stay Sigma-symmetric), in FP64-accurate arithmetic
             {
-                Timed t(h, K_HBM, 0);
+                Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
                 j_resym(S, lds, F.sig, n, h->stream);
             }
             double res; int its;
@@ -1183,12 +1414,15 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
             if (st2) return st2;
             if (info) info->ns_steps += its;
         }
+        if (info)
+            info->comm_resid = comm_resid(h, n, H, ldh, F.normH, S, lds, nullptr, 0, F.sig,
+                                          (o.flags & PSSD_FLAG_RESIDUALS) != 0);
         if (o.flags & 1) {   // residuals
             double *S2 = dalloc(h, nsz);
             GemmArgs c; c.m = c.n = c.k = n; c.A = S; c.lda = lds; c.B = S; c.ldb = lds; c.C = S2; c.ldc = ld;
             gemm(h, c);
             {
-                Timed t(h, K_HBM, 0);
+                Timed t(h, K_HBM, 0, 16.0 * n);
                 add_diag(S2, ld, n, -1.0, h->stream);
             }
             double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
@@ -1200,25 +1434,31 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
     });
 }
 
-int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *Q, int ldq,
-               double *A11, int lda11, double *A22, int lda22, int *p_out, const pssd_opts *opts, pssd_info *info)
+int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, const double *S_in,
+               int lds_in, double *Q, int ldq, double *A11, int lda11, double *A22, int lda22, int *p_out,
+               const pssd_opts *opts, pssd_info *info)
 {
     if (!h) return -1;
     int v = validate(n, sigma, H, ldh);
     if (v) return v;
-    if (!Q) return -6;
-    if (ldq < n) return -7;
+    if (S_in && lds_in < n) return -7;
+    if (!Q) return -8;
+    if (ldq < n) return -9;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision < 0 || o.precision > 2) return -14;
+    if (opts_bad(o)) return -15;
+    int p0 = 0;
+    for (int i = 0; i < n; ++i) p0 += sigma ? (sigma[i] > 0) : (i < n / 2);
+    if (p0 > 0 && !A11) return -10;
+    if (p0 > 0 && lda11 < p0) return -11;
+    if (n - p0 > 0 && !A22) return -12;
+    if (n - p0 > 0 && lda22 < n - p0) return -13;
     info_init(info);
     return guarded(h, info, [&]() -> int {
         Front F;
-        int st = front(h, n, sigma, H, ldh, o, info, F);
+        int st = front(h, n, sigma, H, ldh, o, info, F, S_in, lds_in);
         if (st) return st;
         const int p = F.p, q = n - p;
         if (p_out) *p_out = p;
-        if (p > 0 && (!A11 || lda11 < p)) return p > 0 && !A11 ? -8 : -9;
-        if (q > 0 && (!A22 || lda22 < q)) return !A22 ? -10 : -11;
         const long long ld = n, nsz = (long long)n * n;
         double *U = dalloc(h, nsz);
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
@@ -1232,11 +1472,11 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
         double *X = dalloc(h, nsz);
         int fi;
         if (p > 0) {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * p * (double)p);
             copy_matrix(Bp, p, Cp, p, p, p, h->stream);
         }
         if (q > 0) {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * q * (double)q);
             scale_copy(Bm, q, Cm, q, q, q, -1.0, h->stream);
         }
         if (p > 0 && p == q) {   // both factors in one batched call
@@ -1270,6 +1510,8 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
         }
         if (info && p > 0 && q > 0)     // ||U_+^T K U_-||_F / ||K||_F (backward error of the split of K ~ H)
             info->split_backerr = split_backward_error(h, F.K, U, n, p, E);
+        if (info)
+            info->comm_resid = comm_resid(h, n, H, ldh, F.normH, nullptr, 0, Q, ldq, F.sig, exact_be);
         return PSSD_OK;
     });
 }
@@ -1316,7 +1558,7 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
             gemm(h, g);
         }
         {
-            Timed t(h, K_HBM, 0, 2);
+            Timed t(h, K_HBM, 0, 32.0 * n * (double)n);
             scale_columns(Vt, ld, n, n, w, 1, h->stream);
             sign_fix_columns(Vt, ld, n, n, h->stream);
         }
@@ -1335,12 +1577,14 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
         h2d(h, dperm, perm.data(), sizeof(int) * n);
         h2d(h, D, hd.data(), sizeof(double) * n);
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
             gather_columns(Vt, ld, V, ldv, n, n, dperm, h->stream);
         }
         cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
         if (info && p > 0 && q > 0)     // ||U_+^T K U_-||_F / ||K||_F
             info->split_backerr = split_backward_error(h, F.K, U, n, p, E);
+        if (info)
+            info->comm_resid = comm_resid(h, n, H, ldh, F.normH, nullptr, 0, V, ldv, F.sig, exact_be);
         return PSSD_OK;
 }
 }  // namespace
@@ -1357,7 +1601,7 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
     if (ldv < n) return -7;
     if (!D) return -8;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision < 0 || o.precision > 2) return -9;
+    if (opts_bad(o)) return -9;
     int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
     info_init(info);
     return guarded(h, info, [&]() -> int { return eig_core(h, n, sigma, H, ldh, V, ldv, D, o, info, leaf); });
@@ -1377,17 +1621,18 @@ int pssd_profile_enable(pssd_handle h, int on)
 int pssd_profile_reset(pssd_handle h)
 {
     if (!h) return -1;
-    for (int i = 0; i < 16; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_count[i] = 0; }
+    for (int i = 0; i < 16; ++i) { h->prof_ms[i] = 0; h->prof_flops[i] = 0; h->prof_bytes[i] = 0; h->prof_count[i] = 0; }
     return PSSD_OK;
 }
 
-int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops)
+int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *launches, double *flops, double *bytes)
 {
     if (!h) return -1;
     if (kind < 0 || kind >= K_NKIND) return -2;
     if (total_ms) *total_ms = h->prof_ms[kind];
     if (launches) *launches = h->prof_count[kind];
     if (flops) *flops = h->prof_flops[kind];
+    if (bytes) *bytes = h->prof_bytes[kind];
     return PSSD_OK;
 }
 
@@ -1435,6 +1680,9 @@ int pssd_workspace_bytes(pssd_handle h, int n, const pssd_opts *opts, size_t *by
 
 // process-wide number of kernels the library has launched (all handles)
 long long pssd_launch_count(pssd_handle h) { return h ? g_launches.load() : -1; }
+
+// process-wide number of device allocations (cudaMalloc calls) the library has made
+long long pssd_device_alloc_count(void) { return g_device_allocs.load(); }
 
 }  // extern "C"
 
@@ -1489,19 +1737,20 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
     if (n > NOALLOC_MAX_N) return PSSD_ERR_NOALLOC_TOO_LARGE;
     void *scratch = nullptr;
     if (noalloc_scratch(&scratch) != PSSD_OK) return PSSD_ERR_CUDA;
-    // a private handle whose only workspace chunk is the scratch array: every
-    // temporary of pssd_sign is carved from it, nothing is allocated
+    // A private handle whose only workspace is the scratch array, marked as
+    // caller-owned: every temporary of pssd_sign is carved from it, and a
+    // temporary that would overflow it stops the call (PSSD_ERR_ALLOC inside,
+    // reported as PSSD_ERR_NOALLOC_TOO_LARGE) instead of allocating.
     pssd_handle_s local;
     local.stream = h->stream;
+    local.user_ws = true;
     local.chunks.push_back({(char *)scratch, NOALLOC_SCRATCH_BYTES, 0, false});
     int st = pssd_sign(&local, n, sigma, H, ldh, S, lds, opts, info);
-    if (local.chunks.size() != 1) {   // cannot happen for n <= NOALLOC_MAX_N (bounded workspace)
-        cudaStreamSynchronize(local.stream);
-        for (size_t i = 1; i < local.chunks.size(); ++i) cudaFree(local.chunks[i].base);
-        local.chunks.resize(1);
-        if (st == PSSD_OK) st = PSSD_ERR_NOALLOC_TOO_LARGE;
-    }
     local.chunks.clear();   // the scratch array is not owned by the local handle
+    if (st == PSSD_ERR_ALLOC) {
+        st = PSSD_ERR_NOALLOC_TOO_LARGE;
+        h->last_err = local.last_err;
+    }
     if (st == PSSD_ERR_CUDA) h->last_err = local.last_err;
     return st;
 }
@@ -1528,7 +1777,7 @@ extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, con
     if (!Hbar) return -9;
     if (ldhb < n) return -10;
     pssd_opts o = opts ? *opts : defaults();
-    if (o.precision < 0 || o.precision > 2) return -11;
+    if (opts_bad(o)) return -11;
     int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
     info_init(info);
     return guarded(h, info, [&]() -> int {
@@ -1545,7 +1794,7 @@ extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, con
         h2d(h, dsh, hsh.data(), sizeof(double) * n);
         double *Vit = dalloc(h, nsz);   // V^{-T} = Sigma V Sigma_hat
         {
-            Timed t(h, K_HBM, 0, 3);
+            Timed t(h, K_HBM, 0, 48.0 * n * (double)n);
             copy_matrix(V, ld, Vit, ld, n, n, h->stream);
             scale_rows(Vit, ld, n, n, dsig, h->stream);
             scale_columns(Vit, ld, n, n, dsh, 0, h->stream);
@@ -1566,7 +1815,7 @@ extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, con
                        "memcpy");
         }
         {
-            Timed t(h, K_HBM, 0);
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
             dk_combine(W, ld, D, dlb, n, T, ld, h->stream);   // T = F o W + diag(lambar)
         }
         GemmArgs c; c.m = c.n = c.k = n; c.A = Vit; c.lda = ld; c.B = T; c.ldb = ld; c.C = W; c.ldc = ld;
@@ -1598,6 +1847,7 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
     if (!H || !ldh) return -5;
     if (!V || !ldv) return -7;
     if (!D) return -9;
+    if (opts && opts_bad(*opts)) return -10;
     for (int i = 0; i < count; ++i) {
         int v = validate(n[i], sigma ? sigma[i] : nullptr, H[i], ldh[i]);
         if (v) return v;

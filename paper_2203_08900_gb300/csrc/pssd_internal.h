@@ -45,6 +45,8 @@ struct GemmArgs {
     // GM_DF only: A, B point to the float high parts and Alo, Blo to the float low parts
     // of the operands, split once by split_pairs(); kscale must be exact in FP32 (e.g. +-1)
     const void *Alo = nullptr, *Blo = nullptr;
+    // tensor-core engines: polls per pipeline wait before the kernel gives up (0 = default)
+    long long wait_limit = 0;
 };
 // x -> (hi, lo) = (fl32(x), fl32(x - hi)) for a batch of rows x cols blocks, written compactly
 void split_pairs(const double *x, long long ld, long long sb, int rows, int cols, int batch, float *hi, float *lo,
@@ -54,10 +56,14 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s);
 // ws: tc_gemm_workspace_bytes(g) bytes of device memory; err: device flag.
 size_t tc_gemm_workspace_bytes(const GemmArgs &g);
 int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
+int tc_gemm_prepare(const GemmArgs &g, void *ws, cudaStream_t s);           // operand split pass only
+int tc_gemm_run(const GemmArgs &g, void *ws, int *err, cudaStream_t s);     // product on prepared operands
 // FP64-accurate GEMM on tcgen05 BF16 tensor cores by exact integer slicing
 // (double data, conventions of GM_F64); ws: oz_gemm_workspace_bytes(g) bytes.
 size_t oz_gemm_workspace_bytes(const GemmArgs &g);
 int oz_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s);
+int oz_gemm_prepare(const GemmArgs &g, void *ws, cudaStream_t s);           // exponent and slicing passes only
+int oz_gemm_run(const GemmArgs &g, void *ws, int *err, cudaStream_t s);     // product on prepared slices
 
 // Cholesky and triangular inverse of the s x s diagonal block at (off, off)
 // of each batch matrix, in one launch: L (lower) in place in A with zeros

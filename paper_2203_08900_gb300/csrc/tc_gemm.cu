@@ -21,8 +21,9 @@
 //     stage with tcgen05.commit;
 //   * warps 0-7 wait for the final commit and write C (warp w: TMEM lanes
 //     32 (w % 4) .., i.e. tile rows, and columns 128 (w / 4) ..).
-// Every mbarrier wait is bounded: on timeout the kernel sets *err, skips the
-// remaining work, frees its TMEM and returns.
+// Every pipeline mbarrier wait is bounded by the caller's limit: on timeout the
+// kernel sets *err, skips the remaining work, waits (under a fixed, longer
+// bound) for its own bulk copies and MMAs in flight, frees its TMEM and returns.
 #include <cuda_runtime.h>
 
 #include "pssd_internal.h"
@@ -37,7 +38,7 @@ constexpr int TC_A_BYTES = 2 * TC_BM * TC_BK * 4;      // hi + lo, 16 KB
 constexpr int TC_B_BYTES = 2 * TC_BN * TC_BK * 4;      // hi + lo, 32 KB
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
-constexpr unsigned long long TC_WAIT_LIMIT = 1ull << 26;
+constexpr unsigned long long TC_WAIT_LIMIT = 1ull << 26;   // default pipeline bound and the drain bound
 constexpr int TC_EPI_WARPS = 8;                        // warp w: lanes 32 (w % 4) .., columns 128 (w / 4) ..
 constexpr int TC_ECOLS = TC_BN / (TC_EPI_WARPS / 4);
 constexpr int TC_PRODUCER_WARP = TC_EPI_WARPS, TC_MMA_WARP = TC_EPI_WARPS + 1;
@@ -55,6 +56,7 @@ struct TcArgs {
     const float *Cin; long long ldcin, sCin;
     float alpha, beta;
     int *err;
+    unsigned long long wait_limit;             // polls per pipeline wait before giving up
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -73,9 +75,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 }
 
 // bounded wait for the phase with the given parity; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit)
 {
-    for (unsigned long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (unsigned long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\n"
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const float *srcb = g.b + (((long long)z * (g.n_pad / TC_BN) + tn) * g.kblocks + kb0) * (TC_B_BYTES / 4);
             for (int q = 0; q < nkb; ++q) {
                 const int s = q % TC_STAGES;
-                if (q >= TC_STAGES && !mbar_wait(b_empty + 8 * s, (uint32_t)(((q / TC_STAGES) - 1) & 1))) {
+                if (q >= TC_STAGES && !mbar_wait(b_empty + 8 * s, (uint32_t)(((q / TC_STAGES) - 1) & 1), g.wait_limit)) {
                     s_abort = 1; atomicExch(g.err, 1); break;
                 }
                 if (s_abort) break;
@@ -201,11 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         }
     } else if (warp == TC_MMA_WARP) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0 && nkb > 0) {
+        if (lane == 0) {
             bool ok = true;
             for (int q = 0; q < nkb; ++q) {
                 const int s = q % TC_STAGES;
-                if (!mbar_wait(b_full + 8 * s, (uint32_t)((q / TC_STAGES) & 1))) { ok = false; break; }
+                if (!mbar_wait(b_full + 8 * s, (uint32_t)((q / TC_STAGES) & 1), g.wait_limit)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = smem_u32(smem + s * TC_STAGE_BYTES);
                 const uint32_t ah = st, al = st + TC_A_BYTES / 2;
@@ -219,18 +221,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 mma_commit(b_empty + 8 * s);                   // stage s is free when these MMAs retire
             }
-            if (ok) mma_commit(b_done);
-            else { s_abort = 1; atomicExch(g.err, 2); }
-            if (s_abort) {   // let the MMAs already issued retire before TMEM and the stages go away
-                mma_commit(b_drain);
-                mbar_wait(b_drain, 0u);
+            if (nkb > 0) {
+                if (ok) mma_commit(b_done);
+                else { s_abort = 1; atomicExch(g.err, 2); }
             }
+            // Every MMA issued has retired before TMEM and the stages go away, whatever
+            // the other roles did (an epilogue warp that gave up no longer waits for them).
+            mma_commit(b_drain);
+            mbar_wait(b_drain, 0u, TC_WAIT_LIMIT);
         }
     } else {
         // ---------------- epilogue warps ----------------
         const int quad = warp & 3, c0 = (warp >> 2) * TC_ECOLS;
         bool have = nkb > 0;
-        if (have && !mbar_wait(b_done, 0u)) { have = false; atomicExch(g.err, 3); }
+        if (have && !mbar_wait(b_done, 0u, g.wait_limit)) { have = false; atomicExch(g.err, 3); }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int i = i0 + quad * 32 + lane;
         float *C = g.C + (long long)z * g.sC + (long long)i * g.ldc;
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     __syncthreads();
     if (s_abort && tid == 32 * TC_PRODUCER_WARP) {   // producer lane: let the last copies issued land
         for (int q = max(0, s_issued - TC_STAGES); q < s_issued; ++q)
-            mbar_wait(b_full + 8 * (q % TC_STAGES), (uint32_t)((q / TC_STAGES) & 1));
+            mbar_wait(b_full + 8 * (q % TC_STAGES), (uint32_t)((q / TC_STAGES) & 1), TC_WAIT_LIMIT);
     }
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
@@ -343,15 +347,22 @@ size_t tc_gemm_workspace_bytes(const GemmArgs &g)
     return (size_t)(2 * (mp + np) * kp * g.batch) * sizeof(float) + 1024;
 }
 
-// ws: device workspace of tc_gemm_workspace_bytes(g) bytes; err: device int (0 on entry)
-int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+namespace {
+void tc_layout(const GemmArgs &g, void *ws, int &kp, int &mp, int &np, float *&ta, float *&tb)
+{
+    kp = (g.k + 15) / 16 * 16;
+    mp = (g.m + TC_BM - 1) / TC_BM * TC_BM; np = (g.n + TC_BN - 1) / TC_BN * TC_BN;
+    float *base = (float *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    ta = base; tb = ta + (size_t)2 * mp * kp * g.batch;
+}
+}  // namespace
+
+// operand preparation: masked, scaled, K-major tf32 hi/lo tiles of op(A), op(B) into ws
+int tc_gemm_prepare(const GemmArgs &g, void *ws, cudaStream_t s)
 {
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
-    if (!ensure_dynamic_smem((const void *)tc_gemm_kernel, TC_SMEM_BYTES)) return -2;
-    const int kp = (g.k + 15) / 16 * 16;
-    const int mp = (g.m + TC_BM - 1) / TC_BM * TC_BM, np = (g.n + TC_BN - 1) / TC_BN * TC_BN;
-    float *base = (float *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    float *ta = base, *tb = ta + (size_t)2 * mp * kp * g.batch;
+    int kp, mp, np; float *ta, *tb;
+    tc_layout(g, ws, kp, mp, np, ta, tb);
     {   // A: rows i of op(A), K-major
         dim3 grid((kp + 31) / 32, (mp + 31) / 32, g.batch);
         tf32_split_kernel<<<grid, 256, 0, s>>>((const float *)g.A, g.lda, g.sA, g.ta, g.m, g.k, kp, mp, TC_BM,
@@ -363,6 +374,16 @@ int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
         tf32_split_kernel<<<grid, 256, 0, s>>>((const float *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, kp, np, TC_BN,
                                                triB, nullptr, tb); count_launch();
     }
+    return 0;
+}
+
+// the tensor-core product on operands prepared by tc_gemm_prepare(g, ws); err: device int (0 on entry)
+int tc_gemm_run(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+{
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return 0;
+    if (!ensure_dynamic_smem((const void *)tc_gemm_kernel, TC_SMEM_BYTES)) return -2;
+    int kp, mp, np; float *ta, *tb;
+    tc_layout(g, ws, kp, mp, np, ta, tb);
     TcArgs a;
     a.a = ta; a.b = tb; a.kblocks = kp / 16;
     a.m = g.m; a.n = g.n; a.k = g.k; a.batch = g.batch; a.m_pad = mp; a.n_pad = np;
@@ -371,9 +392,17 @@ int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
     a.Cin = (const float *)g.Cin; a.ldcin = g.ldcin; a.sCin = g.sCin;
     a.alpha = (float)g.alpha; a.beta = (float)g.beta;
     a.err = err;
+    a.wait_limit = g.wait_limit > 0 ? (unsigned long long)g.wait_limit : TC_WAIT_LIMIT;
     dim3 grid(((g.n + TC_BN - 1) / TC_BN) * ((g.m + TC_BM - 1) / TC_BM), 1, g.batch);
     tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(a); count_launch();
     return 0;
+}
+
+// ws: device workspace of tc_gemm_workspace_bytes(g) bytes; err: device int (0 on entry)
+int tc_gemm_launch(const GemmArgs &g, void *ws, int *err, cudaStream_t s)
+{
+    int st = tc_gemm_prepare(g, ws, s);
+    return st ? st : tc_gemm_run(g, ws, err, s);
 }
 
 }  // namespace pssd

@@ -49,6 +49,24 @@ def test_choose_r_matches_oracle(P):
         assert P.choose_r(1 / kap, 2.0 ** -24) == O.choose_r(1 / kap, 2.0 ** -24)
 
 
+@pytest.mark.parametrize("tau", [1e-15, 1e-6])
+def test_library_choose_r_is_minimal(P, tau):
+    """The library's rule (reading R3 of Sec. 5.3) against the product form of
+    Eq. (hatZ) evaluated here: two steps of degree r reach [1 - tau, 1] and
+    two steps of degree r - 1 do not."""
+    for kappa in [10, 1e2, 1e3, 1e4, 1e8, 1e12, 1e16]:
+        ell = 1.0 / kappa
+        r = P.choose_r(ell, tau)
+
+        def ell2(rr):
+            l1 = min(float(O.zolo_eval(ell, ell, rr)), 1.0)
+            return min(float(O.zolo_eval(l1, l1, rr)), 1.0)
+
+        assert 1.0 - ell2(r) <= tau
+        if r > 1:
+            assert 1.0 - ell2(r - 1) > tau
+
+
 def test_argument_errors(P):
     L = P.lib()
     c = (ctypes.c_double * 4)(); a = (ctypes.c_double * 2)(); x = ctypes.c_double(); y = ctypes.c_double()
@@ -59,3 +77,31 @@ def test_argument_errors(P):
     assert L.pssd_status_string(1).decode().startswith("Sigma")
     # null handle is rejected before any device work
     assert L.pssd_sign(None, 4, None, None, 4, None, 4, None, None) == -1
+
+
+def test_option_ranges_are_argument_errors(P):
+    """Options outside their ranges are rejected before any device work (the
+    pointers below are never dereferenced): r outside [0, 64] (the
+    coefficient routine's range), beta > alpha, an unknown precision or
+    method, a non-Zolotarev method in mixed precision, a negative wait bound."""
+    L = P.lib()
+    h = ctypes.c_void_p()
+    assert L.pssd_create(ctypes.byref(h), None) == 0
+    fake = ctypes.c_void_p(0x1000)      # H
+    out = ctypes.c_void_p(0x2000)       # outputs (distinct from H)
+    info = P.Info()
+    bad = [dict(r=65), dict(r=-1), dict(alpha=1.0, beta=2.0), dict(alpha=-1.0), dict(precision=3),
+           dict(method=3), dict(precision=P.PSSD_MIXED, method=P.METHOD_DWH), dict(wait_cycles=-5)]
+    for kw in bad:
+        o = P._opts(**kw)
+        assert L.pssd_sign(h, 4, None, fake, 4, out, 4, ctypes.byref(o), ctypes.byref(info)) == -8, kw
+        assert L.pssd_eig(h, 4, None, fake, 4, out, 4, out, ctypes.byref(o), ctypes.byref(info)) == -9, kw
+        assert L.pssd_split(h, 4, None, fake, 4, None, 4, out, 4, out, 2, out, 2, None, ctypes.byref(o),
+                            ctypes.byref(info)) == -15, kw
+    # a split whose precomputed S has too small a leading dimension, and missing blocks
+    o = P._opts()
+    assert L.pssd_split(h, 4, None, fake, 4, out, 3, out, 4, out, 2, out, 2, None, ctypes.byref(o),
+                        ctypes.byref(info)) == -7
+    assert L.pssd_split(h, 4, None, fake, 4, None, 4, out, 4, None, 2, out, 2, None, ctypes.byref(o),
+                        ctypes.byref(info)) == -10
+    assert L.pssd_destroy(h) == 0

@@ -1,0 +1,72 @@
+"""The comparison iterations of Sec. 6 on the library's kernels (Sigma-DWH and
+scaled Newton, pssd_opts.method), against the oracle's definition-level sign
+and the oracle's own versions of the same iterations (Eq. ZoloIt2 with r = 1;
+Eq. NewtonSign with the Byers-Xu scaling)."""
+import numpy as np
+import pytest
+import torch
+
+import casida_inputs as G
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2203_08900_gb300 import build as b
+    b.build()
+    import paper_2203_08900_gb300 as P
+    P.lib()
+    return P
+
+
+def _dev(H):
+    return torch.from_numpy(np.ascontiguousarray(H)).cuda()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64e"])
+@pytest.mark.parametrize("method", ["dwh", "newton"])
+@pytest.mark.parametrize("case", ["casida_log_k97", "example1_1e2", "example1_1e8"])
+def test_methods_match_the_definition(P, precision, method, case):
+    if case == "casida_log_k97":
+        A, _, _ = G.casida(97, ("loguniform", 1e-2, 1e2), seed=197)        # n = 194, kappa ~ 1e4
+        sig = None
+        sigf = None
+    else:
+        kappa = {"example1_1e2": 1e2, "example1_1e8": 1e8}[case]
+        A, sig = G.example1(120, kappa, seed=5)
+        sigf = sig.astype(float)
+    n = A.shape[0]
+    alpha, beta = O.estimate_bounds(A, sigf)
+    prec = {"fp64": P.PSSD_FP64, "fp64e": P.PSSD_FP64_EMULATED}[precision]
+    m = {"dwh": P.METHOD_DWH, "newton": P.METHOD_NEWTON}[method]
+    S, info = P.sign(_dev(A), sigma=sig, precision=prec, method=m, alpha=alpha, beta=beta)
+    S = S.cpu().numpy()
+    Sd = O.sign_def(A, sigf)
+    nrm2 = max(1.0, np.linalg.norm(Sd, 2))
+    assert info["method"] == m
+    # the congruence form keeps the library at the accuracy of the Zolotarev path
+    assert np.linalg.norm(S - Sd) <= 1e-11 * np.linalg.norm(Sd) * nrm2
+    assert np.linalg.norm(S @ S - np.eye(n)) <= 1e-12 * n * nrm2 ** 2
+    assert 0 <= info["comm_resid"] <= 1e-11 * nrm2
+    # iteration count of the oracle's literal version of the same iteration (same bounds);
+    # the stopping quantity is measured in different bases (X_k vs K_k), so allow one step
+    if method == "dwh":
+        if case != "example1_1e8":   # the oracle's inverse form is not accurate there (reading R6)
+            _, oi = O.dwh_sign_alg(A, sigf, alpha=alpha, beta=beta)
+            assert abs(info["iterations"] - oi["iterations"]) <= 1
+    else:
+        _, oi = O.newton_sign_scaled(A, sigf, alpha=alpha, beta=beta)
+        assert abs(info["iterations"] - oi["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("method", ["dwh", "newton"])
+def test_methods_drive_the_split(P, method):
+    H, _, _ = G.casida(80, ("uniform", 0.1, 100.0), seed=81)
+    m = {"dwh": P.METHOD_DWH, "newton": P.METHOD_NEWTON}[method]
+    Q, A11, A22, p, info = P.split(_dev(H), method=m, flags=P.FLAG_RESIDUALS)
+    lam, _ = O.eig_def(H)
+    ev = np.sort(np.linalg.eigvalsh(A11.cpu().numpy()))
+    assert np.max(np.abs(ev - lam[:p])) <= 1e-10 * np.max(np.abs(lam))
+    assert 0 <= info["split_backerr"] <= 1e-12
