@@ -283,6 +283,48 @@ def sign_def(H, sigma=None):
     return (V @ V.T) * s[None, :]
 
 
+def casida_eig_def(A, B):
+    """Definition-level eigendecomposition of the Casida matrix
+    H = [[A, B], [-B, -A]] (Eq. Casida) from its k x k blocks.
+
+    With T = [[I, I], [I, -I]]/sqrt 2, T H T = [[0, R], [P, 0]] (P = A + B,
+    R = A - B).  An eigenvector [x; y] for lambda satisfies R y = lambda x,
+    P x = lambda y; with P = L L^T (scalar Cholesky) and x = L^{-T} z this is
+    L^T R L z = lambda^2 z (the k x k reduction P^{1/2} R P^{1/2} up to
+    similarity), y = L z / lambda.  Jacobi gives omega^2 and z; the
+    eigenvalues are +-omega and v = T [L^{-T} z; +-L z/omega] sqrt(omega/2)
+    has v^T Sigma v = +-1 (Eq. VSigmaOrth).
+    Returns (lam, V) in the output convention."""
+    A = np.asarray(A, dtype=np.float64); B = np.asarray(B, dtype=np.float64)
+    k = A.shape[0]
+    P = 0.5 * ((A + B) + (A + B).T)
+    R = 0.5 * ((A - B) + (A - B).T)
+    L = cholesky(P)
+    W = L.T @ R @ L
+    w2, Z = jacobi_eigh(0.5 * (W + W.T))
+    if not w2[0] > 0:
+        raise NotDefinite("A - B is not positive definite")
+    om = np.sqrt(w2)
+    X = lu_solve(L.T, Z)                       # L^{-T} z
+    Y = (L @ Z) / om[None, :]                  # L z / omega
+    c = np.sqrt(om / 2.0)[None, :]
+    Vp = np.vstack([X + Y, X - Y]) / math.sqrt(2.0) * c     # T [X; Y]
+    Vm = np.vstack([X - Y, X + Y]) / math.sqrt(2.0) * c     # T [X; -Y]
+    lam = np.r_[om, -om]
+    V = np.hstack([Vp, Vm])
+    lam, V = _order(lam, V)
+    return lam, _sign_fix_columns(V)
+
+
+def casida_sign_def(A, B):
+    """sign(H) of the Casida matrix from casida_eig_def: S = V V^T Sigma
+    (as sign_def, Eq. signDef with V^{-1} = Sigma_hat V^T Sigma)."""
+    k = A.shape[0]
+    _, V = casida_eig_def(A, B)
+    s = np.r_[np.ones(k), -np.ones(k)]
+    return (V @ V.T) * s[None, :]
+
+
 # --------------------------------------------------------------------------
 # algorithm layer: Alg. 8 (hyperbolic Zolo-PD), Alg. 7, Alg. 3
 # --------------------------------------------------------------------------
