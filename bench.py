@@ -469,6 +469,34 @@ def main():
         if "plain_fp64" in line and "fp64_emulated" in line:
             line["fp64_emulated"]["speedup_vs_plain_fp64"] = (line["plain_fp64"]["s_per_solve"]
                                                               / line["fp64_emulated"]["s_per_solve"])
+        # the structure-aware split of the same H from its blocks A, B (k x k polar factor of
+        # C = L_P^T L_R), FP64-emulated and plain FP64
+        Ab = H[:k, :k].contiguous(); Bb = H[:k, k:].contiguous()
+        for name in ("fp64e", "fp64"):
+            reps = max(1, min(3, args.steps))
+            P.casida_split(Ab, Bb, handle=h, precision=PREC[name])      # warm-up
+            torch.cuda.synchronize()
+            h.profile(True); h.profile_reset()
+            g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(reps):
+                Qc, A11c, A22c, _, infoc = P.casida_split(Ab, Bb, handle=h, precision=PREC[name])
+            g1.record(stream)
+            torch.cuda.synchronize()
+            h.profile(False)
+            tc = g0.elapsed_time(g1) / 1e3 / reps
+            kc = {P.KIND_NAMES[i]: h.profile_read(i) for i in range(len(P.KIND_NAMES))}
+            tab = kernel_table(kc, tc * reps, reps, peaks)
+            accc = split_accuracy(P, torch, H, Qc, p, dev)
+            accc.update({"split_backerr_K": infoc["split_backerr"], "comm_rel_split_lib": infoc["comm_resid"]})
+            entry = {"s_per_solve": tc, "timed_solves": reps, "accuracy": accc,
+                     "r_per_pass": infoc["r_used"][:infoc["passes"]], "kernels": tab,
+                     "note": "pssd_casida_split on the blocks A, B of the same H; k x k work"}
+            if "plain_fp64" in line:
+                entry["speedup_vs_plain_fp64_nxn"] = line["plain_fp64"]["s_per_solve"] / tc
+            line["structure_aware_" + ("fp64e" if name == "fp64e" else "fp64")] = entry
+            del Qc, A11c, A22c
+        del Ab, Bb
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(n)
     if rank == 0:

@@ -279,6 +279,39 @@ int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *
                   const pssd_opts *opts, pssd_info *info);
 
 /*
+ * Structure-aware variants for the Casida form (Eq. Casida): they operate on the
+ * blocks A and B directly (the direction named in Sec. 7) and return what
+ * pssd_sign / pssd_split / pssd_eig return for H = [[A, B], [-B, -A]] with
+ * sigma = NULL (n = 2k), in the same layouts and conventions.
+ *
+ * With T = [[I, I], [I, -I]]/sqrt 2, T H T = [[0, R], [P, 0]] (P = A + B,
+ * R = A - B, both SPD exactly when H is definite).  With P = L_P L_P^T,
+ * R = L_R L_R^T the congruence form of the definite case becomes
+ * [[0, C], [C^T, 0]] with the k x k matrix C = L_P^T L_R, whose sign is built from
+ * the orthogonal polar factor U of C: the two-step Zolotarev iteration of Alg. 8
+ * (same coefficients, stopping test and restarts) acts on C alone, every shifted
+ * matrix C_k^T C_k + c I is SPD, and every product is k x k -- about a sixth of
+ * the n x n path's work.  The eigenvalues of H are +-sigma_i(C), and the full
+ * diagonalisation needs one k x k symmetric divide-and-conquer (Alg. 2) of
+ * H_C = U^T C instead of a split of H and two of them.
+ *   k          order of the blocks (n = 2k <= PSSD_MAX_N)
+ *   A, B       device, k x k, symmetric (relative defect at most 1e-12), leading
+ *              dimensions lda, ldb >= k
+ *   precision  PSSD_FP64 or PSSD_FP64_EMULATED; method PSSD_METHOD_ZOLO
+ * Outputs (device): S or Q (2k x 2k, ld >= 2k), A11 and A22 (k x k, A22 = -A11),
+ * V (2k x 2k) and D (2k) exactly as for the n x n entry points.
+ * info->split_backerr is ||U_+^T K U_-||_F / ||K||_F of this congruence form,
+ * ||U^T C - C^T U||_F / (2 sqrt 2 ||C||_F); info->comm_resid as for the n x n calls.
+ */
+int pssd_casida_sign(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *S,
+                     int lds, const pssd_opts *opts, pssd_info *info);
+int pssd_casida_split(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *Q,
+                      int ldq, double *A11, int lda11, double *A22, int lda22, const pssd_opts *opts,
+                      pssd_info *info);
+int pssd_casida_eig(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *V,
+                    int ldv, double *D, const pssd_opts *opts, pssd_info *info);
+
+/*
  * Allocation-free pssd_sign for small problems (the paper has no counterpart;
  * this entry point exists for callers of the library).
  *

@@ -68,7 +68,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
-           "pssd_device_alloc_count"]
+           "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -112,6 +112,11 @@ def lib():
     L.pssd_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp, dp]
     L.pssd_launch_count.argtypes = [vp]
     L.pssd_launch_count.restype = ctypes.c_longlong
+    cas = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int]
+    L.pssd_casida_sign.argtypes = cas + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_casida_split.argtypes = cas + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
+                                          ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_casida_eig.argtypes = cas + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_device_alloc_count.argtypes = []
     L.pssd_device_alloc_count.restype = ctypes.c_longlong
     L.pssd_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
@@ -328,6 +333,64 @@ def eig(H, sigma=None, handle=None, **kw):
     o = _opts(**kw)
     st = lib().pssd_eig(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(V.data_ptr()),
                         V.stride(0), ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return D, V, info.as_dict()
+
+
+def _check_block(X, k=None):
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+            and X.shape[0] == X.shape[1] and X.stride(1) == 1):
+        raise ValueError("A and B must be square row-major float64 CUDA tensors")
+    if k is not None and X.shape[0] != k:
+        raise ValueError("A and B must have the same order")
+    return X.shape[0], X.stride(0)
+
+
+def casida_sign(A, B, handle=None, **kw):
+    """sign(H) of the Casida matrix H = [[A, B], [-B, -A]] by the structure-aware
+    k x k iteration (polar factor of C = L_P^T L_R).  Returns (S, info)."""
+    k, lda = _check_block(A)
+    _, ldb = _check_block(B, k)
+    h = _handle(handle)
+    S = torch.empty(2 * k, 2 * k, dtype=A.dtype, device=A.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_casida_sign(h._h, k, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
+                                ctypes.c_void_p(S.data_ptr()), S.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return S, info.as_dict()
+
+
+def casida_split(A, B, handle=None, **kw):
+    """Structure-aware split of the Casida H.  Returns (Q, A11, A22, k, info)."""
+    k, lda = _check_block(A)
+    _, ldb = _check_block(B, k)
+    h = _handle(handle)
+    Q = torch.empty(2 * k, 2 * k, dtype=A.dtype, device=A.device)
+    A11 = torch.empty(k, k, dtype=A.dtype, device=A.device)
+    A22 = torch.empty(k, k, dtype=A.dtype, device=A.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_casida_split(h._h, k, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
+                                 ctypes.c_void_p(Q.data_ptr()), Q.stride(0), ctypes.c_void_p(A11.data_ptr()),
+                                 A11.stride(0), ctypes.c_void_p(A22.data_ptr()), A22.stride(0), ctypes.byref(o),
+                                 ctypes.byref(info))
+    h._check(st)
+    return Q, A11, A22, k, info.as_dict()
+
+
+def casida_eig(A, B, handle=None, **kw):
+    """Structure-aware full diagonalisation of the Casida H.  Returns (D, V, info)."""
+    k, lda = _check_block(A)
+    _, ldb = _check_block(B, k)
+    h = _handle(handle)
+    V = torch.empty(2 * k, 2 * k, dtype=A.dtype, device=A.device)
+    D = torch.empty(2 * k, dtype=A.dtype, device=A.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_casida_eig(h._h, k, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
+                               ctypes.c_void_p(V.data_ptr()), V.stride(0), ctypes.c_void_p(D.data_ptr()),
+                               ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return D, V, info.as_dict()
 

@@ -8,6 +8,7 @@
 // The HBM-bound passes (symmetrisation, mirror, shift, combine, norms) use
 // 32x32 shared-memory transposes so that both the row and the column access
 // are coalesced.
+#include <algorithm>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -372,6 +373,119 @@ void sym_prepare(const double *H, long long ldh, const double *sig, int n, doubl
 {
     int t = (n + TT - 1) / TT;
     sym_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(H, ldh, sig, n, M, ldm, partials); count_launch();
+}
+
+// Casida blocks (Eq. Casida): P = sym(A + B), R = sym(A - B) over 32x32 tile pairs;
+// partials[2 b] = squared symmetry defects ||A - A^T||^2 + ||B - B^T||^2 of the tile pair,
+// partials[2 b + 1] = its share of ||H||_F^2 = 2 (||A||_F^2 + ||B||_F^2).
+__global__ void __launch_bounds__(256) casida_prepare_kernel(const double *A, long long lda, const double *B,
+                                                             long long ldb, int k, double *P, double *R,
+                                                             long long ldp, double *partials)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    const int blin = blockIdx.y * gridDim.x + blockIdx.x;
+    __shared__ double Ta[TT][TT + 1], Tb[TT][TT + 1], Ua[TT][TT + 1], Ub[TT][TT + 1];
+    __shared__ double red[2][256];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double dsum = 0.0, nsum = 0.0;
+    if (bi >= bj) {
+        for (int yy = ty; yy < TT; yy += 8) {
+            int i = bi * TT + yy, j = bj * TT + tx;
+            bool in = i < k && j < k;
+            Ta[yy][tx] = in ? A[(long long)i * lda + j] : 0.0;
+            Tb[yy][tx] = in ? B[(long long)i * ldb + j] : 0.0;
+            int i2 = bj * TT + yy, j2 = bi * TT + tx;
+            bool in2 = i2 < k && j2 < k;
+            Ua[yy][tx] = in2 ? A[(long long)i2 * lda + j2] : 0.0;
+            Ub[yy][tx] = in2 ? B[(long long)i2 * ldb + j2] : 0.0;
+        }
+        __syncthreads();
+        for (int yy = ty; yy < TT; yy += 8) {
+            int i = bi * TT + yy, j = bj * TT + tx;
+            double a = Ta[yy][tx], at = Ua[tx][yy], b = Tb[yy][tx], bt = Ub[tx][yy];   // (i,j) and (j,i)
+            if (i < k && j < k) {
+                double sa = 0.5 * (a + at), sb = 0.5 * (b + bt);
+                P[(long long)i * ldp + j] = sa + sb;
+                R[(long long)i * ldp + j] = sa - sb;
+                double da = a - at, db = b - bt;
+                if (bi == bj) { dsum += da * da + db * db; nsum += 2.0 * (a * a + b * b); }
+                else { dsum += 2.0 * (da * da + db * db); nsum += 2.0 * (a * a + at * at + b * b + bt * bt); }
+            }
+            int i2 = bj * TT + yy, j2 = bi * TT + tx;
+            if (bi != bj && i2 < k && j2 < k) {
+                double sa = 0.5 * (Ua[yy][tx] + Ta[tx][yy]), sb = 0.5 * (Ub[yy][tx] + Tb[tx][yy]);
+                P[(long long)i2 * ldp + j2] = sa + sb;
+                R[(long long)i2 * ldp + j2] = sa - sb;
+            }
+        }
+    }
+    red[0][threadIdx.x] = dsum; red[1][threadIdx.x] = nsum;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + st];
+            red[1][threadIdx.x] += red[1][threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { partials[2 * blin] = red[0][0]; partials[2 * blin + 1] = red[1][0]; }
+}
+
+void casida_prepare(const double *A, long long lda, const double *B, long long ldb, int k, double *P, double *R,
+                    long long ldp, double *partials, cudaStream_t s)
+{
+    int t = (k + TT - 1) / TT;
+    casida_prepare_kernel<<<dim3(t, t), 256, 0, s>>>(A, lda, B, ldb, k, P, R, ldp, partials); count_launch();
+}
+
+// The orthogonal change of basis T = [[I, I], [I, -I]] / sqrt 2 applied to a pair of k x m
+// blocks: top = c (sx X + sy Y), bottom = c (sx X - sy Y), written to rows 0..k-1 and
+// k..2k-1 of `out` (ld ldo).  Two doubles per thread, coalesced along rows.
+__global__ void casida_combine_kernel(const double *X, long long ldx, const double *Y, long long ldy, int k, int m,
+                                      double sx, double sy, double c, double *out, long long ldo)
+{
+    const long long total = (long long)k * m;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        const double x = sx * X[(long long)i * ldx + j], y = sy * Y[(long long)i * ldy + j];
+        out[(long long)i * ldo + j] = c * (x + y);
+        out[(long long)(i + k) * ldo + j] = c * (x - y);
+    }
+}
+
+void casida_combine(const double *X, long long ldx, const double *Y, long long ldy, int k, int m, double sx,
+                    double sy, double c, double *out, long long ldo, cudaStream_t s)
+{
+    const long long total = (long long)k * m;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (blocks < 1) blocks = 1;
+    casida_combine_kernel<<<blocks, 256, 0, s>>>(X, ldx, Y, ldy, k, m, sx, sy, c, out, ldo); count_launch();
+}
+
+// H = [[A, B], [-B, -A]] (Eq. Casida) assembled from its blocks
+__global__ void casida_build_kernel(const double *A, long long lda, const double *B, long long ldb, int k, double *H,
+                                    long long ldh)
+{
+    const long long total = (long long)k * k;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), j = (int)(e % k);
+        const double a = A[(long long)i * lda + j], b = B[(long long)i * ldb + j];
+        H[(long long)i * ldh + j] = a;
+        H[(long long)i * ldh + j + k] = b;
+        H[(long long)(i + k) * ldh + j] = -b;
+        H[(long long)(i + k) * ldh + j + k] = -a;
+    }
+}
+
+void casida_build(const double *A, long long lda, const double *B, long long ldb, int k, double *H, long long ldh,
+                  cudaStream_t s)
+{
+    const long long total = (long long)k * k;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (blocks < 1) blocks = 1;
+    casida_build_kernel<<<blocks, 256, 0, s>>>(A, lda, B, ldb, k, H, ldh); count_launch();
 }
 
 // S <- (S + Sigma S^T Sigma) / 2: the nearest Sigma-symmetric matrix (Sigma S symmetric), in

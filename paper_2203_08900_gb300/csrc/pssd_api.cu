@@ -427,28 +427,24 @@ void mirror(pssd_handle h, T *A, long long lda, long long sA, int n, int batch)
 }
 
 // ---------------------------------------------------------------------------
-// one Zolotarev step on a symmetric m x m X (full storage):
-//   Xn = Chat (X + X T),  T = sum_j a_j (X^2 + c_{2j-1} I)^{-1}
-// (Eq. ZPartialFrac applied to the symmetric congruence iterate)
+// Tm = sum_j a_j (G + c_{2j-1} I)^{-1} for a symmetric positive (semi)definite m x m G
+// (lower part read), full symmetric output: the partial-fraction sum of Eq. ZPartialFrac.
+// The r shifted matrices are factorised by one batched Cholesky-with-inverse launch
+// sequence, each inverse is R_j^{-T} R_j^{-1} (one batched product, lower) and the
+// weighted sum is one HBM pass.
 // ---------------------------------------------------------------------------
 template <class T>
-int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, const double *a, double chat,
-              int *fail_index)
+int shifted_inverse_sum(pssd_handle h, const T *G, int m, int r, const double *c, const double *a, T *Tm,
+                        int *fail_index)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
-    T *G = talloc<T>(h, msz);
-    T *Tm = talloc<T>(h, msz);
     T *Z = talloc<T>(h, msz * r);
     T *Ri = talloc<T>(h, msz * r);
     double *dsh = dalloc(h, 2 * r + 2);
     std::vector<double> hs(2 * r);
     for (int j = 0; j < r; ++j) { hs[j] = c[2 * j]; hs[r + j] = a[j]; }
     h2d(h, dsh, hs.data(), sizeof(double) * 2 * r);
-    GemmArgs g;                                 // G = X X (lower)
-    g.mode = gm_of<T>();
-    g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
-    gemm(h, g);
     {
         Timed t(h, K_HBM, 0, sizeof(T) * 0.5 * m * (double)m * (1 + r));
         shift_copy_lower<T>(G, ld, Z, ld, msz, m, dsh, r, h->stream);   // Z_j = G + c_{2j-1} I
@@ -467,6 +463,29 @@ int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, c
         combine_lower<T>(Z, ld, msz, dsh + r, r, m, Tm, ld, h->stream);   // T = sum a_j Z_j^{-1}
     }
     mirror<T>(h, Tm, ld, 0, m, 1);
+    release(h, mk);
+    return PSSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one Zolotarev step on a symmetric m x m X (full storage):
+//   Xn = Chat (X + X T),  T = sum_j a_j (X^2 + c_{2j-1} I)^{-1}
+// (Eq. ZPartialFrac applied to the symmetric congruence iterate)
+// ---------------------------------------------------------------------------
+template <class T>
+int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, const double *a, double chat,
+              int *fail_index)
+{
+    Mark mk = mark(h);
+    const long long ld = m, msz = (long long)m * m;
+    T *G = talloc<T>(h, msz);
+    T *Tm = talloc<T>(h, msz);
+    GemmArgs g;                                 // G = X X (lower)
+    g.mode = gm_of<T>();
+    g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
+    gemm(h, g);
+    int st = shifted_inverse_sum<T>(h, G, m, r, c, a, Tm, fail_index);
+    if (st) { release(h, mk); return st; }
     GemmArgs f;                                 // Xn = chat (X + X T) (lower), then mirror
     f.mode = gm_of<T>();
     f.m = f.n = f.k = m; f.A = X; f.lda = ld; f.B = Tm; f.ldb = ld; f.Cin = X; f.ldcin = ld;
@@ -477,13 +496,46 @@ int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, c
     return PSSD_OK;
 }
 
+// one Zolotarev step for the polar factor of a square (non-symmetric) m x m C:
+//   Cn = Chat (C + C T),  T = sum_j a_j (C^T C + c_{2j-1} I)^{-1}
+// (the same rational function of the singular values as zolo_step applies to
+// eigenvalues: Zolo-PD for the polar decomposition, Sec. 5.3)
+template <class T>
+int zolo_step_polar(pssd_handle h, const T *C, T *Cn, int m, int r, const double *c, const double *a, double chat,
+                    int *fail_index)
+{
+    Mark mk = mark(h);
+    const long long ld = m, msz = (long long)m * m;
+    T *G = talloc<T>(h, msz);
+    T *Tm = talloc<T>(h, msz);
+    GemmArgs g;                                 // G = C^T C (lower)
+    g.mode = gm_of<T>();
+    g.m = g.n = g.k = m; g.A = C; g.lda = ld; g.ta = 1; g.B = C; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
+    gemm(h, g);
+    int st = shifted_inverse_sum<T>(h, G, m, r, c, a, Tm, fail_index);
+    if (st) { release(h, mk); return st; }
+    GemmArgs f;                                 // Cn = chat (C + C T)
+    f.mode = gm_of<T>();
+    f.m = f.n = f.k = m; f.A = C; f.lda = ld; f.B = Tm; f.ldb = ld; f.Cin = C; f.ldcin = ld;
+    f.C = Cn; f.ldc = ld; f.alpha = chat; f.beta = chat;
+    gemm(h, f);
+    release(h, mk);
+    return PSSD_OK;
+}
+
 struct SignResult { double *Y; };
 
 // Alg. 8 on the symmetric X0 (scaled so that |lambda| in [ell, 1]); result in Y
 // (one of the two ping-pong buffers, returned).  Fills the pass statistics.
+// polar: X0 is a square non-symmetric matrix with singular values in [ell, 1] and
+// the iteration computes its orthogonal polar factor (the sign of [[0, X0], [X0^T, 0]]).
 int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_restarts, double tau,
-              double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index)
+              double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index, bool polar = false)
 {
+    auto step = [&](const double *X, double *Xn, int r, const double *c, const double *a, double chat) {
+        return polar ? zolo_step_polar<double>(h, X, Xn, m, r, c, a, chat, fail_index)
+                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index);
+    };
     const long long ld = m;
     double *X = X0;
     Mark mk = mark(h);
@@ -497,12 +549,12 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
         if (zolo_coeffs_host(ell, r, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell1 > 1.0) ell1 = 1.0;
         double *X1 = (X == bufA) ? bufB : bufA;
-        int st = zolo_step(h, X, X1, m, r, c, a, chat, fail_index);
+        int st = step(X, X1, r, c, a, chat);
         if (st) { release(h, mk); return st; }
         if (zolo_coeffs_host(ell1, r, c, a, &chat, &ell2)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell2 > 1.0) ell2 = 1.0;
         double *X2 = (X1 == bufA) ? bufB : bufA;   // may be X itself on a restart (no longer needed)
-        st = zolo_step(h, X1, X2, m, r, c, a, chat, fail_index);
+        st = step(X1, X2, r, c, a, chat);
         if (st) { release(h, mk); return st; }
         double d2, y2;
         frob_pair(h, X1, ld, X2, ld, m, m, part, &d2, &y2);
@@ -1822,6 +1874,387 @@ extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, con
         gemm(h, c);                                       // W = V^{-T} T
         GemmArgs d; d.m = d.n = d.k = n; d.A = W; d.lda = ld; d.B = V; d.ldb = ld; d.tb = 1; d.C = Hbar; d.ldc = ldhb;
         gemm(h, d);                                       // Hbar = W V^T
+        return PSSD_OK;
+    });
+}
+
+
+// ===========================================================================
+// Structure-aware variant for the Casida form (Eq. Casida), operating on the
+// blocks A and B directly (the direction named in Sec. 7):
+//   H = [[A, B], [-B, -A]],  A, B symmetric,  Sigma = diag(I_k, -I_k).
+// With the orthogonal T = [[I, I], [I, -I]]/sqrt 2 (T^2 = I):
+//   T H T = [[0, R], [P, 0]],  T Sigma T = [[0, I], [I, 0]],  T (Sigma H) T = diag(P, R),
+//   P = A + B,  R = A - B  (both SPD exactly when H is definite).
+// With P = L_P L_P^T, R = L_R L_R^T the congruence form K = L^T Sigma L of the n x n path
+// becomes, in this basis,
+//   K_T = diag(L_P, L_R)^T [[0, I], [I, 0]] diag(L_P, L_R) = [[0, C], [C^T, 0]],  C = L_P^T L_R,
+// and sign(K_T) = [[0, U], [U^T, 0]] with U the orthogonal polar factor of C = U H_C
+// (H_C = U^T C SPD).  The Zolotarev iteration of Alg. 8 on K_T keeps this block form and
+// acts on C alone: C_{k+1} = Chat (C_k + C_k sum_j a_j (C_k^T C_k + c_{2j-1} I)^{-1}), with the
+// same coefficients, stopping quantity (||K_2 - K_1||_F / ||K_2||_F = ||C_2 - C_1||_F / ||C_2||_F)
+// and restarts: every shifted matrix is an SPD k x k Gram matrix (Cholesky, no pivoting).
+// The eigenvalues of H are +-sigma_i(C) (C^T C = L_R^T P L_R is similar to P R), so
+//   S  = T [[0, L_P^{-T} U L_R^T], [L_R^{-T} U^T L_P^T, 0]] T,
+//   Q_+ = T [L_P^{-T} U F; L_R^{-T} F] / sqrt 2,  Q_- = T [L_P^{-T} U F; -L_R^{-T} F] / sqrt 2,
+//        F = chol(sym(U^T C)),  A11 = F^T F,  A22 = -F^T F,
+//   V_+- = T [L_P^{-T} U W; +-L_R^{-T} W] diag(sqrt(omega)) / sqrt 2 from H_C = W diag(omega) W^T,
+// all from k x k products: about a sixth of the n x n path's work per step.
+// ===========================================================================
+namespace {
+
+struct CasFront {
+    int k = 0;
+    double *L = nullptr, *Li = nullptr;   // [L_P; L_R] and their inverses (two k x k, stride k^2)
+    double *C = nullptr;                   // C = L_P^T L_R
+    double *U = nullptr;                   // polar factor of C
+    double *Hd = nullptr;                  // H = [[A, B], [-B, -A]] (for the commutator probe)
+    double normH = 0.0;
+};
+
+int casida_validate(int k, const double *A, int lda, const double *B, int ldb)
+{
+    if (k < 1 || 2 * (long long)k > PSSD_MAX_N) return -2;
+    if (!A) return -3;
+    if (lda < k) return -4;
+    if (!B) return -5;
+    if (ldb < k) return -6;
+    return 0;
+}
+
+int casida_front(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, const pssd_opts &o,
+                 pssd_info *info, CasFront &F)
+{
+    F.k = k;
+    h->wait_limit = o.wait_cycles;
+    h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+    h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
+    if (info) { info->precision = o.precision; info->method = o.method; info->p = k; }
+    const long long ksz = (long long)k * k;
+    F.L = dalloc(h, 2 * ksz);
+    F.Li = dalloc(h, 2 * ksz);
+    F.C = dalloc(h, ksz);
+    {   // P = sym(A + B), R = sym(A - B); symmetry defects of A and B
+        const int t = (k + 31) / 32, nb = t * t;
+        Mark mk = mark(h);
+        double *part = dalloc(h, 2 * (size_t)nb);
+        {
+            Timed tt(h, K_HBM, 0, 32.0 * ksz);
+            casida_prepare(A, lda, B, ldb, k, F.L, F.L + ksz, k, part, h->stream);
+        }
+        std::vector<double> hp(2 * (size_t)nb);
+        d2h_sync(h, hp.data(), part, hp.size() * sizeof(double));
+        release(h, mk);
+        double d2 = 0, m2 = 0;
+        for (int i = 0; i < nb; ++i) { d2 += hp[2 * i]; m2 += hp[2 * i + 1]; }
+        if (!std::isfinite(d2) || !std::isfinite(m2)) return PSSD_ERR_NONFINITE;
+        F.normH = std::sqrt(m2);
+        if (!(m2 > 0.0)) return PSSD_ERR_NOT_DEFINITE;
+        if (std::sqrt(d2) > 1e-12 * std::sqrt(m2)) return PSSD_ERR_NOT_PSEUDOSYMMETRIC;
+    }
+    int fi = -1;   // L_P, L_R and their inverses in one batched factorisation
+    if (chol_inv<double>(h, F.L, k, k, ksz, 2, F.Li, ksz, &fi)) {
+        if (info) info->fail_index = fi;
+        return PSSD_ERR_NOT_DEFINITE;
+    }
+    GemmArgs g;   // C = L_P^T L_R
+    g.m = g.n = g.k = k; g.A = F.L; g.lda = k; g.ta = 1; g.triA = TRI_UPPER;
+    g.B = F.L + ksz; g.ldb = k; g.triB = TRI_LOWER; g.C = F.C; g.ldc = k;
+    gemm(h, g);
+    return PSSD_OK;
+}
+
+// bounds alpha >= sigma_max(C) = max|lambda(H)|, beta <= sigma_min(C) = min|lambda(H)| by power
+// iteration on C^T C and on (C^T C)^{-1} = L_R^{-1} L_P^{-T} L_P^{-1} L_R^{-T} (the reading of
+// Alg. 8's first step used by the n x n path, with the same safety factors), then the polar
+// factor U of C by Alg. 8 on C / alpha
+int casida_polar(pssd_handle h, CasFront &F, const pssd_opts &o, pssd_info *info)
+{
+    const int k = F.k;
+    const long long ksz = (long long)k * k;
+    double alpha = o.alpha, beta = o.beta;
+    if (!(alpha > 0.0) || !(beta > 0.0)) {
+        Mark mk = mark(h);
+        double *v = dalloc(h, k), *w = dalloc(h, k), *u = dalloc(h, k), *tmp = dalloc(h, 32 * (size_t)k + 8);
+        cudaStream_t s = h->stream;
+        const double *C = F.C, *LPi = F.Li, *LRi = F.Li + ksz;
+        if (!(alpha > 0.0)) {
+            double rq = power_max(h, k, [&](double *x, double *y) {
+                Timed t(h, K_GEMV, 4.0 * k * (double)k, 16.0 * k * (double)k);
+                gemv(C, k, 0, TRI_NONE, k, x, u, tmp, s);           // u = C x
+                gemv(C, k, 1, TRI_NONE, k, u, y, tmp, s);           // y = C^T u
+            }, v, w, tmp + 32 * (size_t)k, 60);
+            alpha = 1.05 * std::sqrt(rq);
+        }
+        if (!(beta > 0.0)) {
+            double rq = power_max(h, k, [&](double *x, double *y) {
+                Timed t(h, K_GEMV, 4.0 * k * (double)k, 16.0 * k * (double)k);
+                gemv(LRi, k, 1, TRI_UPPER, k, x, u, tmp, s);        // L_R^{-T} x
+                gemv(LPi, k, 0, TRI_LOWER, k, u, y, tmp, s);        // L_P^{-1} .
+                gemv(LPi, k, 1, TRI_UPPER, k, y, u, tmp, s);        // L_P^{-T} .
+                gemv(LRi, k, 0, TRI_LOWER, k, u, y, tmp, s);        // L_R^{-1} .
+            }, v, w, tmp + 32 * (size_t)k, 60);
+            beta = 0.9 / std::sqrt(rq);
+        }
+        release(h, mk);
+    }
+    if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;
+    if (beta > alpha) beta = alpha;
+    if (info) { info->alpha = alpha; info->beta = beta; }
+    double *X0 = dalloc(h, ksz), *bA = dalloc(h, ksz), *bB = dalloc(h, ksz);
+    {
+        Timed t(h, K_HBM, 0, 16.0 * ksz);
+        scale_copy<double, double>(F.C, k, X0, k, k, k, 1.0 / alpha, h->stream);
+    }
+    int fi = -1;
+    const int maxr = o.max_restarts < 0 ? 2 : o.max_restarts;
+    int st = zolo_sign(h, X0, k, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.U, info, &fi, /*polar=*/true);
+    if (st == PSSD_ERR_NOT_DEFINITE && info) info->fail_index = fi;
+    return st;
+}
+
+// the full H in the workspace (for the commutator probe of the outputs)
+void casida_materialise(pssd_handle h, CasFront &F, const double *A, int lda, const double *B, int ldb)
+{
+    const int n = 2 * F.k;
+    F.Hd = dalloc(h, (size_t)n * n);
+    Timed t(h, K_HBM, 0, 48.0 * F.k * (double)F.k);
+    casida_build(A, lda, B, ldb, F.k, F.Hd, n, h->stream);
+}
+
+int casida_check_opts(const pssd_opts &o)
+{
+    if (opts_bad(o)) return 1;
+    if (o.precision == PSSD_MIXED || o.method != PSSD_METHOD_ZOLO) return 1;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int pssd_casida_sign(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *S,
+                                int lds, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = casida_validate(k, A, lda, B, ldb);
+    if (v) return v;
+    if (!S) return -7;
+    if (lds < 2 * k) return -8;
+    pssd_opts o = opts ? *opts : defaults();
+    if (casida_check_opts(o)) return -9;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        CasFront F;
+        int st = casida_front(h, k, A, lda, B, ldb, o, info, F);
+        if (!st) st = casida_polar(h, F, o, info);
+        if (st) return st;
+        const long long ksz = (long long)k * k;
+        const double *LP = F.L, *LR = F.L + ksz, *LPi = F.Li, *LRi = F.Li + ksz;
+        double *T1 = dalloc(h, ksz), *X = dalloc(h, ksz), *Y = dalloc(h, ksz);
+        GemmArgs a; a.m = a.n = a.k = k; a.A = LPi; a.lda = k; a.ta = 1; a.triA = TRI_UPPER; a.B = F.U; a.ldb = k;
+        a.C = T1; a.ldc = k;
+        gemm(h, a);                                   // L_P^{-T} U
+        GemmArgs b; b.m = b.n = b.k = k; b.A = T1; b.lda = k; b.B = LR; b.ldb = k; b.tb = 1; b.triB = TRI_UPPER;
+        b.C = X; b.ldc = k;
+        gemm(h, b);                                   // X = L_P^{-T} U L_R^T
+        GemmArgs c; c.m = c.n = c.k = k; c.A = LRi; c.lda = k; c.ta = 1; c.triA = TRI_UPPER; c.B = F.U; c.ldb = k;
+        c.tb = 1; c.C = T1; c.ldc = k;
+        gemm(h, c);                                   // L_R^{-T} U^T
+        GemmArgs d; d.m = d.n = d.k = k; d.A = T1; d.lda = k; d.B = LP; d.ldb = k; d.tb = 1; d.triB = TRI_UPPER;
+        d.C = Y; d.ldc = k;
+        gemm(h, d);                                   // Y = L_R^{-T} U^T L_P^T
+        {   // S = T [[0, X], [Y, 0]] T = (1/2) [[X + Y, Y - X], [X - Y, -X - Y]]
+            Timed t(h, K_HBM, 0, 64.0 * ksz);
+            casida_combine(X, k, Y, k, k, k, 1.0, 1.0, 0.5, S, lds, h->stream);
+            casida_combine(X, k, Y, k, k, k, -1.0, 1.0, 0.5, S + k, lds, h->stream);
+        }
+        if (info) {
+            casida_materialise(h, F, A, lda, B, ldb);
+            const int n = 2 * k;
+            std::vector<double> hs(n);
+            for (int i = 0; i < n; ++i) hs[i] = i < k ? 1.0 : -1.0;
+            double *sig = dalloc(h, n);
+            h2d(h, sig, hs.data(), sizeof(double) * n);
+            info->comm_resid = comm_resid(h, n, F.Hd, n, F.normH, S, lds, nullptr, 0, sig,
+                                          (o.flags & PSSD_FLAG_RESIDUALS) != 0);
+        }
+        return PSSD_OK;
+    });
+}
+
+extern "C" int pssd_casida_split(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *Q,
+                                 int ldq, double *A11, int lda11, double *A22, int lda22, const pssd_opts *opts,
+                                 pssd_info *info)
+{
+    if (!h) return -1;
+    int v = casida_validate(k, A, lda, B, ldb);
+    if (v) return v;
+    if (!Q) return -7;
+    if (ldq < 2 * k) return -8;
+    if (!A11) return -9;
+    if (lda11 < k) return -10;
+    if (!A22) return -11;
+    if (lda22 < k) return -12;
+    pssd_opts o = opts ? *opts : defaults();
+    if (casida_check_opts(o)) return -13;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        CasFront F;
+        int st = casida_front(h, k, A, lda, B, ldb, o, info, F);
+        if (!st) st = casida_polar(h, F, o, info);
+        if (st) return st;
+        const long long ksz = (long long)k * k;
+        const double *LPi = F.Li, *LRi = F.Li + ksz;
+        double *Hc = dalloc(h, ksz), *Fi = dalloc(h, ksz), *T1 = dalloc(h, ksz), *X = dalloc(h, ksz);
+        double *Y = dalloc(h, ksz);
+        GemmArgs g; g.m = g.n = g.k = k; g.A = F.U; g.lda = k; g.ta = 1; g.B = F.C; g.ldb = k; g.C = Hc; g.ldc = k;
+        g.lowerC = 1;
+        gemm(h, g);                                   // H_C = U^T C (lower: its symmetric part)
+        int fi;
+        if (chol_inv<double>(h, Hc, k, k, 0, 1, Fi, 0, &fi)) return PSSD_ERR_BASIS;   // F = chol(H_C)
+        GemmArgs a; a.m = a.n = a.k = k; a.A = F.U; a.lda = k; a.B = Hc; a.ldb = k; a.triB = TRI_LOWER;
+        a.C = T1; a.ldc = k;
+        gemm(h, a);                                   // U F
+        GemmArgs b; b.m = b.n = b.k = k; b.A = LPi; b.lda = k; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = k;
+        b.C = X; b.ldc = k;
+        gemm(h, b);                                   // X = L_P^{-T} U F
+        GemmArgs c; c.m = c.n = c.k = k; c.A = LRi; c.lda = k; c.ta = 1; c.triA = TRI_UPPER; c.B = Hc; c.ldb = k;
+        c.triB = TRI_LOWER; c.C = Y; c.ldc = k;
+        gemm(h, c);                                   // Y = L_R^{-T} F
+        {   // Q_+ = T [X; Y]/sqrt 2 = [X + Y; X - Y]/2,  Q_- = T [X; -Y]/sqrt 2 = [X - Y; X + Y]/2
+            Timed t(h, K_HBM, 0, 64.0 * ksz);
+            casida_combine(X, k, Y, k, k, k, 1.0, 1.0, 0.5, Q, ldq, h->stream);
+            casida_combine(X, k, Y, k, k, k, 1.0, -1.0, 0.5, Q + k, ldq, h->stream);
+        }
+        GemmArgs e; e.m = e.n = e.k = k; e.A = Hc; e.lda = k; e.ta = 1; e.triA = TRI_UPPER; e.B = Hc; e.ldb = k;
+        e.triB = TRI_LOWER; e.C = A11; e.ldc = lda11; e.lowerC = 1;
+        gemm(h, e);                                   // A11 = F^T F
+        mirror(h, A11, lda11, 0, k, 1);
+        {
+            Timed t(h, K_HBM, 0, 16.0 * ksz);
+            scale_copy<double, double>(A11, lda11, A22, lda22, k, k, -1.0, h->stream);   // A22 = -F^T F
+        }
+        if (info) {
+            // backward error of the split of K_T: ||U_+^T K_T U_-||_F / ||K_T||_F with
+            // U_+- = [U; +-I]/sqrt 2 is ||U^T C - C^T U||_F / (2 sqrt 2 ||C||_F)
+            const bool exact = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
+            double d2, e2, c2;
+            double *part = dalloc(h, 2 * (size_t)frob_blocks(k, k));
+            if (exact) {
+                GemmArgs p1; p1.m = p1.n = p1.k = k; p1.A = F.U; p1.lda = k; p1.ta = 1; p1.B = F.C; p1.ldb = k;
+                p1.C = T1; p1.ldc = k;
+                gemm(h, p1);                          // U^T C
+                GemmArgs p2; p2.m = p2.n = p2.k = k; p2.A = F.C; p2.lda = k; p2.ta = 1; p2.B = F.U; p2.ldb = k;
+                p2.C = X; p2.ldc = k;
+                gemm(h, p2);                          // C^T U
+                frob_pair(h, T1, k, X, k, k, k, part, &e2, &d2);
+            } else {   // 16-column probe of E = U^T C - C^T U
+                constexpr int sc = 16;
+                double *Om = dalloc(h, (size_t)k * sc), *P1 = dalloc(h, (size_t)k * sc), *P2 = dalloc(h, (size_t)k * sc);
+                {
+                    Timed t(h, K_HBM, 0, 8.0 * k * sc);
+                    fill_gaussian(Om, sc, k, sc, 0xca51dull, h->stream);
+                }
+                GemmArgs q1; q1.m = k; q1.n = sc; q1.k = k; q1.A = F.C; q1.lda = k; q1.B = Om; q1.ldb = sc; q1.C = P1; q1.ldc = sc;
+                gemm(h, q1);                          // C Om
+                GemmArgs q2; q2.m = k; q2.n = sc; q2.k = k; q2.A = F.U; q2.lda = k; q2.ta = 1; q2.B = P1; q2.ldb = sc;
+                q2.C = P2; q2.ldc = sc;
+                gemm(h, q2);                          // U^T C Om
+                GemmArgs q3; q3.m = k; q3.n = sc; q3.k = k; q3.A = F.U; q3.lda = k; q3.B = Om; q3.ldb = sc; q3.C = P1; q3.ldc = sc;
+                gemm(h, q3);                          // U Om
+                GemmArgs q4; q4.m = k; q4.n = sc; q4.k = k; q4.A = F.C; q4.lda = k; q4.ta = 1; q4.B = P1; q4.ldb = sc;
+                q4.Cin = P2; q4.ldcin = sc; q4.beta = -1.0; q4.C = Om; q4.ldc = sc;
+                gemm(h, q4);                          // C^T U Om - U^T C Om
+                frob_pair(h, nullptr, sc, Om, sc, k, sc, part, &d2, &e2);
+                e2 /= sc;
+            }
+            frob_pair(h, nullptr, k, F.C, k, k, k, part, &d2, &c2);
+            info->split_backerr = std::sqrt(e2 / c2) / (2.0 * std::sqrt(2.0));
+            casida_materialise(h, F, A, lda, B, ldb);
+            const int n = 2 * k;
+            std::vector<double> hs(n);
+            for (int i = 0; i < n; ++i) hs[i] = i < k ? 1.0 : -1.0;
+            double *sig = dalloc(h, n);
+            h2d(h, sig, hs.data(), sizeof(double) * n);
+            info->comm_resid = comm_resid(h, n, F.Hd, n, F.normH, nullptr, 0, Q, ldq, sig, exact);
+        }
+        return PSSD_OK;
+    });
+}
+
+extern "C" int pssd_casida_eig(pssd_handle h, int k, const double *A, int lda, const double *B, int ldb, double *V,
+                               int ldv, double *D, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = casida_validate(k, A, lda, B, ldb);
+    if (v) return v;
+    if (!V) return -7;
+    if (ldv < 2 * k) return -8;
+    if (!D) return -9;
+    pssd_opts o = opts ? *opts : defaults();
+    if (casida_check_opts(o)) return -10;
+    const int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        CasFront F;
+        int st = casida_front(h, k, A, lda, B, ldb, o, info, F);
+        if (!st) st = casida_polar(h, F, o, info);
+        if (st) return st;
+        const long long ksz = (long long)k * k;
+        const double *LPi = F.Li, *LRi = F.Li + ksz;
+        double *Hc = dalloc(h, ksz), *W = dalloc(h, ksz), *w = dalloc(h, k);
+        GemmArgs g; g.m = g.n = g.k = k; g.A = F.U; g.lda = k; g.ta = 1; g.B = F.C; g.ldb = k; g.C = Hc; g.ldc = k;
+        g.lowerC = 1;
+        gemm(h, g);                                   // H_C = sym(U^T C), eigenvalues sigma_i(C)
+        mirror(h, Hc, k, 0, k, 1);
+        int maxdepth = 0;
+        st = sym_eig(h, Hc, k, W, w, leaf, 1, &maxdepth, 0x3003ull);   // H_C = W diag(w) W^T (Alg. 2)
+        if (st) return st;
+        if (info) info->levels = maxdepth;
+        double *T1 = dalloc(h, ksz), *X = dalloc(h, ksz), *Y = dalloc(h, ksz);
+        GemmArgs a; a.m = a.n = a.k = k; a.A = F.U; a.lda = k; a.B = W; a.ldb = k; a.C = T1; a.ldc = k;
+        gemm(h, a);                                   // U W
+        GemmArgs b; b.m = b.n = b.k = k; b.A = LPi; b.lda = k; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = k;
+        b.C = X; b.ldc = k;
+        gemm(h, b);                                   // L_P^{-T} U W
+        GemmArgs c; c.m = c.n = c.k = k; c.A = LRi; c.lda = k; c.ta = 1; c.triA = TRI_UPPER; c.B = W; c.ldb = k;
+        c.C = Y; c.ldc = k;
+        gemm(h, c);                                   // L_R^{-T} W
+        // order: eigenvalues ascending (D: +omega ascending, then -omega in the same order)
+        std::vector<double> hw(k);
+        d2h_sync(h, hw.data(), w, sizeof(double) * k);
+        std::vector<int> perm(k);
+        for (int i = 0; i < k; ++i) perm[i] = i;
+        std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return hw[x] < hw[y]; });
+        std::vector<double> hd(2 * (size_t)k);
+        for (int i = 0; i < k; ++i) { hd[i] = hw[perm[i]]; hd[k + i] = -hw[perm[i]]; }
+        int *dperm = ialloc(h, k);
+        h2d(h, dperm, perm.data(), sizeof(int) * k);
+        h2d(h, D, hd.data(), sizeof(double) * 2 * k);
+        {   // columns scaled by sqrt(omega) (v = sqrt|lambda| L^{-T} u) and put in order
+            Timed t(h, K_HBM, 0, 64.0 * ksz);
+            scale_columns(X, k, k, k, w, 1, h->stream);
+            scale_columns(Y, k, k, k, w, 1, h->stream);
+            gather_columns(X, k, T1, k, k, k, dperm, h->stream);
+            gather_columns(Y, k, X, k, k, k, dperm, h->stream);
+        }
+        {   // V_+ = T [X; Y]/sqrt 2 = [X + Y; X - Y]/2,  V_- = T [X; -Y]/sqrt 2 = [X - Y; X + Y]/2
+            Timed t(h, K_HBM, 0, 96.0 * ksz);
+            casida_combine(T1, k, X, k, k, k, 1.0, 1.0, 0.5, V, ldv, h->stream);
+            casida_combine(T1, k, X, k, k, k, 1.0, -1.0, 0.5, V + k, ldv, h->stream);
+            sign_fix_columns(V, ldv, 2 * k, 2 * k, h->stream);
+        }
+        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
+        if (info) {
+            casida_materialise(h, F, A, lda, B, ldb);
+            const int n = 2 * k;
+            std::vector<double> hs(n);
+            for (int i = 0; i < n; ++i) hs[i] = i < k ? 1.0 : -1.0;
+            double *sig = dalloc(h, n);
+            h2d(h, sig, hs.data(), sizeof(double) * n);
+            info->comm_resid = comm_resid(h, n, F.Hd, n, F.normH, nullptr, 0, V, ldv, sig,
+                                          (o.flags & PSSD_FLAG_RESIDUALS) != 0);
+            cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+        }
         return PSSD_OK;
     });
 }

@@ -83,6 +83,14 @@ void sym_prepare(const double *H, long long ldh, const double *sig, int n, doubl
                  double *partials, cudaStream_t s);  // M = sym(diag(sig) H); partials: defect^2, norm^2 per block
 int sym_prepare_blocks(int n);
 void reduce_sum(const double *x, int count, double *out, cudaStream_t s);
+// Casida blocks: P = sym(A + B), R = sym(A - B); partials per tile pair: symmetry defect^2, ||H||_F^2 share
+void casida_prepare(const double *A, long long lda, const double *B, long long ldb, int k, double *P, double *R,
+                    long long ldp, double *partials, cudaStream_t s);
+// rows 0..k-1 of out = c (sx X + sy Y), rows k..2k-1 = c (sx X - sy Y) (k x m blocks)
+void casida_combine(const double *X, long long ldx, const double *Y, long long ldy, int k, int m, double sx,
+                    double sy, double c, double *out, long long ldo, cudaStream_t s);
+void casida_build(const double *A, long long lda, const double *B, long long ldb, int k, double *H, long long ldh,
+                  cudaStream_t s);  // H = [[A, B], [-B, -A]]
 void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s);  // S = (S + Sig S^T Sig)/2
 void dk_combine(const double *W, long long ldw, const double *lam, const double *lambar, int n, double *X,
                 long long ldx, cudaStream_t s);  // Daleckii-Krein weights of sign(), plus diag(lambar)
