@@ -71,6 +71,9 @@ extern "C" {
                                        emulated FP64 contractions with float pairs (for comparison) */
 #define PSSD_FLAG_EMU_SIMT 4        /* emulated FP64 contractions with float pairs on the FP32 pipe instead of
                                        integer slices on the tensor cores (for comparison) */
+#define PSSD_FLAG_NO_REFINE 8       /* pssd_eig, pssd_casida_eig: skip the final refinement step of the
+                                       symmetric eigendecomposition (one Ogita-Aishima correction, about
+                                       6 m^3 flops for an m x m symmetric problem) */
 
 /* iteration for the sign function (pssd_opts.method; PSSD_FP64 and PSSD_FP64_EMULATED).
  * All three run on the same congruence form K = L^T Sigma L and the same kernels.
@@ -366,6 +369,16 @@ int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch
                        long long sA, const double *B, long long ldb, long long sB, const double *Cin,
                        long long ldcin, long long sCin, double *C, long long ldc, long long sC,
                        const double *kscale);
+
+/* Test hook: the symmetric divide-and-conquer of Alg. 2 (Zolotarev sign of the
+ * shifted subproblem, orthonormal split, recursion to Jacobi leaves of order <=
+ * opts->leaf) on a symmetric m x m B (device, ld ldb), in the arithmetic of
+ * opts->precision (PSSD_FP64 or PSSD_FP64_EMULATED), followed by one refinement
+ * step unless opts->flags has PSSD_FLAG_NO_REFINE: W (device m x m, ld ldw)
+ * receives orthonormal eigenvectors as columns and w (device, m) the eigenvalues,
+ * in no particular order.  B is not modified. */
+int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb, double *W, int ldw, double *w,
+                      const pssd_opts *opts, pssd_info *info);
 
 /* ---------------------------------------------------------------------------
  * Profiling hooks (no counterpart in the paper; for measurement only).

@@ -27,6 +27,7 @@ KIND_NAMES = ["dgemm", "chol_leaf", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", 
               "ozprep", "tcprep"]
 FLAG_NO_TENSOR_CORES = 2
 FLAG_EMU_SIMT = 4
+FLAG_NO_REFINE = 8
 METHOD_ZOLO, METHOD_DWH, METHOD_NEWTON = 0, 1, 2
 
 
@@ -68,7 +69,8 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_profile_enable", "pssd_profile_reset", "pssd_profile_read", "pssd_launch_count",
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
-           "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig"]
+           "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
+           "pssd_test_sym_eig"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -117,6 +119,8 @@ def lib():
     L.pssd_casida_split.argtypes = cas + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
                                           ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_casida_eig.argtypes = cas + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_test_sym_eig.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.POINTER(Opts),
+                                    ctypes.POINTER(Info)]
     L.pssd_device_alloc_count.argtypes = []
     L.pssd_device_alloc_count.restype = ctypes.c_longlong
     L.pssd_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
@@ -479,6 +483,21 @@ def eig_batched(Hs, sigmas=None, handle=None, **kw):
     st = lib().pssd_eig_batched(h._h, count, ns, sp, Hp, lds, Vp, ldv, Dp, ctypes.byref(o), infos)
     h._check(st)
     return Ds, Vs, [infos[i].as_dict() for i in range(count)]
+
+
+def test_sym_eig(B, handle=None, **kw):
+    """Test hook: the symmetric divide-and-conquer (Alg. 2) on a symmetric float64
+    CUDA tensor B.  Returns (w, W, info), eigenvalues unordered."""
+    m, ldb = _check_H(B)
+    h = _handle(handle)
+    W = torch.empty_like(B)
+    w = torch.empty(m, dtype=B.dtype, device=B.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_test_sym_eig(h._h, m, ctypes.c_void_p(B.data_ptr()), ldb, ctypes.c_void_p(W.data_ptr()),
+                                 W.stride(0), ctypes.c_void_p(w.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return w, W, info.as_dict()
 
 
 def test_gemm_f32(A, B, use_tc=True, ta=0, tb=0, triA=0, triB=0, lowerC=0, alpha=1.0, beta=0.0, Cin=None,

@@ -231,72 +231,100 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s)
 // triangular inverse
 // --------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(512) chol_leaf_kernel(T *A, long long lda, long long sA, T *Rinv, long long ldr,
-                                                        long long sR, int off, int s, int *info)
+__global__ void __launch_bounds__(256) chol_leaf_kernel(T *A, long long lda, long long sA, T *Rinv, long long ldr,
+                                                        long long sR, int off, int s, int S, int *info)
 {
-    // The s x s diagonal block at (off, off) of batch matrix blockIdx.x, held in
-    // shared memory (row stride s + 1): right-looking Cholesky, one square root
-    // and one reciprocal per column, then X = L^{-1} by row-oriented forward
-    // substitution (row j of X is final once divided by L_jj, and is then
-    // eliminated from the rows below).  blockDim = (32, 16).
+    // The s x s diagonal block at (off, off) of batch matrix blockIdx.x, in shared memory
+    // (row stride s + 1).  256 threads in groups of G = 256 / S (S = the power of two >= s,
+    // at least 32): group i owns row i during the factorisation and column i of the inverse.
+    // Factorisation, column j: every thread takes the pivot L_jj (final after column j - 1);
+    // group i forms its scaled entry L_ij = A_ij / L_jj into a shared column; after one barrier
+    // group i updates its row, A_il -= L_ij L_lj for l in j+1..i, its G threads taking every
+    // G-th l: two barriers per column.  Inverse: group c computes column c of X = L^{-1} by
+    // forward substitution, x_c = 1/L_cc, x_q = -(sum_{k=c}^{q-1} L_qk x_k) / L_qq, each
+    // thread summing every G-th k and the group reducing with shuffles: no block barriers.
     extern __shared__ unsigned char leaf_smem[];
-    T *L = (T *)leaf_smem;
-    T *X = L + (size_t)s * (s + 1);
-    T *rv = X + (size_t)s * (s + 1);
+    T *L = (T *)leaf_smem;                    // row i = row i of L
+    T *X = L + (size_t)s * (s + 1);           // row c = column c of L^{-1}
+    T *cj = X + (size_t)s * (s + 1);          // scaled column j
+    T *rv = cj + s;                           // 1 / L_jj
     __shared__ int bad;
-    const int ls = s + 1, z = blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int ls = s + 1, z = blockIdx.x, tid = threadIdx.x;
+    const int G = 256 / S, gi = tid / G, gt = tid - gi * G;
     A += (long long)z * sA + (long long)off * lda + off;
     Rinv += (long long)z * sR + (long long)off * ldr + off;
     if (tid == 0) bad = 0;
-    for (int i = ty; i < s; i += 16)
-        for (int j = tx; j < s; j += 32) {
-            L[i * ls + j] = (j <= i) ? A[(long long)i * lda + j] : (T)0;
-            X[i * ls + j] = (i == j) ? (T)1 : (T)0;
+    {   // coalesced load: thread (row tid / S + G t, column tid % S)
+        const int c = tid % S;
+        if (c < s)
+            for (int r = tid / S; r < s; r += G) L[r * ls + c] = (c <= r) ? A[(long long)r * lda + c] : (T)0;
+    }
+    const unsigned gmask = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
+    // pivot j: square root and reciprocal once, by one thread (FP64 square roots and
+    // divisions are long sequences on the FP64 pipe, which is narrow on this part)
+    auto finalise = [&](int j) {
+        T d = L[j * ls + j];
+        if (!(d > 0) || !isfinite((double)d)) {
+            if (!bad) { bad = 1; if (info[z] == 0) info[z] = off + j + 1; }
+            d = 1;
         }
+        d = sqrt(d);
+        L[j * ls + j] = d;
+        rv[j] = (T)1 / d;
+    };
+    __syncthreads();
+    if (tid == 0) finalise(0);
     __syncthreads();
     for (int j = 0; j < s; ++j) {
-        if (tid == 0) {
-            T d = L[j * ls + j];
-            if (!(d > 0) || !isfinite((double)d)) {
-                if (!bad) { bad = 1; if (info[z] == 0) info[z] = off + j + 1; }
-                d = 1;
+        const T r = rv[j];
+        if (gt == 0 && gi > j && gi < s) cj[gi] = L[gi * ls + j] * r;
+        __syncthreads();
+        if (gi > j && gi < s) {
+            const T lij = cj[gi];
+            if (gt == 0) L[gi * ls + j] = lij;
+            T *row = L + gi * ls;
+            for (int l = j + 1 + gt; l <= gi; l += G) row[l] -= lij * cj[l];
+            if (gi == j + 1) {             // row j+1 is final: its pivot next
+                __syncwarp(gmask);
+                if (gt == 0) finalise(j + 1);
             }
-            d = sqrt(d);
-            L[j * ls + j] = d;
-            rv[j] = (T)1 / d;
-        }
-        __syncthreads();
-        const T r = rv[j];
-        for (int i = j + 1 + tid; i < s; i += 512) L[i * ls + j] *= r;
-        __syncthreads();
-        for (int i = j + 1 + ty; i < s; i += 16) {
-            const T lij = L[i * ls + j];
-            for (int l = j + 1 + tx; l <= i; l += 32) L[i * ls + l] -= lij * L[l * ls + j];
         }
         __syncthreads();
     }
-    for (int j = 0; j < s; ++j) {
-        const T r = rv[j];
-        for (int c = tid; c <= j; c += 512) X[j * ls + c] *= r;
-        __syncthreads();
-        for (int i = j + 1 + ty; i < s; i += 16) {
-            const T lij = L[i * ls + j];
-            for (int c = tx; c <= j; c += 32) X[i * ls + c] -= lij * X[j * ls + c];
+    {
+        const int c = gi;
+        T *x = X + (size_t)(c < s ? c : 0) * ls;
+        if (c < s) {
+            for (int t = gt; t < c; t += G) x[t] = (T)0;
+            if (gt == 0) x[c] = rv[c];
         }
-        __syncthreads();
+        __syncwarp();
+        for (int q = 1; q < s; ++q) {             // the same trip count for every thread (shuffles)
+            T part = 0;
+            if (c < s && q > c) {
+                const T *Lq = L + q * ls;
+                for (int k = c + gt; k < q; k += G) part += Lq[k] * x[k];
+            }
+            for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(gmask, part, o);
+            if (c < s && q > c && gt == 0) x[q] = -part * rv[q];
+            __syncwarp(gmask);
+        }
     }
-    for (int i = ty; i < s; i += 16)
-        for (int j = tx; j < s; j += 32) {
-            A[(long long)i * lda + j] = (j <= i) ? L[i * ls + j] : (T)0;
-            Rinv[(long long)i * ldr + j] = (j <= i) ? X[i * ls + j] : (T)0;
-        }
+    __syncthreads();
+    {   // coalesced store of L and of L^{-1} (row r of L^{-1} = entries r of the columns in X)
+        const int c = tid % S;
+        if (c < s)
+            for (int r = tid / S; r < s; r += G) {
+                A[(long long)r * lda + c] = (c <= r) ? L[r * ls + c] : (T)0;
+                Rinv[(long long)r * ldr + c] = (c <= r) ? X[c * ls + r] : (T)0;
+            }
+    }
 }
 
 template <class T>
 size_t chol_leaf_smem(int s)
 {
-    return (2 * (size_t)s * (s + 1) + s) * sizeof(T);
+    return (2 * (size_t)s * (s + 1) + 2 * (size_t)s) * sizeof(T);
 }
 
 template <class T>
@@ -306,7 +334,9 @@ int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long lo
     const size_t sm = chol_leaf_smem<T>(CholLeaf<T>::max_s);
     if (!ensure_dynamic_smem((const void *)chol_leaf_kernel<T>, (int)sm)) return -1;
     if (s <= 0 || s > CholLeaf<T>::max_s) return -2;
-    chol_leaf_kernel<T><<<batch, dim3(32, 16), chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info); count_launch();
+    int S = 32;
+    while (S < s) S *= 2;                        // 32, 64 or 128: groups of 8, 4 or 2 threads
+    chol_leaf_kernel<T><<<batch, 256, chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, S, info); count_launch();
     return 0;
 }
 
@@ -488,6 +518,40 @@ void casida_build(const double *A, long long lda, const double *B, long long ldb
     casida_build_kernel<<<blocks, 256, 0, s>>>(A, lda, B, ldb, k, H, ldh); count_launch();
 }
 
+// S <- (S + S^T) / 2 in place, over 32x32 tile pairs: the symmetric part of a product of
+// two commuting symmetric matrices, whose computed value carries a first-order commutator
+// error that averaging cancels (taking one triangle would keep it)
+template <class T>
+__global__ void __launch_bounds__(256) sym_average_kernel(T *S, long long lds, int n)
+{
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi < bj) return;
+    __shared__ T P[TT][TT + 1], Q[TT][TT + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bi * TT + yy, j = bj * TT + tx;
+        P[yy][tx] = (i < n && j < n) ? S[(long long)i * lds + j] : (T)0;
+        int i2 = bj * TT + yy, j2 = bi * TT + tx;
+        Q[yy][tx] = (i2 < n && j2 < n) ? S[(long long)i2 * lds + j2] : (T)0;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < TT; yy += 8) {
+        int i = bi * TT + yy, j = bj * TT + tx;
+        if (i < n && j < n) S[(long long)i * lds + j] = (T)0.5 * (P[yy][tx] + Q[tx][yy]);
+        int i2 = bj * TT + yy, j2 = bi * TT + tx;
+        if (bi != bj && i2 < n && j2 < n) S[(long long)i2 * lds + j2] = (T)0.5 * (Q[yy][tx] + P[tx][yy]);
+    }
+}
+
+template <class T>
+void sym_average(T *S, long long lds, int n, cudaStream_t s)
+{
+    int t = (n + TT - 1) / TT;
+    sym_average_kernel<T><<<dim3(t, t), 256, 0, s>>>(S, lds, n); count_launch();
+}
+template void sym_average<double>(double *, long long, int, cudaStream_t);
+template void sym_average<float>(float *, long long, int, cudaStream_t);
+
 // S <- (S + Sigma S^T Sigma) / 2: the nearest Sigma-symmetric matrix (Sigma S symmetric), in
 // place, over 32x32 tile pairs
 __global__ void __launch_bounds__(256) j_resym_kernel(double *S, long long lds, const double *sig, int n)
@@ -541,6 +605,34 @@ void dk_combine(const double *W, long long ldw, const double *lam, const double 
 {
     int gx = (n + 255) / 256; if (gx > 16) gx = 16;
     dk_combine_kernel<<<dim3(gx, n), 256, 0, s>>>(W, ldw, lam, lambar, n, X, ldx); count_launch();
+}
+
+// Correction of one refinement step of an approximate symmetric eigendecomposition
+// A ~ Z diag(lam) Z^T (Ogita and Aishima's iteration): with S = Z^T A Z and
+// Gm = Z^T Z - I (both full, symmetric), R = -Gm and
+//   F_ii = R_ii / 2,
+//   F_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)   if |lam_j - lam_i| > omega,
+//   F_ij = R_ij / 2                                  otherwise (a cluster: keep orthogonality only).
+__global__ void eig_refine_correction_kernel(const double *S, long long lds, const double *Gm, long long ldg,
+                                             const double *lam, int n, double omega, double *F, long long ldf)
+{
+    const int i = blockIdx.y;
+    const double li = lam[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double r = -Gm[(long long)i * ldg + j];
+        const double d = lam[j] - li;
+        double v = 0.5 * r;
+        if (i != j && fabs(d) > omega) v = (S[(long long)i * lds + j] + lam[j] * r) / d;
+        F[(long long)i * ldf + j] = v;
+    }
+}
+
+void eig_refine_correction(const double *S, long long lds, const double *Gm, long long ldg, const double *lam, int n,
+                           double omega, double *F, long long ldf, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    eig_refine_correction_kernel<<<dim3(gx, n), 256, 0, s>>>(S, lds, Gm, ldg, lam, n, omega, F, ldf);
+    count_launch();
 }
 
 // X[i][j] *= r[i] (row scaling)
@@ -925,6 +1017,23 @@ __global__ void normalize_kernel(double *y, double *x, int n, double *norm_out)
 void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s)
 {
     normalize_kernel<<<1, 1024, 0, s>>>(y, x, n, norm_out); count_launch();
+}
+
+// Lanczos three-term update w <- w - alpha v - beta vprev with alpha, beta read
+// from device memory (beta may be null): no host round trip per step
+__global__ void lanczos_update_kernel(double *w, const double *v, const double *vprev, const double *alpha,
+                                      const double *beta, int n)
+{
+    const double a = alpha[0], b = beta ? beta[0] : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        w[i] = w[i] - a * v[i] - (vprev ? b * vprev[i] : 0.0);
+}
+
+void lanczos_update(double *w, const double *v, const double *vprev, const double *alpha, const double *beta, int n,
+                    cudaStream_t s)
+{
+    int blocks = (n + 255) / 256; if (blocks > 64) blocks = 64;
+    lanczos_update_kernel<<<blocks, 256, 0, s>>>(w, v, vprev, alpha, beta, n); count_launch();
 }
 
 __global__ void dot_kernel(const double *x, const double *y, int n, double *out)

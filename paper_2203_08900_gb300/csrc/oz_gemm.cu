@@ -417,25 +417,65 @@ __device__ __forceinline__ long long oz_fixed56(double v, int e)
     return (b >> 63) ? -(long long)f : (long long)f;
 }
 
-// exponent e(r) with max_p |X(r,p)| < 2^e, by 32 x 32 tiles and atomicMax
-__global__ void __launch_bounds__(256) oz_exp_kernel(const double *X, long long ld, long long sb, int trans, int rows,
-                                                     int k, int tri, const double *ks, int rows_pad, int *e)
+// One operand of the preparation passes: op(X) is rows x k (trans: op(X)[r][p] = X[p][r]),
+// with structural zeros (tri), an optional inner scaling ks[p], rows padded to rows_pad.
+struct OzOperand {
+    const double *X; long long ld, sb; int trans, rows, tri; const double *ks;
+    int rows_pad, tile_rows; int *e; __nv_bfloat16 *out;
+};
+
+// exponents e(r) with max_p |op(X)[r][p]| < 2^e of both operands in one launch; blocks
+// [0, nA) serve A, the rest B.  Rows contiguous in memory (trans = 0): a block holds 8 warps,
+// each one row over a 1024-column chunk (8 loads in flight per lane), a shuffle max and an
+// atomicMax.  Transposed (trans = 1): a block covers 32 rows of op(X) (32 memory columns)
+// over a 256-term chunk of p, its 8 warps each reading 32 p rows of 32 consecutive doubles,
+// then a shared-memory max and one atomicMax per row.
+__global__ void __launch_bounds__(256) oz_exp_kernel(OzOperand a, OzOperand b, int k, int nA)
 {
-    __shared__ int T[32][33];
-    const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    X += (long long)z * sb;
-    for (int yy = ty; yy < 32; yy += 8) {
-        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = oz_frexp_exp(oz_load(X, ld, 1, rows, k, tri, ks, r, p)); }
-        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = oz_frexp_exp(oz_load(X, ld, 0, rows, k, tri, ks, r, p)); }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int r = r0 + threadIdx.x;
+    const bool isA = (int)blockIdx.x < nA;
+    const OzOperand &o = isA ? a : b;
+    const int blk = isA ? (int)blockIdx.x : (int)blockIdx.x - nA;
+    const int z = blockIdx.z, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const double *X = o.X + (long long)z * o.sb;
+    if (!o.trans) {
+        const int kc = (k + 1023) / 1024;                  // chunks per row
+        const int r = (blk / kc) * 8 + warp, p0 = (blk % kc) * 1024;
+        if (r >= o.rows) return;
         int mx = INT_MIN / 2;
-        for (int q = 0; q < 32; ++q) mx = max(mx, T[threadIdx.x][q]);
-        if (r < rows && mx > INT_MIN / 2) atomicMax(&e[z * rows_pad + r], mx);
+        for (int pp = p0; pp < p0 + 1024 && pp < k; pp += 256) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                mx = max(mx, oz_frexp_exp(oz_load(X, o.ld, 0, o.rows, k, o.tri, o.ks, r, pp + t * 32 + lane)));
+        }
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+        if (lane == 0 && mx > INT_MIN / 2) atomicMax(&o.e[z * o.rows_pad + r], mx);
+    } else {
+        __shared__ int red[8][33];
+        const int kc = (k + 255) / 256;
+        const int r0 = (blk / kc) * 32, p0 = (blk % kc) * 256;
+        const int r = r0 + lane;
+        int mx = INT_MIN / 2;
+#pragma unroll 4
+        for (int t = 0; t < 32; ++t) {
+            const int pp = p0 + warp + 8 * t;
+            mx = max(mx, oz_frexp_exp(oz_load(X, o.ld, 1, o.rows, k, o.tri, o.ks, r, pp)));
+        }
+        red[warp][lane] = mx;
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int w = 1; w < 8; ++w) mx = max(mx, red[w][lane]);
+            if (r < o.rows && mx > INT_MIN / 2) atomicMax(&o.e[z * o.rows_pad + r], mx);
+        }
     }
+}
+
+// number of blocks oz_exp_kernel uses for one operand
+int oz_exp_blocks(const OzOperand &o, int k)
+{
+    if (!o.trans) return ((o.rows + 7) / 8) * ((k + 1023) / 1024);
+    return ((o.rows + 31) / 32) * ((k + 255) / 256);
 }
 
 // eight BF16 slices in the tiled layout the GEMM streams: for row r of tile
@@ -446,41 +486,73 @@ __global__ void __launch_bounds__(256) oz_exp_kernel(const double *X, long long 
 // shared-memory swizzle the MMA descriptors expect).
 // F = round(x 2^{56-e}) is cut into balanced base-128 digits d_8 .. d_2 in
 // [-64, 63]; the rest is d_1, |d_1| <= 128; x 2^{-e} = sum_t d_t 2^{-7t} + O(2^-57).
-__global__ void __launch_bounds__(256) oz_slice_kernel(const double *X, long long ld, long long sb, int trans,
-                                                       int rows, int k, int tri, const double *ks, int rows_pad,
-                                                       int k_pad, int tile_rows, const int *e, __nv_bfloat16 *out)
+// One CTA per 32 rows x 64 columns of op(X): the tile is read coalesced (along memory
+// rows, transposing through shared memory when trans = 1), then each thread takes 8
+// consecutive columns of one row -- half of a 16-column k block -- and writes each of
+// its 8 slices as one 16-byte store; the 32 lanes of a warp cover 16 rows x both halves
+// of one k block, i.e. 512 contiguous bytes per slice.
+__global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand a, OzOperand b, int k, int k_pad, int nA)
 {
-    __shared__ double T[32][33];
-    const int z = blockIdx.z, r0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    X += (long long)z * sb;
-    for (int yy = ty; yy < 32; yy += 8) {
-        if (trans) { int p = p0 + yy, r = r0 + tx; T[tx][yy] = oz_load(X, ld, 1, rows, k, tri, ks, r, p); }
-        else { int r = r0 + yy, p = p0 + tx; T[yy][tx] = oz_load(X, ld, 0, rows, k, tri, ks, r, p); }
+    __shared__ double T[32][65];               // T[row][column] of the tile
+    const bool isA = (int)blockIdx.x < nA;
+    const OzOperand &o = isA ? a : b;
+    const int blk = isA ? (int)blockIdx.x : (int)blockIdx.x - nA;
+    const int pt = (k_pad + 63) / 64;           // 64-column tiles per row band
+    const int z = blockIdx.z, r0 = (blk / pt) * 32, p0 = (blk % pt) * 64;
+    const int tid = threadIdx.x;
+    const double *X = o.X + (long long)z * o.sb;
+    const int trans = o.trans, rows = o.rows, tri = o.tri, rows_pad = o.rows_pad, tile_rows = o.tile_rows;
+    const long long ld = o.ld;
+    const double *ks = o.ks;
+    const int *e = o.e;
+    __nv_bfloat16 *out = o.out;
+    if (trans) {   // memory rows are p: a warp reads 32 consecutive r of one p
+        for (int it = 0; it < 8; ++it) {
+            const int pl = it * 8 + (tid >> 5), rl = tid & 31;
+            T[rl][pl] = oz_load(X, ld, 1, rows, k, tri, ks, r0 + rl, p0 + pl);
+        }
+    } else {       // memory rows are r: a warp reads 32 consecutive p of one r
+        for (int it = 0; it < 8; ++it) {
+            const int rl = it * 4 + (tid >> 6), pl = tid & 63;
+            T[rl][pl] = oz_load(X, ld, 0, rows, k, tri, ks, r0 + rl, p0 + pl);
+        }
     }
     __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rl = (warp & 1) * 16 + (lane >> 1);          // row within the tile
+    const int kb = warp >> 1;                              // k block within the tile (0..3)
+    const int half = lane & 1;                             // columns 8 half .. 8 half + 7 of the k block
+    const int r = r0 + rl, pb = p0 + kb * 16 + half * 8;
+    if (r >= rows_pad || pb >= k_pad) return;
+    const int ex = (r < rows) ? e[z * rows_pad + r] : -4000;
+    long long f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = (ex > -2000) ? oz_fixed56(T[rl][kb * 16 + half * 8 + q], ex) : 0;
     const int kblocks = k_pad / 16, tiles = rows_pad / tile_rows;
-    for (int yy = ty; yy < 32; yy += 8) {
-        const int r = r0 + yy, p = p0 + tx;
-        if (r >= rows_pad || p >= k_pad) continue;
-        long long f = 0;
-        if (r < rows) {
-            const int ex = e[z * rows_pad + r];
-            if (ex > -2000) f = oz_fixed56(T[yy][tx], ex);
-        }
-        const int rr = r % tile_rows, kk = p & 15;
-        const long long blk = ((long long)z * tiles + r / tile_rows) * kblocks + (p >> 4);
-        __nv_bfloat16 *o = out + blk * (OZ_S * tile_rows * 16) + rr * 16 + ((((kk >> 3) ^ (rr >> 2)) & 1) << 3) +
-                           (kk & 7);
-        const int sstride = tile_rows * 16;
+    const int rr = r % tile_rows;
+    const long long oblk = ((long long)z * tiles + r / tile_rows) * kblocks + (pb >> 4);
+    __nv_bfloat16 *dst = out + oblk * (OZ_S * tile_rows * 16) + rr * 16 + ((half ^ (rr >> 2)) & 1) * 8;
+    const int sstride = tile_rows * 16;
+    uint32_t w[OZ_S][4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        long long fa = f[q], fb = f[q + 1];
+        uint16_t da[OZ_S], db[OZ_S];
 #pragma unroll
         for (int t = OZ_S; t >= 2; --t) {
-            const int d = (int)((f + 64) & 127) - 64;
-            f = (f - d) >> 7;
-            o[(t - 1) * sstride] = __float2bfloat16_rn((float)d);
+            const int ca = (int)((fa + 64) & 127) - 64, cb = (int)((fb + 64) & 127) - 64;
+            fa = (fa - ca) >> 7; fb = (fb - cb) >> 7;
+            da[t - 1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)ca));
+            db[t - 1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)cb));
         }
-        o[0] = __float2bfloat16_rn((float)f);
+        da[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)fa));
+        db[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)fb));
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t) w[t][q >> 1] = (uint32_t)da[t] | ((uint32_t)db[t] << 16);
     }
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t)
+        *reinterpret_cast<uint4 *>(dst + t * sstride) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
 __global__ void fill_int_kernel(int *x, long long n, int v)
@@ -525,19 +597,17 @@ int oz_gemm_prepare(const GemmArgs &g, void *ws, cudaStream_t s)
     const OzLayout L = oz_layout(g, ws);
     const int triB = g.triB == TRI_LOWER ? TRI_UPPER : (g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE);
     fill_int_kernel<<<64, 256, 0, s>>>(L.ea, (long long)(L.mp + L.np) * g.batch, INT_MIN / 2); count_launch();
+    // op(A) rows are memory rows unless A is transposed; op(B) columns are memory rows when B is transposed
+    OzOperand oa{(const double *)g.A, g.lda, g.sA, g.ta, g.m, g.triA, (const double *)g.kscale, L.mp, OZ_BM, L.ea, L.sa};
+    OzOperand ob{(const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, triB, nullptr, L.np, OZ_BN, L.eb, L.sb};
     {
-        dim3 gr((L.kp + 31) / 32, (L.mp + 31) / 32, g.batch);
-        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                         (const double *)g.kscale, L.mp, L.ea); count_launch();
-        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.A, g.lda, g.sA, g.ta, g.m, g.k, g.triA,
-                                           (const double *)g.kscale, L.mp, L.kp, OZ_BM, L.ea, L.sa); count_launch();
+        const int nA = oz_exp_blocks(oa, g.k), nB = oz_exp_blocks(ob, g.k);
+        oz_exp_kernel<<<dim3(nA + nB, 1, g.batch), 256, 0, s>>>(oa, ob, g.k, nA); count_launch();
     }
     {
-        dim3 gr((L.kp + 31) / 32, (L.np + 31) / 32, g.batch);
-        oz_exp_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                         L.np, L.eb); count_launch();
-        oz_slice_kernel<<<gr, 256, 0, s>>>((const double *)g.B, g.ldb, g.sB, g.tb ? 0 : 1, g.n, g.k, triB, nullptr,
-                                           L.np, L.kp, OZ_BN, L.eb, L.sb); count_launch();
+        const int pt = (L.kp + 63) / 64;
+        const int nA = pt * (L.mp / 32), nB = pt * (L.np / 32);
+        oz_slice_kernel<<<dim3(nA + nB, 1, g.batch), 256, 0, s>>>(oa, ob, g.k, L.kp, nA); count_launch();
     }
     return 0;
 }

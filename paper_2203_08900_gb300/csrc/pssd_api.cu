@@ -31,6 +31,7 @@
 #include <type_traits>
 #include <string>
 #include <vector>
+#include <cfloat>
 
 #include "pssd.h"
 #include "pssd_internal.h"
@@ -474,24 +475,40 @@ int shifted_inverse_sum(pssd_handle h, const T *G, int m, int r, const double *c
 // ---------------------------------------------------------------------------
 template <class T>
 int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, const double *a, double chat,
-              int *fail_index)
+              int *fail_index, const T *G0 = nullptr, double ell = 1.0)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
-    T *G = talloc<T>(h, msz);
     T *Tm = talloc<T>(h, msz);
-    GemmArgs g;                                 // G = X X (lower)
-    g.mode = gm_of<T>();
-    g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
-    gemm(h, g);
+    const T *G = G0;
+    if (!G) {                                   // G = X X (lower), unless the caller has it
+        T *Gw = talloc<T>(h, msz);
+        GemmArgs g;
+        g.mode = gm_of<T>();
+        g.m = g.n = g.k = m; g.A = X; g.lda = ld; g.B = X; g.ldb = ld; g.C = Gw; g.ldc = ld; g.lowerC = 1;
+        gemm(h, g);
+        G = Gw;
+    }
     int st = shifted_inverse_sum<T>(h, G, m, r, c, a, Tm, fail_index);
     if (st) { release(h, mk); return st; }
-    GemmArgs f;                                 // Xn = chat (X + X T) (lower), then mirror
+    // Xn = chat (X + X T).  X and T commute in exact arithmetic, but T is as large as
+    // a_1 / (x^2 + c_1) where X has eigenvalues x near 0, and the computed X T carries a
+    // commutator error of that size; its symmetric part (X T + T X)/2 cancels the error to
+    // first order.  FP64 steps whose lower bound l is small form the full product and
+    // average it; later steps (l near 1, T of moderate size) and the FP32 steps (whose
+    // shifts are floored away from 0) take the lower triangle and mirror it.
+    const bool full = std::is_same<T, double>::value && ell < 0.05;
+    GemmArgs f;
     f.mode = gm_of<T>();
     f.m = f.n = f.k = m; f.A = X; f.lda = ld; f.B = Tm; f.ldb = ld; f.Cin = X; f.ldcin = ld;
-    f.C = Xn; f.ldc = ld; f.alpha = chat; f.beta = chat; f.lowerC = 1;
+    f.C = Xn; f.ldc = ld; f.alpha = chat; f.beta = chat; f.lowerC = full ? 0 : 1;
     gemm(h, f);
-    mirror<T>(h, Xn, ld, 0, m, 1);
+    if (full) {
+        Timed t(h, K_HBM, 0, 2.0 * sizeof(T) * m * (double)m);
+        sym_average<T>(Xn, ld, m, h->stream);
+    } else {
+        mirror<T>(h, Xn, ld, 0, m, 1);
+    }
     release(h, mk);
     return PSSD_OK;
 }
@@ -530,11 +547,15 @@ struct SignResult { double *Y; };
 // polar: X0 is a square non-symmetric matrix with singular values in [ell, 1] and
 // the iteration computes its orthogonal polar factor (the sign of [[0, X0], [X0^T, 0]]).
 int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_restarts, double tau,
-              double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index, bool polar = false)
+              double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index, bool polar = false,
+              const double *G0 = nullptr)
 {
+    // G0: X0^2 (lower) when the caller has formed it (symmetric case, first step only)
+    double step_ell = 1.0;   // lower bound of the step being taken
     auto step = [&](const double *X, double *Xn, int r, const double *c, const double *a, double chat) {
+        const double *G = (X == X0 && !polar) ? G0 : nullptr;
         return polar ? zolo_step_polar<double>(h, X, Xn, m, r, c, a, chat, fail_index)
-                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index);
+                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index, G, step_ell);
     };
     const long long ld = m;
     double *X = X0;
@@ -549,11 +570,13 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
         if (zolo_coeffs_host(ell, r, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell1 > 1.0) ell1 = 1.0;
         double *X1 = (X == bufA) ? bufB : bufA;
+        step_ell = ell;
         int st = step(X, X1, r, c, a, chat);
         if (st) { release(h, mk); return st; }
         if (zolo_coeffs_host(ell1, r, c, a, &chat, &ell2)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (ell2 > 1.0) ell2 = 1.0;
         double *X2 = (X1 == bufA) ? bufB : bufA;   // may be X itself on a restart (no longer needed)
+        step_ell = ell1;
         st = step(X1, X2, r, c, a, chat);
         if (st) { release(h, mk); return st; }
         double d2, y2;
@@ -593,7 +616,7 @@ int dwh_sign(pssd_handle h, double *X0, int m, double ell, double *bufA, double 
         double c[2], a[1], chat, ell1;
         if (zolo_coeffs_host(ell, 1, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         double *Xn = (X == bufA) ? bufB : bufA;
-        int st = zolo_step<double>(h, X, Xn, m, 1, c, a, chat, fail_index);
+        int st = zolo_step<double>(h, X, Xn, m, 1, c, a, chat, fail_index, nullptr, ell);
         if (st) { release(h, mk); return st; }
         double d2, y2;
         frob_pair(h, X, ld, Xn, ld, m, m, part, &d2, &y2);
@@ -655,6 +678,8 @@ int newton_sign(pssd_handle h, const double *Linv, const double *sig, double alp
             f.C = Xn; f.ldc = ld; f.alpha = 0.5 / z; f.beta = 0.5 * z; f.lowerC = 1;
             gemm(h, f);                                                   // (z X + (X^2)^{-1} X / z) / 2
         }
+        // lower part, mirrored: the first step is a symmetric sandwich; after it |lambda(X)| >= 1,
+        // so (X^2)^{-1} is of moderate size and so is the commutator error of (X^2)^{-1} X
         mirror<double>(h, Xn, ld, 0, m, 1);
         double d2, y2;
         frob_pair(h, X, ld, Xn, ld, m, m, part, &d2, &y2);
@@ -833,11 +858,12 @@ double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *ds
 }
 
 // ---------------------------------------------------------------------------
-// orthonormal basis of the columns of Y (n x m, ld ldy) by CholeskyQR2 -> U (ld ldu),
-// for `batch` independent blocks Y + z sY -> U + z sU
+// orthonormal basis of the columns of Y (n x m, ld ldy) by Cholesky QR repeated
+// `passes` times (CholeskyQR2 by default) -> U (ld ldu), for `batch` independent
+// blocks Y + z sY -> U + z sU
 // ---------------------------------------------------------------------------
 int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double *U, long long ldu, int batch = 1,
-            long long sY = 0, long long sU = 0)
+            long long sY = 0, long long sU = 0, int passes = 2)
 {
     Mark mk = mark(h);
     const long long gsz = (long long)m * m, wsz = (long long)n * m;
@@ -845,15 +871,16 @@ int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double 
     double *Gi = dalloc(h, (size_t)(gsz * batch));
     double *W = dalloc(h, (size_t)(wsz * batch));
     const double *src = Y; long long lds = ldy, ss = sY;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
         GemmArgs g;  // G = Y^T Y (lower)
         g.m = g.n = m; g.k = n; g.batch = batch; g.A = src; g.lda = lds; g.sA = ss; g.ta = 1; g.B = src; g.ldb = lds;
         g.sB = ss; g.C = G; g.ldc = m; g.sC = gsz; g.lowerC = 1;
         gemm(h, g);
         int fi;
         if (chol_inv(h, G, m, m, gsz, batch, Gi, gsz, &fi)) { release(h, mk); return PSSD_ERR_BASIS; }
-        double *dst = (pass == 0) ? W : U;
-        long long ldd = (pass == 0) ? m : ldu, sd = (pass == 0) ? wsz : sU;
+        const bool last = pass == passes - 1;
+        double *dst = last ? U : W;
+        long long ldd = last ? ldu : m, sd = last ? sU : wsz;
         GemmArgs q;  // U = Y G^{-T}
         q.m = n; q.n = m; q.k = m; q.batch = batch; q.A = src; q.lda = lds; q.sA = ss; q.B = Gi; q.ldb = m;
         q.sB = gsz; q.tb = 1; q.triB = TRI_UPPER; q.C = dst; q.ldc = ldd; q.sC = sd;
@@ -866,9 +893,14 @@ int cholqr2(pssd_handle h, const double *Y, long long ldy, int n, int m, double 
 
 // Symmetric split of B (m x m, symmetric) given Y ~ sign(B - sigma I):
 //   U = [U_+ U_-] (m x m, ld m), Bp = U_+^T B U_+ (p x p), Bm = U_-^T B U_- ;
-//   E = U_+^T U_- (p x (m-p)) if E != nullptr.
+//   E = U_+^T B U_- (p x (m-p)) if E != nullptr.
+// The sketch (I +- Y)/2 Omega has the condition number of a Gaussian block, which
+// multiplies the projector's error in the cross product U_+^T U_-.  refine: apply
+// the projectors once more to the orthonormal bases, (I +- Y)/2 U_+-, and take one
+// Cholesky QR pass of the result (condition number 1 + O(error)), which brings
+// ||U^T U - I|| back to the projector's own error.
 int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, double *U, double *Bp, double *Bm,
-              double *E, uint64_t seed)
+              double *E, uint64_t seed, bool refine = false)
 {
     Mark mk = mark(h);
     const long long ld = m;
@@ -894,6 +926,24 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
     } else {
         if (p > 0) st = cholqr2(h, Yb, ld, m, p, U, ld);
         if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld);
+    }
+    if (!st && refine) {
+        if (p > 0) {   // (I + Y)/2 U_+
+            GemmArgs g; g.m = m; g.n = p; g.k = m; g.A = Y; g.lda = ld; g.B = U; g.ldb = ld; g.Cin = U; g.ldcin = ld;
+            g.C = Yb; g.ldc = ld; g.alpha = 0.5; g.beta = 0.5;
+            gemm(h, g);
+        }
+        if (m - p > 0) {   // (I - Y)/2 U_-
+            GemmArgs g; g.m = m; g.n = m - p; g.k = m; g.A = Y; g.lda = ld; g.B = U + p; g.ldb = ld; g.Cin = U + p;
+            g.ldcin = ld; g.C = Yb + p; g.ldc = ld; g.alpha = -0.5; g.beta = 0.5;
+            gemm(h, g);
+        }
+        if (p > 0 && p == m - p) {
+            st = cholqr2(h, Yb, ld, m, p, U, ld, 2, p, p, 1);
+        } else {
+            if (p > 0) st = cholqr2(h, Yb, ld, m, p, U, ld, 1, 0, 0, 1);
+            if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld, 1, 0, 0, 1);
+        }
     }
     if (st) { release(h, mk); return st; }
     double *W = Yb;   // reuse: W = B U  (m x m)
@@ -1024,6 +1074,107 @@ double comm_resid(pssd_handle h, int n, const double *H, long long ldh, double n
     return normH > 0 ? std::sqrt(c2) / normH : NAN;
 }
 
+// eigenvalues (ascending) and eigenvectors (columns of Z, row-major n x n) of a small
+// symmetric matrix by cyclic Jacobi on the host
+void small_sym_eig(std::vector<double> A, int n, std::vector<double> &w, std::vector<double> &Z)
+{
+    Z.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                if (i != j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {   // Z <- Z J
+                    const double zkp = Z[(size_t)k * n + p], zkq = Z[(size_t)k * n + q];
+                    Z[(size_t)k * n + p] = c * zkp - sn * zkq;
+                    Z[(size_t)k * n + q] = sn * zkp + c * zkq;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) { return A[(size_t)x * n + x] < A[(size_t)y * n + y]; });
+    std::vector<double> Zs((size_t)n * n);
+    w.resize(n);
+    for (int j = 0; j < n; ++j) {
+        w[j] = A[(size_t)idx[j] * n + idx[j]];
+        for (int i = 0; i < n; ++i) Zs[(size_t)i * n + j] = Z[(size_t)i * n + idx[j]];
+    }
+    Z.swap(Zs);
+}
+
+// Lanczos quadrature of the spectrum of a symmetric m x m B: s steps from a Gaussian
+// start vector v give a tridiagonal T whose eigenvalues theta_j (ascending) and squared
+// first eigenvector components tau_j are the nodes and weights of the Gauss rule for the
+// spectral measure of v; with v random, sum_{theta_j <= x} tau_j approximates the
+// fraction of the eigenvalues of B below x, and wide gaps between consecutive nodes mark
+// sparse parts of the spectrum.  The recurrence runs on the device (alpha_j, beta_j stay
+// in device memory); the host reads T once.  *resid = beta_s, the norm of the residual
+// after the last step: [theta_1 - beta_s, theta_s + beta_s] encloses the spectrum of B in
+// practice (the extreme Ritz values converge first, from inside).  Returns false if the
+// recurrence produced a non-finite value.
+bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::vector<double> &th,
+                   std::vector<double> &tau, double *resid)
+{
+    const int steps = std::min(m, 24);
+    Mark mk = mark(h);
+    double *V = dalloc(h, 3 * (size_t)m), *ab = dalloc(h, 2 * (size_t)steps + 2), *tmp = dalloc(h, 32 * (size_t)m + 8);
+    double *vp = V, *vc = V + m, *w = V + 2 * m;
+    double *al = ab, *be = ab + steps + 1;
+    {
+        Timed t(h, K_GEMV, 0, 24.0 * m);
+        fill_gaussian(vc, m, 1, m, seed, h->stream);
+        normalize_vec(vc, vc, m, nullptr, h->stream);
+    }
+    for (int j = 0; j < steps; ++j) {
+        Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
+        gemv(B, m, 0, TRI_NONE, m, vc, w, tmp, h->stream);                       // w = B v_j
+        dot_vec(vc, w, m, al + j, h->stream);                                     // alpha_j
+        lanczos_update(w, vc, j ? vp : nullptr, al + j, j ? be + j - 1 : nullptr, m, h->stream);
+        normalize_vec(w, vp, m, be + j, h->stream);                               // beta_j, v_{j+1}
+        std::swap(vp, vc);
+    }
+    std::vector<double> hab(2 * (size_t)steps + 2);
+    d2h_sync(h, hab.data(), ab, hab.size() * sizeof(double));
+    release(h, mk);
+    int s = steps;
+    for (int j = 0; j < steps - 1; ++j)
+        if (!(hab[steps + 1 + j] > 1e-12 * std::fabs(hab[j]) + 1e-300)) { s = j + 1; break; }
+    std::vector<double> T((size_t)s * s, 0.0), Z;
+    for (int j = 0; j < s; ++j) {
+        T[(size_t)j * s + j] = hab[j];
+        if (j + 1 < s) T[(size_t)j * s + j + 1] = T[(size_t)(j + 1) * s + j] = hab[steps + 1 + j];
+    }
+    for (double x : T) if (!std::isfinite(x)) return false;
+    *resid = std::fabs(hab[steps + 1 + s - 1]);
+    if (!std::isfinite(*resid)) return false;
+    small_sym_eig(T, s, th, Z);
+    tau.resize(s);
+    for (int j = 0; j < s; ++j) tau[j] = Z[j] * Z[j];   // first component of eigenvector j
+    return true;
+}
+
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
 // and Jacobi leaves: W (m x m, ld m) eigenvectors as columns, w eigenvalues
 // (device).  B is preserved.
@@ -1050,40 +1201,131 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
     double dmin = srt.front(), dmax = srt.back();
     double *U = dalloc(h, msz);
     int p = 0;
-    for (int attempt = 0;; ++attempt) {
-        if (attempt >= 4) { release(h, outer); return PSSD_ERR_BASIS; }
-        double sigma = (attempt == 0) ? 0.5 * (srt[(m - 1) / 2] + srt[m / 2])
-                                      : dmin + (dmax - dmin) * (0.5 + 0.11 * attempt);
-        Mark mk = mark(h);
-        double *X0 = dalloc(h, msz), *bA = dalloc(h, msz), *bB = dalloc(h, msz);
-        double *tmp = dalloc(h, m + 2);
+    // Candidate shifts (Alg. 2, "find shift"; reading R7).  The inverse-form Zolotarev step
+    // loses accuracy like u / xmin, xmin = min |lambda(X0)| of X0 = (B - sigma I)/alpha, so the
+    // shift should sit in a sparse part of the spectrum but still split it roughly in half:
+    // the midpoints of the widest gaps between Lanczos quadrature nodes whose cumulative
+    // weight lies in [0.35, 0.65], the median of the diagonal, the widest gaps with weight in
+    // [0.25, 0.75], then points of the diagonal's range (fallbacks).
+    std::vector<double> cands;
+    double lan_lo = 0.0, lan_hi = -1.0;   // spectral enclosure from the Lanczos run (empty if it failed)
+    bool deg = false;
+    {
+        std::vector<double> th, tau;
+        std::vector<std::pair<double, double>> inner, outer_gaps;   // (width, midpoint)
+        double bs;
+        if (lanczos_nodes(h, B, m, seed ^ 0x1a2c05ull, th, tau, &bs)) {
+            // a recurrence that broke down early (B v in a small Krylov space: a few distinct
+            // eigenvalues) gives no reliable enclosure; keep the infinity norm then
+            if (th.size() >= 8) { lan_lo = th.front() - bs; lan_hi = th.back() + bs; }
+            // B = sigma I to rounding (a multiple eigenvalue): any orthonormal basis diagonalises it
+            const double scale = std::max(std::fabs(th.front()), std::fabs(th.back()));
+            if (th.back() - th.front() + 2.0 * bs <= 32.0 * DBL_EPSILON * scale) deg = true;
+            double cum = 0.0;
+            for (size_t j = 0; j + 1 < th.size(); ++j) {
+                cum += tau[j];
+                const std::pair<double, double> gp{th[j + 1] - th[j], 0.5 * (th[j] + th[j + 1])};
+                if (cum >= 0.35 && cum <= 0.65) inner.push_back(gp);
+                else if (cum >= 0.25 && cum <= 0.75) outer_gaps.push_back(gp);
+            }
+            std::sort(inner.rbegin(), inner.rend());
+            std::sort(outer_gaps.rbegin(), outer_gaps.rend());
+        }
+        for (size_t i = 0; i < inner.size() && i < 3; ++i) cands.push_back(inner[i].second);
+        cands.push_back(0.5 * (srt[(m - 1) / 2] + srt[m / 2]));
+        for (size_t i = 0; i < outer_gaps.size() && i < 2; ++i) cands.push_back(outer_gaps[i].second);
+        for (int a = 1; a <= 3; ++a) cands.push_back(dmin + (dmax - dmin) * (0.5 + 0.11 * a));
+    }
+    double *Xa = dalloc(h, msz), *Ga = dalloc(h, msz), *Xb = dalloc(h, msz), *Gb = dalloc(h, msz);
+    double *tmp = dalloc(h, 32 * (size_t)m + 8);
+    // X0 = (B - sigma I)/alpha and G = X0^2 (lower); false if B = sigma I.  alpha bounds
+    // ||B - sigma I||_2: ||B - sigma I||_inf always does, but overestimates a dense matrix's
+    // 2-norm by a factor growing like sqrt(m), which shrinks every |lambda(X0)| (and so the
+    // accuracy and the convergence rate of the sign iteration) by the same factor; the
+    // Lanczos enclosure is within a small factor of the 2-norm and is taken when smaller.
+    auto prepare = [&](double sigma, double *X0, double *G, double &alpha) -> bool {
         {
             Timed t(h, K_HBM, 0, 24.0 * m * (double)m);
             copy_matrix(B, ld, X0, ld, m, m, h->stream);
             add_diag(X0, ld, m, -sigma, h->stream);
             row_abs_sum_max(X0, ld, m, tmp, tmp + m, h->stream);
         }
-        double alpha;
         d2h_sync(h, &alpha, tmp + m, sizeof(double));
-        if (!(alpha > 0.0)) {   // B = sigma I: any orthonormal basis diagonalises it
-            release(h, mk);
-            std::vector<double> eye((size_t)m * m, 0.0);
-            for (int i = 0; i < m; ++i) eye[(size_t)i * m + i] = 1.0;
-            h2d(h, W, eye.data(), sizeof(double) * msz);
-            h2d(h, w, dg.data(), sizeof(double) * m);
-            cudaStreamSynchronize(h->stream);
-            release(h, outer);
-            return PSSD_OK;
+        if (!(alpha > 0.0)) return false;
+        if (lan_hi >= lan_lo) {
+            const double a2 = std::max(lan_hi - sigma, sigma - lan_lo);
+            if (a2 > 0.0 && a2 < alpha) alpha = a2;
         }
         {
             Timed t(h, K_HBM, 0, 16.0 * m * (double)m);
             scale_copy(X0, ld, X0, ld, m, m, 1.0 / alpha, h->stream);
         }
+        GemmArgs g; g.m = g.n = g.k = m; g.A = X0; g.lda = ld; g.B = X0; g.ldb = ld; g.C = G; g.ldc = ld; g.lowerC = 1;
+        gemm(h, g);
+        return true;
+    };
+    // xmin^2 = lambda_min(G) by 20 steps of power iteration on G^{-1} = R^{-T} R^{-1}
+    // (R = chol(G)); 0 if G is not numerically positive definite (sigma on an eigenvalue)
+    auto screen = [&](const double *G) -> double {
+        Mark ms = mark(h);
+        double *Rc = dalloc(h, msz), *Ri = dalloc(h, msz), *v = dalloc(h, m), *vw = dalloc(h, m), *u = dalloc(h, m);
+        {
+            Timed t(h, K_HBM, 0, 16.0 * m * (double)m);
+            copy_matrix(G, ld, Rc, ld, m, m, h->stream);
+        }
+        int fi;
+        double xm = 0.0;
+        if (!chol_inv<double>(h, Rc, m, ld, 0, 1, Ri, 0, &fi)) {
+            const double rq = power_max(h, m, [&](double *x, double *y) {
+                Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
+                gemv(Ri, ld, 0, TRI_LOWER, m, x, u, tmp, h->stream);      // R^{-1} x
+                gemv(Ri, ld, 1, TRI_UPPER, m, u, y, tmp, h->stream);      // R^{-T} .
+            }, v, vw, tmp + 32 * (size_t)m, 20);
+            if (rq > 0.0 && std::isfinite(rq)) xm = 1.0 / std::sqrt(rq);
+        }
+        release(h, ms);
+        return xm;
+    };
+    auto identity = [&]() {   // B = sigma I: any orthonormal basis diagonalises it
+        std::vector<double> eye((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i) eye[(size_t)i * m + i] = 1.0;
+        h2d(h, W, eye.data(), sizeof(double) * msz);
+        h2d(h, w, dg.data(), sizeof(double) * m);
+        cudaStreamSynchronize(h->stream);
+        release(h, outer);
+        return PSSD_OK;
+    };
+    if (deg) return identity();
+    double best_x = -1.0;
+    size_t ci = 0;
+    for (int screened = 0; ci < cands.size() && screened < 3; ++ci, ++screened) {
+        double alpha;
+        if (!prepare(cands[ci], Xa, Ga, alpha)) return identity();
+        const double xm = screen(Ga);
+        if (xm > best_x) { best_x = xm; std::swap(Xa, Xb); std::swap(Ga, Gb); }
+        if (best_x >= 1e-5) { ++ci; break; }
+    }
+    for (int attempt = 0;; ++attempt) {
+        double *X0, *G0, ell;
+        if (attempt == 0 && best_x > 0.0) {
+            // the screened shift; l from the estimate (the power iteration approaches xmin from
+            // above, hence the factor); a wrong l shows in the stopping test and falls back
+            X0 = Xb; G0 = Gb; ell = std::max(1e-10, 0.3 * best_x);
+        } else {
+            if (ci >= cands.size()) { release(h, outer); return PSSD_ERR_BASIS; }
+            double alpha;
+            if (!prepare(cands[ci++], Xa, Ga, alpha)) return identity();
+            X0 = Xa; G0 = Ga; ell = 1e-10;   // conservative lower bound on |lambda(X0)|
+        }
+        Mark mk = mark(h);
+        double *bA = dalloc(h, msz), *bB = dalloc(h, msz);
         double *Y = nullptr;
         int fi;
-        const double ell = 1e-10;   // conservative lower bound on |lambda(X0)| (reading R7)
-        int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi);
-        if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE) { release(h, mk); continue; }
+        int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi, false, G0);
+        if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE || st == PSSD_ERR_NONFINITE) {
+            release(h, mk);
+            continue;
+        }
         if (st) { release(h, outer); return st; }
         {
             Timed t(h, K_HBM, 0, 8.0 * m);
@@ -1095,7 +1337,7 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
         if (p <= 0 || p >= m) { release(h, mk); continue; }
         // bases and projected blocks; Bp, Bm persist below the Zolotarev temporaries
         double *Bp = dalloc(h, (size_t)p * p), *Bm = dalloc(h, (size_t)(m - p) * (m - p));
-        st = sym_split(h, B, Y, m, p, U, Bp, Bm, nullptr, seed + 17 * depth + attempt);
+        st = sym_split(h, B, Y, m, p, U, Bp, Bm, nullptr, seed + 17 * depth + attempt, true);
         if (st) { release(h, mk); continue; }
         // recurse
         double *Wp = dalloc(h, (size_t)p * p), *Wm = dalloc(h, (size_t)(m - p) * (m - p));
@@ -1113,6 +1355,72 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
         break;
     }
     release(h, outer);
+    return PSSD_OK;
+}
+
+// One step of iterative refinement of an approximate eigendecomposition A ~ Z diag(d) Z^T
+// of a symmetric m x m A (Ogita and Aishima, "Iterative refinement for symmetric
+// eigenvalue decomposition", 2018): from the first-order expansion of the exact
+// eigenvectors Z (I + F), with S = Z^T A Z and R = I - Z^T Z,
+//   d_i = S_ii / (1 - R_ii),  F_ii = R_ii / 2,
+//   F_ij = (S_ij + d_j R_ij) / (d_j - d_i) for pairs farther apart than
+//   omega = 2 (||offdiag S||_F + max|d| ||R||_F), else R_ij / 2,
+// and Z <- Z + Z F.  The splits of the recursion leave a residual set by the sign
+// iteration's accuracy; one step brings ||A Z - Z D|| / ||A|| and ||Z^T Z - I|| down to
+// the rounding level of the products above.  Z (ld ldz) and d (device) in place.
+int sym_refine(pssd_handle h, const double *A, long long lda, int m, double *Z, long long ldz, double *d)
+{
+    Mark mk = mark(h);
+    const long long msz = (long long)m * m;
+    double *W = dalloc(h, msz), *S = dalloc(h, msz), *Gm = dalloc(h, msz), *dg = dalloc(h, 2 * (size_t)m);
+    double *part = dalloc(h, 2 * (size_t)frob_blocks(m, m));
+    {
+        GemmArgs g; g.m = g.n = g.k = m; g.A = A; g.lda = lda; g.B = Z; g.ldb = ldz; g.C = W; g.ldc = m;
+        gemm(h, g);                                                          // A Z
+        GemmArgs s2; s2.m = s2.n = m; s2.k = m; s2.A = Z; s2.lda = ldz; s2.ta = 1; s2.B = W; s2.ldb = m;
+        s2.C = S; s2.ldc = m; s2.lowerC = 1;
+        gemm(h, s2);                                                         // S = Z^T A Z (lower)
+        GemmArgs gg; gg.m = gg.n = m; gg.k = m; gg.A = Z; gg.lda = ldz; gg.ta = 1; gg.B = Z; gg.ldb = ldz;
+        gg.C = Gm; gg.ldc = m; gg.lowerC = 1;
+        gemm(h, gg);                                                         // Z^T Z (lower)
+    }
+    mirror(h, S, m, 0, m, 1);
+    mirror(h, Gm, m, 0, m, 1);
+    {
+        Timed t(h, K_HBM, 0, 16.0 * m * (double)m + 32.0 * m);
+        add_diag<double>(Gm, m, m, -1.0, h->stream);                         // Gm = Z^T Z - I = -R
+        get_diag(S, m, m, dg, h->stream);
+        get_diag(Gm, m, m, dg + m, h->stream);
+    }
+    std::vector<double> hd(2 * (size_t)m);
+    d2h_sync(h, hd.data(), dg, hd.size() * sizeof(double));
+    double s2, r2, dd;
+    frob_pair(h, nullptr, m, S, m, m, m, part, &dd, &s2);
+    frob_pair(h, nullptr, m, Gm, m, m, m, part, &dd, &r2);
+    double diag2 = 0.0, dmax = 0.0;
+    std::vector<double> lam(m);
+    for (int i = 0; i < m; ++i) {
+        diag2 += hd[i] * hd[i];
+        lam[i] = hd[i] / (1.0 + hd[m + i]);
+        if (!std::isfinite(lam[i])) { release(h, mk); return PSSD_ERR_NONFINITE; }
+        dmax = std::max(dmax, std::fabs(lam[i]));
+    }
+    const double omega = 2.0 * (std::sqrt(std::max(0.0, s2 - diag2)) + dmax * std::sqrt(r2));
+    h2d(h, dg, lam.data(), sizeof(double) * m);
+    {
+        Timed t(h, K_HBM, 0, 24.0 * m * (double)m);
+        eig_refine_correction(S, m, Gm, m, dg, m, omega, W, m, h->stream);  // F (in W)
+    }
+    {
+        GemmArgs g; g.m = g.n = g.k = m; g.A = Z; g.lda = ldz; g.B = W; g.ldb = m; g.Cin = Z; g.ldcin = ldz;
+        g.C = S; g.ldc = m; g.beta = 1.0;
+        gemm(h, g);                                                          // Z + Z F
+        Timed t(h, K_HBM, 0, 16.0 * m * (double)m + 16.0 * m);
+        copy_matrix(S, m, Z, ldz, m, m, h->stream);
+        copy_matrix(dg, m, d, m, 1, m, h->stream);
+    }
+    cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // lam goes out of scope
+    release(h, mk);
     return PSSD_OK;
 }
 
@@ -1584,7 +1892,7 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
         const bool exact_be = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
         double *E = exact_be ? dalloc(h, (size_t)p * q + 1) : nullptr;
-        st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
+        st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull, true);
         if (st) return st;
         double *Wp = dalloc(h, (size_t)p * p + 1), *Wm = dalloc(h, (size_t)q * q + 1);
         double *w = dalloc(h, n);
@@ -1602,6 +1910,10 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
             GemmArgs g; g.m = n; g.n = q; g.k = q; g.A = U + p; g.lda = ld; g.B = Wm; g.ldb = q; g.C = Uf + p;
             g.ldc = ld;
             gemm(h, g);
+        }
+        if (!(o.flags & PSSD_FLAG_NO_REFINE)) {   // K ~ Uf diag(w) Uf^T, refined once
+            st = sym_refine(h, F.K, ld, n, Uf, ld, w);
+            if (st) return st;
         }
         double *Vt = dalloc(h, nsz);
         {   // V = L^{-T} Uf |Lambda|^{1/2}
@@ -2107,8 +2419,11 @@ extern "C" int pssd_casida_split(pssd_handle h, int k, const double *A, int lda,
         double *Hc = dalloc(h, ksz), *Fi = dalloc(h, ksz), *T1 = dalloc(h, ksz), *X = dalloc(h, ksz);
         double *Y = dalloc(h, ksz);
         GemmArgs g; g.m = g.n = g.k = k; g.A = F.U; g.lda = k; g.ta = 1; g.B = F.C; g.ldb = k; g.C = Hc; g.ldc = k;
-        g.lowerC = 1;
-        gemm(h, g);                                   // H_C = U^T C (lower: its symmetric part)
+        gemm(h, g);                                   // U^T C
+        {
+            Timed t(h, K_HBM, 0, 16.0 * ksz);
+            sym_average<double>(Hc, k, k, h->stream);  // H_C = sym(U^T C), the polar decomposition's SPD factor
+        }
         int fi;
         if (chol_inv<double>(h, Hc, k, k, 0, 1, Fi, 0, &fi)) return PSSD_ERR_BASIS;   // F = chol(H_C)
         GemmArgs a; a.m = a.n = a.k = k; a.A = F.U; a.lda = k; a.B = Hc; a.ldb = k; a.triB = TRI_LOWER;
@@ -2200,28 +2515,50 @@ extern "C" int pssd_casida_eig(pssd_handle h, int k, const double *A, int lda, c
         if (!st) st = casida_polar(h, F, o, info);
         if (st) return st;
         const long long ksz = (long long)k * k;
-        const double *LPi = F.Li, *LRi = F.Li + ksz;
+        const double *LR = F.L + ksz, *LRi = F.Li + ksz;
         double *Hc = dalloc(h, ksz), *W = dalloc(h, ksz), *w = dalloc(h, k);
         GemmArgs g; g.m = g.n = g.k = k; g.A = F.U; g.lda = k; g.ta = 1; g.B = F.C; g.ldb = k; g.C = Hc; g.ldc = k;
-        g.lowerC = 1;
-        gemm(h, g);                                   // H_C = sym(U^T C), eigenvalues sigma_i(C)
-        mirror(h, Hc, k, 0, k, 1);
+        gemm(h, g);                                   // U^T C
+        {
+            Timed t(h, K_HBM, 0, 16.0 * ksz);
+            sym_average<double>(Hc, k, k, h->stream);  // H_C = sym(U^T C), eigenvalues sigma_i(C)
+        }
         int maxdepth = 0;
         st = sym_eig(h, Hc, k, W, w, leaf, 1, &maxdepth, 0x3003ull);   // H_C = W diag(w) W^T (Alg. 2)
         if (st) return st;
         if (info) info->levels = maxdepth;
+        // W also diagonalises C^T C = H_C^2, which does not involve U: one refinement step
+        // against C^T C (eigenvalues omega^2) removes the error that U's inexactness left in H_C.
+        const bool refine = !(o.flags & PSSD_FLAG_NO_REFINE);
+        if (refine) {
+            GemmArgs g2; g2.m = g2.n = g2.k = k; g2.A = F.C; g2.lda = k; g2.ta = 1; g2.B = F.C; g2.ldb = k;
+            g2.C = Hc; g2.ldc = k; g2.lowerC = 1;
+            gemm(h, g2);                              // C^T C (lower)
+            mirror(h, Hc, k, 0, k, 1);
+            st = sym_refine(h, Hc, k, k, W, k, w);
+            if (st) return st;
+        }
+        std::vector<double> hw(k);
+        d2h_sync(h, hw.data(), w, sizeof(double) * k);
+        std::vector<double> hs(2 * (size_t)k);       // column scales of X and Y
+        for (int i = 0; i < k; ++i) {
+            if (refine) hw[i] = hw[i] > 0.0 ? std::sqrt(hw[i]) : -1.0;
+            if (!(hw[i] > 0.0) || !std::isfinite(hw[i])) return PSSD_ERR_NOT_DEFINITE;
+            hs[i] = 1.0 / std::sqrt(hw[i]);           // X: sqrt(omega) / omega
+            hs[k + i] = std::sqrt(hw[i]);             // Y: sqrt(omega)
+        }
+        double *dsc = dalloc(h, 2 * (size_t)k);
+        h2d(h, dsc, hs.data(), sizeof(double) * 2 * k);
         double *T1 = dalloc(h, ksz), *X = dalloc(h, ksz), *Y = dalloc(h, ksz);
-        GemmArgs a; a.m = a.n = a.k = k; a.A = F.U; a.lda = k; a.B = W; a.ldb = k; a.C = T1; a.ldc = k;
-        gemm(h, a);                                   // U W
-        GemmArgs b; b.m = b.n = b.k = k; b.A = LPi; b.lda = k; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = k;
+        // R y = omega x with y = L_R^{-T} W gives x = L_R W / omega (the eigenvectors of
+        // C^T C alone fix both halves; L_P^{-T} U W is the same vector in exact arithmetic)
+        GemmArgs b; b.m = b.n = b.k = k; b.A = LR; b.lda = k; b.triA = TRI_LOWER; b.B = W; b.ldb = k;
         b.C = X; b.ldc = k;
-        gemm(h, b);                                   // L_P^{-T} U W
+        gemm(h, b);                                   // L_R W
         GemmArgs c; c.m = c.n = c.k = k; c.A = LRi; c.lda = k; c.ta = 1; c.triA = TRI_UPPER; c.B = W; c.ldb = k;
         c.C = Y; c.ldc = k;
         gemm(h, c);                                   // L_R^{-T} W
         // order: eigenvalues ascending (D: +omega ascending, then -omega in the same order)
-        std::vector<double> hw(k);
-        d2h_sync(h, hw.data(), w, sizeof(double) * k);
         std::vector<int> perm(k);
         for (int i = 0; i < k; ++i) perm[i] = i;
         std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return hw[x] < hw[y]; });
@@ -2230,10 +2567,10 @@ extern "C" int pssd_casida_eig(pssd_handle h, int k, const double *A, int lda, c
         int *dperm = ialloc(h, k);
         h2d(h, dperm, perm.data(), sizeof(int) * k);
         h2d(h, D, hd.data(), sizeof(double) * 2 * k);
-        {   // columns scaled by sqrt(omega) (v = sqrt|lambda| L^{-T} u) and put in order
+        {   // columns scaled (v = sqrt|lambda| [x; y] up to T) and put in order
             Timed t(h, K_HBM, 0, 64.0 * ksz);
-            scale_columns(X, k, k, k, w, 1, h->stream);
-            scale_columns(Y, k, k, k, w, 1, h->stream);
+            scale_columns(X, k, k, k, dsc, 0, h->stream);
+            scale_columns(Y, k, k, k, dsc + k, 0, h->stream);
             gather_columns(X, k, T1, k, k, k, dperm, h->stream);
             gather_columns(Y, k, X, k, k, k, dperm, h->stream);
         }
@@ -2334,6 +2671,47 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// test hook: the symmetric divide-and-conquer of Alg. 2 (Zolotarev signs of
+// shifted subproblems, Jacobi leaves) on a symmetric m x m B, in the handle's
+// arithmetic for the given precision mode (PSSD_FP64 or PSSD_FP64_EMULATED):
+// W (m x m, columns eigenvectors, unordered) and w (m eigenvalues), device
+// ---------------------------------------------------------------------------
+extern "C" int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb, double *W, int ldw, double *w,
+                                 const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    if (m < 1 || m > PSSD_MAX_N) return -2;
+    if (!B) return -3;
+    if (ldb < m) return -4;
+    if (!W) return -5;
+    if (ldw < m) return -6;
+    if (!w) return -7;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o) || o.precision == PSSD_MIXED) return -8;
+    const int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        h->wait_limit = o.wait_cycles;
+        h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+        h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
+        const long long msz = (long long)m * m;
+        double *Bc = dalloc(h, msz), *Wc = dalloc(h, msz);
+        {
+            Timed t(h, K_HBM, 0, 16.0 * msz);
+            copy_matrix(B, ldb, Bc, m, m, m, h->stream);
+        }
+        int maxdepth = 0;
+        int st = sym_eig(h, Bc, m, Wc, w, leaf, 0, &maxdepth, 0x5e11ull);
+        if (!st && !(o.flags & PSSD_FLAG_NO_REFINE)) st = sym_refine(h, Bc, m, m, Wc, m, w);
+        if (st) return st;
+        if (info) info->levels = maxdepth;
+        Timed t(h, K_HBM, 0, 16.0 * msz);
+        copy_matrix(Wc, m, W, ldw, m, m, h->stream);
+        return PSSD_OK;
+    });
+}
 
 // ---------------------------------------------------------------------------
 // test hook: one FP32 contraction through the library's GEMM dispatch

@@ -92,8 +92,13 @@ void casida_combine(const double *X, long long ldx, const double *Y, long long l
 void casida_build(const double *A, long long lda, const double *B, long long ldb, int k, double *H, long long ldh,
                   cudaStream_t s);  // H = [[A, B], [-B, -A]]
 void j_resym(double *S, long long lds, const double *sig, int n, cudaStream_t s);  // S = (S + Sig S^T Sig)/2
+template <class T>
+void sym_average(T *S, long long lds, int n, cudaStream_t s);  // S = (S + S^T)/2 in place
 void dk_combine(const double *W, long long ldw, const double *lam, const double *lambar, int n, double *X,
                 long long ldx, cudaStream_t s);  // Daleckii-Krein weights of sign(), plus diag(lambar)
+// F = refinement correction of A ~ Z diag(lam) Z^T from S = Z^T A Z and Gm = Z^T Z - I (full, symmetric)
+void eig_refine_correction(const double *S, long long lds, const double *Gm, long long ldg, const double *lam, int n,
+                           double omega, double *F, long long ldf, cudaStream_t s);
 void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
 template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
@@ -120,6 +125,9 @@ void gemv(const double *A, long long lda, int ta, int tri, int n, const double *
           double *tmp, cudaStream_t s);  // y = op(A) x, square n; tmp: 32 n doubles (ta = 1)
 void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s);  // x = y/||y||
 void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s);
+// w <- w - alpha[0] v - beta[0] vprev (device scalars; vprev and beta may be null)
+void lanczos_update(double *w, const double *v, const double *vprev, const double *alpha, const double *beta, int n,
+                    cudaStream_t s);
 void scale_columns(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs,
                    cudaStream_t s);
 void sign_fix_columns(double *X, long long ldx, int m, int n, cudaStream_t s);

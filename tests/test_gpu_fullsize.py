@@ -192,3 +192,63 @@ def test_config_n16384_same_q_exact_spectrum_fp64e(P):
     assert err <= 1e-10
     del D, V, H
     torch.cuda.empty_cache()
+
+
+def _eig_checks(H, D, V, k):
+    """||HV - VD||_F / ||H||_F (the spec residual, one FP64 product of order n on the
+    GPU) and the Sigma-orthogonality ||(V^T Sigma V - Sigma_hat) X||_F / ||X||_F on 16
+    Gaussian probe columns."""
+    n = 2 * k
+    R = torch.addmm(V * D[None, :], H, V, beta=-1.0)          # H V - V D
+    res = float(torch.linalg.norm(R) / torch.linalg.norm(H))
+    del R
+    g = torch.Generator(device="cuda"); g.manual_seed(11)
+    X = torch.randn(n, 16, dtype=torch.float64, device="cuda", generator=g)
+    J = torch.cat([torch.ones(k, dtype=torch.float64, device="cuda"), -torch.ones(k, dtype=torch.float64, device="cuda")])
+    orth = float(torch.linalg.norm(V.T @ (J[:, None] * (V @ X)) - torch.sign(D)[:, None] * X) / torch.linalg.norm(X))
+    return res, orth
+
+
+@pytest.mark.parametrize("same_q", [True, False])
+def test_config_n16384_casida_eig_fp64e(P, same_q):
+    """The structure-aware diagonalisation (k x k polar factor of C = L_P^T L_R,
+    then one k x k symmetric divide-and-conquer) at the benchmark's size and
+    distribution.  Q1 = Q2: every eigenvalue against the closed form
+    +-sqrt(d1_i d2_i).  Both inputs: ||HV - VD||_F / ||H||_F <= 1e-11 and
+    ||(V^T Sigma V - Sigma_hat) X||_F / ||X||_F <= 1e-12 n on probes."""
+    k = 8192
+    n = 2 * k
+    H, d1, d2 = G.casida_torch(k, ("loguniform", 1e-2, 1e2), seed=1234 if not same_q else 4321, device="cuda",
+                               same_q=same_q)
+    A = H[:k, :k].contiguous(); B = H[:k, k:].contiguous()
+    D, V, info = P.casida_eig(A, B, precision=P.PSSD_FP64_EMULATED)
+    if same_q:
+        om = torch.sort(torch.sqrt(d1 * d2)).values
+        ref = torch.cat([om, -om])
+        err = float(torch.max(torch.abs(D - ref)) / om[-1])
+        assert err <= 1e-10
+    del A, B
+    res, orth = _eig_checks(H, D, V, k)
+    print(f"\ncasida n=16384 fp64e same_q={same_q}: ||HV-VD||/||H|| {res:.3e}  VSV {orth:.3e}  "
+          f"levels {info['levels']}  {info['seconds']:.2f} s")
+    assert res <= 1e-11
+    assert orth <= 1e-12 * n
+    del D, V, H
+    torch.cuda.empty_cache()
+
+
+def test_config_n16384_eig_fp64e(P):
+    """The n x n full diagonalisation of the benchmark's input in FP64-emulated
+    arithmetic: ||HV - VD||_F / ||H||_F <= 1e-11 and the probed Sigma-orthogonality."""
+    k = 8192
+    n = 2 * k
+    H, _, _ = G.casida_torch(k, ("loguniform", 1e-2, 1e2), seed=1234, device="cuda")
+    H = H.contiguous()
+    D, V, info = P.eig(H, precision=P.PSSD_FP64_EMULATED)
+    res, orth = _eig_checks(H, D, V, k)
+    print(f"\nn x n n=16384 fp64e: ||HV-VD||/||H|| {res:.3e}  VSV {orth:.3e}  levels {info['levels']}  "
+          f"{info['seconds']:.2f} s")
+    assert res <= 1e-11
+    assert orth <= 1e-12 * n
+    del D, V, H
+    torch.cuda.empty_cache()
