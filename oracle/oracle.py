@@ -19,8 +19,7 @@ Two layers (both FP64):
   inverse-form step Eq. (ZoloIt2), then Alg. 7, then the symmetric definite
   subproblems by Jacobi (Thm. DefDivConq).
 
-Readings of the paper where it is garbled or silent (each also listed in the
-design notes):
+Readings of the paper where it is garbled or silent:
   R1  Eq. (Compcis): the argument is i*K'/(2r+1) with the integer index i.
   R2  Eq. (ZPartialFrac2): the product between the two products is a quotient.
   R3  r is the smallest value for which two steps map [l,1] into [1-tau,1].
