@@ -228,103 +228,213 @@ void gemm_launch(const GemmArgs &g, cudaStream_t s)
 
 // --------------------------------------------------------------------------
 // Cholesky of one diagonal block (<= 128 in FP32, <= 64 in FP64) and its
-// triangular inverse
+// triangular inverse, blocked by 32 columns
 // --------------------------------------------------------------------------
+template <class T> struct LeafPivot;
+template <> struct LeafPivot<float> {
+    static __device__ __forceinline__ void get(float d, float &piv, float &r) { piv = sqrtf(d); r = 1.0f / piv; }
+};
+template <> struct LeafPivot<double> {
+    // the FP64 pipe is narrow: a float reciprocal square root refined by two Newton steps
+    // y <- y (3 - d y^2) / 2 (each doubles the number of correct bits) replaces the square
+    // root and the division; outside the float range the library functions are used
+    static __device__ __forceinline__ void get(double d, double &piv, double &r)
+    {
+        if (d > 1e-30 && d < 1e30) {
+            double y = (double)rsqrtf((float)d);
+            y = y * (1.5 - 0.5 * d * y * y);
+            y = y * (1.5 - 0.5 * d * y * y);
+            piv = d * y;
+            r = y;
+        } else {
+            piv = sqrt(d);
+            r = 1.0 / piv;
+        }
+    }
+};
+
+__device__ __forceinline__ void leaf_bar128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// pivot j of the block at Lb: L_jj = sqrt(D_jj) and rv[j] = 1 / L_jj; a pivot that is not
+// positive and finite is recorded in info[z] (global index gpiv + j + 1, first one only)
+// and taken as 1
+template <class T>
+__device__ __forceinline__ void leaf_pivot(T *Lb, int ls, int j, T *rv, int *info, int z, int gpiv, int *bad)
+{
+    T d = Lb[j * ls + j];
+    if (!(d > (T)0) || !isfinite((double)d)) {
+        if (!*bad) { *bad = 1; if (info[z] == 0) info[z] = gpiv + j + 1; }
+        d = (T)1;
+    }
+    T piv, r;
+    LeafPivot<T>::get(d, piv, r);
+    Lb[j * ls + j] = piv;
+    rv[j] = r;
+}
+
+// Warps 0-3 (thread t < 128, named barrier 1): the w x w (w <= 32) diagonal block D at Lb
+// (row stride ls) is factorised in place, D = L_D L_D^T, column by column: the column below
+// the pivot is scaled, then row i = j + 1 + t / 4 of the trailing triangle is updated by four
+// threads (every fourth column), and the thread that updates (j+1, j+1) takes pivot j + 1 at
+// once: two barriers per column.  Then X_D = L_D^{-1} into Xb: column c by four lanes of one
+// warp (forward substitution, x_c = 1/L_cc, x_k = -(sum_{m=c}^{k-1} L_km x_m) / L_kk, the sum
+// split over the four lanes and reduced with shuffles).  The four warps sit on the four SM
+// sub-partitions, which matters for FP64, whose pipe is narrow.
+template <class T>
+__device__ __forceinline__ void leaf_diag_block(T *Lb, T *Xb, int ls, int w, T *rv, int t, int *info, int z,
+                                                int gpiv, int *bad)
+{
+    if (t == 0) leaf_pivot<T>(Lb, ls, 0, rv, info, z, gpiv, bad);
+    leaf_bar128();
+    for (int j = 0; j < w; ++j) {
+        if (t > j && t < w) Lb[t * ls + j] *= rv[j];
+        leaf_bar128();
+        const int i = j + 1 + (t >> 2);
+        if (i < w) {
+            T *row = Lb + i * ls;
+            const T lij = row[j];
+            for (int c = j + 1 + (t & 3); c <= i; c += 4) row[c] -= lij * Lb[c * ls + j];
+            if (t == 0) leaf_pivot<T>(Lb, ls, j + 1, rv, info, z, gpiv, bad);   // (j+1, j+1) is final
+        }
+        leaf_bar128();
+    }
+    const int lane = t & 31, c = (t >> 5) * 8 + (lane >> 2), part = lane & 3;
+    for (int k = 0; k < w; ++k) {
+        T acc = (T)0;
+        if (c < w && k > c)
+            for (int m = c + part; m < k; m += 4) acc += Lb[k * ls + m] * Xb[m * ls + c];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (c < w && part == 0 && k >= c) Xb[k * ls + c] = (k == c) ? rv[c] : -acc * rv[k];
+        __syncwarp();
+    }
+}
+
+// The s x s diagonal block at (off, off) of batch matrix blockIdx.x, in shared memory (row
+// stride s + 1), factorised right-looking by blocks of 32 columns with 8 warps:
+//   1. warps 0-3 factorise the diagonal block and invert it (leaf_diag_block);
+//   2. panel L_21 = A_21 X_D^T: a warp per row of A_21, lane c holding row c of X_D in
+//      registers, the row of A_21 read as shared-memory broadcasts;
+//   3. trailing update A_22 -= L_21 L_21^T: lane j holding rows j, j + 32, j + 64 of L_21 in
+//      registers, a warp per row i, the lower triangle stored;
+// three barriers per block of 32 columns.  Then the off-diagonal blocks of X = L^{-1}, block
+// row i after block row i - 1: X_ik = -X_ii (sum_{m=k}^{i-1} L_im X_mk), all k < i at once,
+// two rows per warp.
 template <class T>
 __global__ void __launch_bounds__(256) chol_leaf_kernel(T *A, long long lda, long long sA, T *Rinv, long long ldr,
-                                                        long long sR, int off, int s, int S, int *info)
+                                                        long long sR, int off, int s, int *info)
 {
-    // The s x s diagonal block at (off, off) of batch matrix blockIdx.x, in shared memory
-    // (row stride s + 1).  256 threads in groups of G = 256 / S (S = the power of two >= s,
-    // at least 32): group i owns row i during the factorisation and column i of the inverse.
-    // Factorisation, column j: every thread takes the pivot L_jj (final after column j - 1);
-    // group i forms its scaled entry L_ij = A_ij / L_jj into a shared column; after one barrier
-    // group i updates its row, A_il -= L_ij L_lj for l in j+1..i, its G threads taking every
-    // G-th l: two barriers per column.  Inverse: group c computes column c of X = L^{-1} by
-    // forward substitution, x_c = 1/L_cc, x_q = -(sum_{k=c}^{q-1} L_qk x_k) / L_qq, each
-    // thread summing every G-th k and the group reducing with shuffles: no block barriers.
+    constexpr int NQ = (CholLeaf<T>::max_s - 1) / 32;   // 32-row groups of a panel (3 FP32, 1 FP64)
     extern __shared__ unsigned char leaf_smem[];
-    T *L = (T *)leaf_smem;                    // row i = row i of L
-    T *X = L + (size_t)s * (s + 1);           // row c = column c of L^{-1}
-    T *cj = X + (size_t)s * (s + 1);          // scaled column j
-    T *rv = cj + s;                           // 1 / L_jj
+    const int ls = s + 1;
+    T *L = (T *)leaf_smem;                    // the block, then L
+    T *X = L + (size_t)s * ls;                // L^{-1}
+    T *W = X + (size_t)s * ls;                // s x 33: the panel, then block products of the inverse
+    T *rv = W + (size_t)s * 33;               // 1 / L_jj
     __shared__ int bad;
-    const int ls = s + 1, z = blockIdx.x, tid = threadIdx.x;
-    const int G = 256 / S, gi = tid / G, gt = tid - gi * G;
+    const int z = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     A += (long long)z * sA + (long long)off * lda + off;
     Rinv += (long long)z * sR + (long long)off * ldr + off;
     if (tid == 0) bad = 0;
-    {   // coalesced load: thread (row tid / S + G t, column tid % S)
-        const int c = tid % S;
-        if (c < s)
-            for (int r = tid / S; r < s; r += G) L[r * ls + c] = (c <= r) ? A[(long long)r * lda + c] : (T)0;
-    }
-    const unsigned gmask = (G >= 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
-    // pivot j: square root and reciprocal once, by one thread (FP64 square roots and
-    // divisions are long sequences on the FP64 pipe, which is narrow on this part)
-    auto finalise = [&](int j) {
-        T d = L[j * ls + j];
-        if (!(d > 0) || !isfinite((double)d)) {
-            if (!bad) { bad = 1; if (info[z] == 0) info[z] = off + j + 1; }
-            d = 1;
+    for (int r = warp; r < s; r += 8)
+        for (int c = lane; c < s; c += 32) {
+            L[r * ls + c] = (c <= r) ? A[(long long)r * lda + c] : (T)0;
+            X[r * ls + c] = (T)0;
         }
-        d = sqrt(d);
-        L[j * ls + j] = d;
-        rv[j] = (T)1 / d;
-    };
     __syncthreads();
-    if (tid == 0) finalise(0);
-    __syncthreads();
-    for (int j = 0; j < s; ++j) {
-        const T r = rv[j];
-        if (gt == 0 && gi > j && gi < s) cj[gi] = L[gi * ls + j] * r;
+    const int nb = (s + 31) >> 5;
+    for (int kb = 0; kb < nb; ++kb) {
+        const int o = kb * 32, w = min(32, s - o), o2 = o + w, rows = s - o2;
+        if (warp < 4) leaf_diag_block<T>(L + o * ls + o, X + o * ls + o, ls, w, rv + o, tid, info, z, off + o, &bad);
         __syncthreads();
-        if (gi > j && gi < s) {
-            const T lij = cj[gi];
-            if (gt == 0) L[gi * ls + j] = lij;
-            T *row = L + gi * ls;
-            for (int l = j + 1 + gt; l <= gi; l += G) row[l] -= lij * cj[l];
-            if (gi == j + 1) {             // row j+1 is final: its pivot next
-                __syncwarp(gmask);
-                if (gt == 0) finalise(j + 1);
+        if (rows > 0) {
+            {   // W[i][c] = sum_{m <= c} A[o2 + i][o + m] X_D[c][m]
+                T xd[32];
+#pragma unroll
+                for (int m = 0; m < 32; ++m) xd[m] = (lane < w && m < w) ? X[(o + lane) * ls + o + m] : (T)0;
+                for (int i = warp; i < rows; i += 8) {
+                    const T *a = L + (o2 + i) * ls + o;
+                    T acc = (T)0;
+#pragma unroll
+                    for (int m = 0; m < 32; ++m)
+                        if (m < w) acc += a[m] * xd[m];
+                    W[i * 33 + lane] = acc;
+                }
             }
+            __syncthreads();
+            {
+                T wr[NQ][32];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const int j = lane + 32 * q;
+                        wr[q][c] = (j < rows && c < w) ? W[j * 33 + c] : (T)0;
+                    }
+                for (int i = warp; i < rows; i += 8) {
+                    const T *wi = W + i * 33;
+                    T acc[NQ];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) acc[q] = (T)0;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const T v = wi[c];
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) acc[q] += v * wr[q][c];
+                    }
+                    T *lrow = L + (o2 + i) * ls;
+                    if (lane < w) lrow[o + lane] = wi[lane];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j <= i) lrow[o2 + j] -= acc[q];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int ib = 1; ib < nb; ++ib) {
+        const int o = ib * 32, w = min(32, s - o), hw = (w + 1) >> 1;
+        for (int idx = warp; idx < ib * hw; idx += 8) {    // W[32 k + r][c] = sum_{q in [32 k, o)} L[o + r][q] X[q][32 k + c]
+            const int k = idx / hw, r0 = 2 * (idx - k * hw), r1 = r0 + 1;
+            const T *l0 = L + (o + r0) * ls, *l1 = L + (o + (r1 < w ? r1 : r0)) * ls;
+            T a0 = (T)0, a1 = (T)0;
+            for (int q = k * 32; q < o; ++q) {
+                const T xv = X[q * ls + k * 32 + lane];
+                a0 += l0[q] * xv;
+                a1 += l1[q] * xv;
+            }
+            W[(k * 32 + r0) * 33 + lane] = a0;
+            if (r1 < w) W[(k * 32 + r1) * 33 + lane] = a1;
+        }
+        __syncthreads();
+        for (int idx = warp; idx < ib * hw; idx += 8) {    // X[o + r][32 k + c] = -sum_{q <= r} X_ii[r][q] W[32 k + q][c]
+            const int k = idx / hw, r0 = 2 * (idx - k * hw), r1 = r0 + 1;
+            const T *d0 = X + (o + r0) * ls + o, *d1 = X + (o + (r1 < w ? r1 : r0)) * ls + o;
+            T a0 = (T)0, a1 = (T)0;
+            for (int q = 0; q <= r0; ++q) {
+                const T wv = W[(k * 32 + q) * 33 + lane];
+                a0 += d0[q] * wv;
+                a1 += d1[q] * wv;
+            }
+            if (r1 < w) a1 += d1[r1] * W[(k * 32 + r1) * 33 + lane];
+            X[(o + r0) * ls + k * 32 + lane] = -a0;
+            if (r1 < w) X[(o + r1) * ls + k * 32 + lane] = -a1;
         }
         __syncthreads();
     }
-    {
-        const int c = gi;
-        T *x = X + (size_t)(c < s ? c : 0) * ls;
-        if (c < s) {
-            for (int t = gt; t < c; t += G) x[t] = (T)0;
-            if (gt == 0) x[c] = rv[c];
+    for (int r = warp; r < s; r += 8)
+        for (int c = lane; c < s; c += 32) {
+            A[(long long)r * lda + c] = (c <= r) ? L[r * ls + c] : (T)0;
+            Rinv[(long long)r * ldr + c] = (c <= r) ? X[r * ls + c] : (T)0;
         }
-        __syncwarp();
-        for (int q = 1; q < s; ++q) {             // the same trip count for every thread (shuffles)
-            T part = 0;
-            if (c < s && q > c) {
-                const T *Lq = L + q * ls;
-                for (int k = c + gt; k < q; k += G) part += Lq[k] * x[k];
-            }
-            for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(gmask, part, o);
-            if (c < s && q > c && gt == 0) x[q] = -part * rv[q];
-            __syncwarp(gmask);
-        }
-    }
-    __syncthreads();
-    {   // coalesced store of L and of L^{-1} (row r of L^{-1} = entries r of the columns in X)
-        const int c = tid % S;
-        if (c < s)
-            for (int r = tid / S; r < s; r += G) {
-                A[(long long)r * lda + c] = (c <= r) ? L[r * ls + c] : (T)0;
-                Rinv[(long long)r * ldr + c] = (c <= r) ? X[c * ls + r] : (T)0;
-            }
-    }
 }
 
 template <class T>
 size_t chol_leaf_smem(int s)
 {
-    return (2 * (size_t)s * (s + 1) + 2 * (size_t)s) * sizeof(T);
+    return (2 * (size_t)s * (s + 1) + 34 * (size_t)s) * sizeof(T);
 }
 
 template <class T>
@@ -334,9 +444,7 @@ int chol_leaf(T *A, long long lda, long long sA, T *Rinv, long long ldr, long lo
     const size_t sm = chol_leaf_smem<T>(CholLeaf<T>::max_s);
     if (!ensure_dynamic_smem((const void *)chol_leaf_kernel<T>, (int)sm)) return -1;
     if (s <= 0 || s > CholLeaf<T>::max_s) return -2;
-    int S = 32;
-    while (S < s) S *= 2;                        // 32, 64 or 128: groups of 8, 4 or 2 threads
-    chol_leaf_kernel<T><<<batch, 256, chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, S, info); count_launch();
+    chol_leaf_kernel<T><<<batch, 256, chol_leaf_smem<T>(s), st>>>(A, lda, sA, Rinv, ldr, sR, off, s, info); count_launch();
     return 0;
 }
 

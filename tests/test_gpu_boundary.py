@@ -54,7 +54,9 @@ def test_split_with_precomputed_sign(P, precision):
     for A, ref in ((A1, lam[:p1]), (A0, lam[:p0])):
         assert np.max(np.abs(np.sort(np.linalg.eigvalsh(A.cpu().numpy())) - ref)) <= 1e-10 * nrm
     assert np.max(np.abs(np.sort(np.linalg.eigvalsh(B1.cpu().numpy()))[::-1] - lam[p1:])) <= 1e-10 * nrm
-    assert 0 <= i1["split_backerr"] <= 1e-12
+    # S enters in H's coordinates and is mapped to K's by L^T S L^{-T}, which multiplies its
+    # rounding error by up to kappa(L) = kappa(M)^(1/2) (about 1e2 here): 10x the internal path's bound
+    assert 0 <= i1["split_backerr"] <= 1e-11
     assert 0 <= i1["comm_resid"] <= 1e-11 * np.linalg.norm(Pref, 2)   # ~ ||S||_2 for the non-normal S
 
 
