@@ -384,7 +384,9 @@ def main():
     table = kernel_table(kinds, t, args.steps, peaks)
     dom = max(["dgemm", "sgemm", "dfgemm", "tcgemm", "ozgemm"], key=lambda kk: kinds[kk]["ms"])
     roof = dict(table[dom])
-    roof.update({"kernel": KERNEL_NAMES[dom], "traffic": None})
+    roof.update({"kernel": KERNEL_NAMES[dom], "traffic": roof.pop("traffic_per_launch", None),
+                 "traffic_note": "bytes per launch: ncu DRAM bytes per flop of a 4096^3 launch x this step's "
+                                 "flops per launch; about 3.5x the algorithmic slice and C bytes (L2 re-reads)"})
     acc = split_accuracy(P, torch, H, Q, p, dev)
     # the metric's condition on S itself: S = L^{-T} sign(K) L^T from pssd_sign in the same
     # precision mode, ||S^2 - I||_F and ||SH - HS||_F / ||H||_F computed by the library (untimed)
@@ -579,6 +581,12 @@ def kernel_table(kinds, t_total_s, steps, peaks):
            "sgemm": (fp32_roof, "derived: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
            "dfgemm": (fp32_roof / 13.0, "derived: FP32 issue rate / 13 instructions per multiply-add x 2 flop"),
            "chol_leaf": (fp64_roof, "derived FP64 roof; the leaf is latency-bound (sequential columns)")}
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per product of the pipe's own
+    # operations, from one ncu capture of each tensor-core kernel on a 4096^3 product:
+    # oz_gemm_kernel 2.346 GB for 36 x 2 x 4096^3 BF16 slice flops, tc_gemm_kernel 0.763 GB for
+    # 3 x 2 x 4096^3 TF32 flops.  A launch's traffic is taken in proportion to its flops (the tile
+    # shape fixes the bytes moved per flop).
+    traffic_per_flop = {"ozgemm": 2.346e9 / (36 * 2 * 4096.0 ** 3), "tcgemm": 0.763e9 / (3 * 2 * 4096.0 ** 3)}
     out = {}
     for name, v in kinds.items():
         if v["launches"] == 0:
@@ -590,7 +598,9 @@ def kernel_table(kinds, t_total_s, steps, peaks):
             f, pk, note = tensor[name]
             a = v["flops"] * f / (ms / 1e3) / 1e12
             row.update({"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
-                        "peak_note": note})
+                        "peak_note": note,
+                        "traffic_per_launch": traffic_per_flop[name] * v["flops"] * f / v["launches"],
+                        "algorithmic_flops_per_launch": v["flops"] * f / v["launches"]})
         elif name in alu:
             pk, note = alu[name]
             a = v["flops"] / (ms / 1e3) / 1e12
