@@ -71,6 +71,8 @@ extern "C" {
                                        emulated FP64 contractions with float pairs (for comparison) */
 #define PSSD_FLAG_EMU_SIMT 4        /* emulated FP64 contractions with float pairs on the FP32 pipe instead of
                                        integer slices on the tensor cores (for comparison) */
+#define PSSD_FLAG_RECOMPUTE 16      /* pssd_sign_vjp_rev: keep only the per-step iterates and recompute the
+                                       shifted factorisations in the backward pass (less memory) */
 #define PSSD_FLAG_NO_REFINE 8       /* pssd_eig, pssd_casida_eig: skip the final refinement step of the
                                        symmetric eigendecomposition (one Ogita-Aishima correction, about
                                        6 m^3 flops for an m x m symmetric problem) */
@@ -280,6 +282,28 @@ int pssd_eig_batched(pssd_handle h, int count, const int *n, const signed char *
 int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
                   const double *Sbar, int ldsb, const double *lambar, double *Hbar, int ldhb,
                   const pssd_opts *opts, pssd_info *info);
+
+/*
+ * Step-reversal adjoint of S = sign(H) (Alg. 8 run backwards) and of the sum of the positive
+ * eigenvalues: Hbar = d<Sbar, S>/dH + pos_weight * d(sum_{lambda > 0} lambda)/dH, where the
+ * second term is P_+^T, P_+ = (I + S)/2 (Lemma SignProj).  The forward computation (pssd_sign,
+ * Zolotarev method, PSSD_FP64 or PSSD_FP64_EMULATED) records every step's input iterate and,
+ * unless opts->flags has PSSD_FLAG_RECOMPUTE, the r shifted inverses (X_k^2 + c I)^{-1} of the
+ * step; the backward pass reverses each step X_{k+1} = Chat (X_k + X_k sum_j a_j Z_j) through
+ * them, then the congruence K = L^T Sigma L and the Cholesky factorisation M = L L^T.  The
+ * coefficients and the bounds alpha, beta are held fixed: the result is the exact gradient of
+ * the computed iteration.  H enters only through sym(Sigma H), so Hbar is the gradient with
+ * respect to pseudosymmetric H (the unconstrained gradient projected by X -> Sigma sym(Sigma X)).
+ *   Sbar     device n x n (ld ldsb) or NULL (zero cotangent of S)
+ *   Hbar     device n x n (ld ldhb), written
+ * Memory: about (2 (max_restarts + 1) (1 + r) + 16) n^2 doubles with stored inverses,
+ * (2 (max_restarts + 1) + 16 + r) n^2 with PSSD_FLAG_RECOMPUTE (r: the first pass's degree).
+ * Returns -7 (ldsb), -8 (pos_weight not finite), -9/-10 (Hbar, ldhb), -11 (options: mixed
+ * precision or a method other than PSSD_METHOD_ZOLO), or a status of pssd_sign.
+ */
+int pssd_sign_vjp_rev(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                      const double *Sbar, int ldsb, double pos_weight, double *Hbar, int ldhb,
+                      const pssd_opts *opts, pssd_info *info);
 
 /*
  * Structure-aware variants for the Casida form (Eq. Casida): they operate on the

@@ -28,6 +28,7 @@ KIND_NAMES = ["dgemm", "chol_leaf", "hbm_pass", "gemv", "jacobi_leaf", "sgemm", 
 FLAG_NO_TENSOR_CORES = 2
 FLAG_EMU_SIMT = 4
 FLAG_NO_REFINE = 8
+FLAG_RECOMPUTE = 16
 METHOD_ZOLO, METHOD_DWH, METHOD_NEWTON = 0, 1, 2
 
 
@@ -70,7 +71,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
            "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
-           "pssd_test_sym_eig"]
+           "pssd_test_sym_eig", "pssd_sign_vjp_rev"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -103,6 +104,8 @@ def lib():
     L.pssd_sign_noalloc.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_sign_vjp.argtypes = sig + [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.POINTER(Opts),
                                       ctypes.POINTER(Info)]
+    L.pssd_sign_vjp_rev.argtypes = sig + [vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(Info)]
     ll = ctypes.c_longlong
     L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
                                      vp, ll, ll, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
@@ -425,20 +428,48 @@ def sign_vjp(H, Sbar=None, lambar=None, sigma=None, handle=None, **kw):
     return Hbar
 
 
+def sign_vjp_rev(H, Sbar=None, pos_weight=0.0, sigma=None, handle=None, **kw):
+    """Step-reversal adjoint: dL/dH for L = <Sbar, sign(H)> + pos_weight * (sum of the
+    positive eigenvalues), reversing each Zolotarev step through its recorded shifted
+    inverses (flags=FLAG_RECOMPUTE: recompute them from per-step checkpoints).  The result
+    is the gradient with respect to pseudosymmetric H."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    if Sbar is not None:
+        Sbar = Sbar.contiguous()
+        if Sbar.shape != H.shape or Sbar.dtype != torch.float64 or not Sbar.is_cuda:
+            raise ValueError("Sbar must match H")
+    Hbar = torch.empty_like(H)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_sign_vjp_rev(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh,
+                                 ctypes.c_void_p(Sbar.data_ptr() if Sbar is not None else 0), n,
+                                 ctypes.c_double(pos_weight), ctypes.c_void_p(Hbar.data_ptr()), Hbar.stride(0),
+                                 ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return Hbar
+
+
 class SignFn(torch.autograd.Function):
-    """S = sign(H) with the library's adjoint as backward (FP64)."""
+    """S = sign(H) with the library's adjoint as backward (FP64).  adjoint="steps" (default)
+    reverses the Zolotarev steps (gradient with respect to pseudosymmetric H); "spectral"
+    uses the Daleckii-Krein form on the eigendecomposition (unconstrained gradient)."""
 
     @staticmethod
-    def forward(ctx, H, sigma=None):
+    def forward(ctx, H, sigma=None, adjoint="steps"):
         S, _ = sign(H.detach(), sigma=sigma)
         ctx.save_for_backward(H)
         ctx.sigma = sigma
+        ctx.adjoint = adjoint
         return S
 
     @staticmethod
     def backward(ctx, gS):
         (H,) = ctx.saved_tensors
-        return sign_vjp(H.detach(), Sbar=gS.contiguous(), sigma=ctx.sigma), None
+        if ctx.adjoint == "steps":
+            return sign_vjp_rev(H.detach(), Sbar=gS.contiguous(), sigma=ctx.sigma), None, None
+        return sign_vjp(H.detach(), Sbar=gS.contiguous(), sigma=ctx.sigma), None, None
 
 
 class EigvalsFn(torch.autograd.Function):

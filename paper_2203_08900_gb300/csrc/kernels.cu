@@ -743,6 +743,24 @@ void eig_refine_correction(const double *S, long long lds, const double *Gm, lon
     count_launch();
 }
 
+// Phi(X): the lower triangle with its diagonal halved, the strict upper triangle zeroed
+// (the operator of the Cholesky factorisation's adjoint)
+__global__ void tril_half_diag_kernel(double *X, long long ldx, int n)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double *x = X + (long long)i * ldx + j;
+        if (j > i) *x = 0.0;
+        else if (j == i) *x *= 0.5;
+    }
+}
+
+void tril_half_diag(double *X, long long ldx, int n, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    tril_half_diag_kernel<<<dim3(gx, n), 256, 0, s>>>(X, ldx, n); count_launch();
+}
+
 // X[i][j] *= r[i] (row scaling)
 __global__ void scale_rows_kernel(double *X, long long ldx, int m, int n, const double *r)
 {

@@ -436,11 +436,12 @@ void mirror(pssd_handle h, T *A, long long lda, long long sA, int n, int batch)
 // ---------------------------------------------------------------------------
 template <class T>
 int shifted_inverse_sum(pssd_handle h, const T *G, int m, int r, const double *c, const double *a, T *Tm,
-                        int *fail_index)
+                        int *fail_index, T *zstore = nullptr)
 {
+    // zstore (r m^2, optional): receives the r inverses Z_j, full symmetric, for the adjoint
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
-    T *Z = talloc<T>(h, msz * r);
+    T *Z = zstore ? zstore : talloc<T>(h, msz * r);
     T *Ri = talloc<T>(h, msz * r);
     double *dsh = dalloc(h, 2 * r + 2);
     std::vector<double> hs(2 * r);
@@ -459,6 +460,7 @@ int shifted_inverse_sum(pssd_handle h, const T *G, int m, int r, const double *c
     l.B = Ri; l.ldb = ld; l.sB = msz; l.triB = TRI_LOWER;
     l.C = Z; l.ldc = ld; l.sC = msz; l.lowerC = 1;
     gemm(h, l);
+    if (zstore) mirror<T>(h, Z, ld, msz, m, r);
     {
         Timed t(h, K_HBM, 0, sizeof(T) * 0.5 * m * (double)m * (r + 1));
         combine_lower<T>(Z, ld, msz, dsh + r, r, m, Tm, ld, h->stream);   // T = sum a_j Z_j^{-1}
@@ -475,7 +477,7 @@ int shifted_inverse_sum(pssd_handle h, const T *G, int m, int r, const double *c
 // ---------------------------------------------------------------------------
 template <class T>
 int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, const double *a, double chat,
-              int *fail_index, const T *G0 = nullptr, double ell = 1.0)
+              int *fail_index, const T *G0 = nullptr, double ell = 1.0, T *zstore = nullptr)
 {
     Mark mk = mark(h);
     const long long ld = m, msz = (long long)m * m;
@@ -489,7 +491,7 @@ int zolo_step(pssd_handle h, const T *X, T *Xn, int m, int r, const double *c, c
         gemm(h, g);
         G = Gw;
     }
-    int st = shifted_inverse_sum<T>(h, G, m, r, c, a, Tm, fail_index);
+    int st = shifted_inverse_sum<T>(h, G, m, r, c, a, Tm, fail_index, zstore);
     if (st) { release(h, mk); return st; }
     // Xn = chat (X + X T).  X and T commute in exact arithmetic, but T is as large as
     // a_1 / (x^2 + c_1) where X has eigenvalues x near 0, and the computed X T carries a
@@ -542,20 +544,46 @@ int zolo_step_polar(pssd_handle h, const T *C, T *Cn, int m, int r, const double
 
 struct SignResult { double *Y; };
 
+// Record of a Zolotarev sign computation for the step-reversal adjoint: for every step its
+// input iterate X_k (a checkpoint), its coefficients and, unless they are to be recomputed
+// from X_k, the shifted inverses Z_j = (X_k^2 + c_{2j-1} I)^{-1} (full, symmetric).  The
+// slots are allocated before the iteration (xslot[s]: m^2, zslot[s]: r_s m^2 or null).
+struct SignTape {
+    struct Step { int r = 0; double c[128], a[64], chat = 0.0; double *X = nullptr, *Z = nullptr; };
+    std::vector<Step> steps;
+    std::vector<double *> xslot, zslot;
+};
+
 // Alg. 8 on the symmetric X0 (scaled so that |lambda| in [ell, 1]); result in Y
 // (one of the two ping-pong buffers, returned).  Fills the pass statistics.
 // polar: X0 is a square non-symmetric matrix with singular values in [ell, 1] and
 // the iteration computes its orthogonal polar factor (the sign of [[0, X0], [X0^T, 0]]).
 int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_restarts, double tau,
               double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index, bool polar = false,
-              const double *G0 = nullptr)
+              const double *G0 = nullptr, SignTape *tape = nullptr)
 {
     // G0: X0^2 (lower) when the caller has formed it (symmetric case, first step only)
+    // tape: record every step for the adjoint (symmetric case)
     double step_ell = 1.0;   // lower bound of the step being taken
     auto step = [&](const double *X, double *Xn, int r, const double *c, const double *a, double chat) {
         const double *G = (X == X0 && !polar) ? G0 : nullptr;
+        double *zs = nullptr;
+        if (tape && !polar) {
+            const size_t s = tape->steps.size();
+            if (s >= tape->xslot.size()) return PSSD_ERR_NO_CONVERGENCE;   // more steps than planned
+            SignTape::Step rec;
+            rec.r = r; rec.chat = chat; rec.X = tape->xslot[s]; rec.Z = tape->zslot[s];
+            std::copy(c, c + 2 * r, rec.c);
+            std::copy(a, a + r, rec.a);
+            {
+                Timed t(h, K_HBM, 0, 16.0 * m * (double)m);
+                copy_matrix(X, m, rec.X, m, m, m, h->stream);
+            }
+            zs = rec.Z;
+            tape->steps.push_back(rec);
+        }
         return polar ? zolo_step_polar<double>(h, X, Xn, m, r, c, a, chat, fail_index)
-                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index, G, step_ell);
+                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index, G, step_ell, zs);
     };
     const long long ld = m;
     double *X = X0;
@@ -1433,6 +1461,7 @@ struct Front {
     double *M = nullptr, *L = nullptr, *Linv = nullptr, *K = nullptr;
     double *Y = nullptr;     // ~ sign(K)
     double normH = 0.0;
+    double alpha = 0.0;      // X0 = K / alpha
 };
 
 int validate(int n, const signed char *sigma, const double *H, int ldh)
@@ -1447,8 +1476,11 @@ int validate(int n, const signed char *sigma, const double *H, int ldh)
 }
 
 int front(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, const pssd_opts &o,
-          pssd_info *info, Front &F, const double *S_in = nullptr, long long lds_in = 0)
+          pssd_info *info, Front &F, const double *S_in = nullptr, long long lds_in = 0, SignTape *tape = nullptr,
+          bool tape_store = true)
 {
+    // tape: record the Zolotarev steps for the adjoint (FP64 / FP64e Zolotarev only); tape_store:
+    // keep the shifted inverses of every step, else only the per-step iterates
     F.n = n;
     h->wait_limit = o.wait_cycles;
     if (info) info->method = o.method;
@@ -1541,6 +1573,7 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
     if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;
     if (beta > alpha) beta = alpha;
     if (info) { info->alpha = alpha; info->beta = beta; }
+    F.alpha = alpha;
     // a5: K = L^T Sigma L (lower, mirrored), X0 = K / alpha
     {
         GemmArgs g; g.m = g.n = g.k = n; g.A = F.L; g.lda = ld; g.ta = 1; g.triA = TRI_UPPER; g.kscale = F.sig;
@@ -1576,13 +1609,29 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         scale_copy<double, double>(F.K, ld, X0, ld, n, n, 1.0 / alpha, h->stream);
     }
     int maxr = o.max_restarts < 0 ? 2 : o.max_restarts;
+    if (tape) {   // slots in the order zolo_sign takes the steps: two per pass, r from the same rule
+        double l = beta / alpha;
+        for (int pass = 0; pass <= maxr; ++pass) {
+            l = std::min(l, 1.0);
+            const int r = (pass == 0 && o.r > 0) ? o.r : choose_r_host(l, 1e-15, 8);
+            double c[128], a[64], ch, l1, l2;
+            if (r < 1 || zolo_coeffs_host(l, r, c, a, &ch, &l1)) return PSSD_ERR_NONFINITE;
+            l1 = std::min(l1, 1.0);
+            if (zolo_coeffs_host(l1, r, c, a, &ch, &l2)) return PSSD_ERR_NONFINITE;
+            for (int t = 0; t < 2; ++t) {
+                tape->xslot.push_back(dalloc(h, nsz));
+                tape->zslot.push_back(tape_store ? dalloc(h, nsz * r) : nullptr);
+            }
+            l = std::min(l2, 1.0);
+        }
+    }
     int st;
     if (o.method == PSSD_METHOD_DWH)
         st = dwh_sign(h, X0, n, beta / alpha, bA, bB, &F.Y, info, &fi);
     else if (o.method == PSSD_METHOD_NEWTON)
         st = newton_sign(h, F.Linv, F.sig, alpha, X0, n, beta / alpha, bA, bB, &F.Y, info, &fi);
     else
-        st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi);
+        st = zolo_sign(h, X0, n, beta / alpha, o.r, maxr, 1e-15, bA, bB, &F.Y, info, &fi, false, nullptr, tape);
     if (st == PSSD_ERR_NOT_DEFINITE && info) info->fail_index = fi;
     return st;
 }
@@ -2130,6 +2179,171 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
 // F vanishes between eigenvalues of the same sign and is at most 1/min|lambda|
 // elsewhere, so the pull-back is as well conditioned as the split itself.
 // ===========================================================================
+namespace {
+// Step-reversal adjoint of S = L^{-T} Y L^T with Y = X_N, the last Zolotarev iterate, and of
+// the sum of the positive eigenvalues (gradient P_+^T, P_+ = (I + S)/2): the gradient of the
+// computed function, coefficients and bounds held fixed.  Backward of one step
+// X' = chat (X + X T), T = sum_j a_j Z_j, Z_j = (X^2 + c_{2j-1} I)^{-1}:
+//   Abar = chat X X'bar,  B = sum_j a_j Z_j Abar Z_j,
+//   Xbar = chat (X'bar + X'bar T) - (X B + B X)
+// (dZ_j = -Z_j (X dX + dX X) Z_j; X, T, Z_j symmetric and commuting).  Then K = alpha X_0,
+// K = L^T Sigma L gives Lbar += Sigma L (Kbar + Kbar^T); S = L^{-T} Y L^T gives, with
+// Ghat = L^{-1} G L, Ybar = sym(Ghat) and Lbar += L^{-T} (Ghat^T Y - Y Ghat^T); the
+// Cholesky factorisation M = L L^T gives Mbar = sym(L^{-T} Phi(L^T Lbar) L^{-1}) (Phi: lower
+// triangle, diagonal halved); M = sym(Sigma H) gives Hbar = Sigma Mbar.  Since the forward
+// reads H only through sym(Sigma H), Hbar is the gradient with respect to pseudosymmetric H:
+// the unconstrained gradient projected by X -> Sigma sym(Sigma X).
+int sign_vjp_steps(pssd_handle h, const Front &F, const SignTape &tape, const double *Gb, long long ldg,
+                   double pos_weight, double *Hbar, long long ldhb)
+{
+    const int n = F.n;
+    const long long ld = n, nsz = (long long)n * n;
+    const double *L = F.L, *Li = F.Linv, *Y = F.Y;
+    Mark mk = mark(h);
+    double *T1 = dalloc(h, nsz), *W = dalloc(h, nsz), *Lb = dalloc(h, nsz), *Xb = dalloc(h, nsz);
+    double *Xn = dalloc(h, nsz);
+    if (Gb) {
+        double *Gh = Xn;
+        GemmArgs a; a.m = a.n = a.k = n; a.A = Gb; a.lda = ldg; a.B = L; a.ldb = ld; a.triB = TRI_LOWER;
+        a.C = T1; a.ldc = ld;
+        gemm(h, a);                                                            // G L
+        GemmArgs b; b.m = b.n = b.k = n; b.A = Li; b.lda = ld; b.triA = TRI_LOWER; b.B = T1; b.ldb = ld;
+        b.C = Gh; b.ldc = ld;
+        gemm(h, b);                                                            // Ghat = L^{-1} G L
+        GemmArgs c; c.m = c.n = c.k = n; c.A = Gh; c.lda = ld; c.ta = 1; c.B = Y; c.ldb = ld; c.C = T1; c.ldc = ld;
+        gemm(h, c);                                                            // Ghat^T Y
+        GemmArgs d; d.m = d.n = d.k = n; d.A = Y; d.lda = ld; d.B = Gh; d.ldb = ld; d.tb = 1; d.Cin = T1;
+        d.ldcin = ld; d.C = T1; d.ldc = ld; d.alpha = -1.0; d.beta = 1.0;
+        gemm(h, d);                                                            // - Y Ghat^T
+        Timed t(h, K_HBM, 0, 32.0 * n * (double)n);
+        copy_matrix(Gh, ld, Xb, ld, n, n, h->stream);                          // Ybar = sym(Ghat) (below)
+    }
+    if (Gb) {
+        for (int s = (int)tape.steps.size() - 1; s >= 0; --s) {
+            const SignTape::Step &stp = tape.steps[s];
+            const int r = stp.r;
+            Mark ms = mark(h);
+            double *Tm = dalloc(h, nsz), *Ab = dalloc(h, nsz), *Bs = dalloc(h, nsz), *W1 = dalloc(h, nsz);
+            double *Z = stp.Z;
+            {
+                Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+                sym_average<double>(Xb, ld, n, h->stream);
+            }
+            if (!Z) {   // recompute the shifted inverses from the checkpointed iterate
+                Z = dalloc(h, nsz * r);
+                double *G2 = W1;
+                GemmArgs g; g.m = g.n = g.k = n; g.A = stp.X; g.lda = ld; g.B = stp.X; g.ldb = ld; g.C = G2;
+                g.ldc = ld; g.lowerC = 1;
+                gemm(h, g);                                                    // X^2 (lower)
+                int fi;
+                int st = shifted_inverse_sum<double>(h, G2, n, r, stp.c, stp.a, Tm, &fi, Z);
+                if (st) { release(h, mk); return st; }
+            } else {    // T = sum_j a_j Z_j from the stored inverses
+                double *da = dalloc(h, r);
+                h2d(h, da, stp.a, sizeof(double) * r);
+                Timed t(h, K_HBM, 0, 8.0 * 0.5 * n * (double)n * (r + 1));
+                combine_lower<double>(Z, ld, nsz, da, r, n, Tm, ld, h->stream);
+            }
+            if (stp.Z) mirror<double>(h, Tm, ld, 0, n, 1);
+            GemmArgs ga; ga.m = ga.n = ga.k = n; ga.A = stp.X; ga.lda = ld; ga.B = Xb; ga.ldb = ld; ga.C = Ab;
+            ga.ldc = ld; ga.alpha = stp.chat;
+            gemm(h, ga);                                                       // Abar = chat X Xbar'
+            for (int j = 0; j < r; ++j) {
+                const double *Zj = Z + (long long)j * nsz;
+                GemmArgs g1; g1.m = g1.n = g1.k = n; g1.A = Zj; g1.lda = ld; g1.B = Ab; g1.ldb = ld; g1.C = W1;
+                g1.ldc = ld;
+                gemm(h, g1);                                                   // Z_j Abar
+                GemmArgs g2; g2.m = g2.n = g2.k = n; g2.A = W1; g2.lda = ld; g2.B = Zj; g2.ldb = ld; g2.C = Bs;
+                g2.ldc = ld; g2.alpha = stp.a[j];
+                if (j) { g2.Cin = Bs; g2.ldcin = ld; g2.beta = 1.0; }
+                gemm(h, g2);                                                   // B += a_j Z_j Abar Z_j
+            }
+            GemmArgs gx; gx.m = gx.n = gx.k = n; gx.A = Xb; gx.lda = ld; gx.B = Tm; gx.ldb = ld; gx.Cin = Xb;
+            gx.ldcin = ld; gx.C = Xn; gx.ldc = ld; gx.alpha = stp.chat; gx.beta = stp.chat;
+            gemm(h, gx);                                                       // chat (Xbar' + Xbar' T)
+            GemmArgs g3; g3.m = g3.n = g3.k = n; g3.A = stp.X; g3.lda = ld; g3.B = Bs; g3.ldb = ld; g3.Cin = Xn;
+            g3.ldcin = ld; g3.C = Xn; g3.ldc = ld; g3.alpha = -1.0; g3.beta = 1.0;
+            gemm(h, g3);                                                       // - X B
+            GemmArgs g4; g4.m = g4.n = g4.k = n; g4.A = Bs; g4.lda = ld; g4.B = stp.X; g4.ldb = ld; g4.Cin = Xn;
+            g4.ldcin = ld; g4.C = Xn; g4.ldc = ld; g4.alpha = -1.0; g4.beta = 1.0;
+            gemm(h, g4);                                                       // - B X
+            std::swap(Xb, Xn);
+            release(h, ms);
+        }
+        {
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+            sym_average<double>(Xb, ld, n, h->stream);                         // Xbar_0
+        }
+        GemmArgs gk; gk.m = gk.n = gk.k = n; gk.A = L; gk.lda = ld; gk.triA = TRI_LOWER; gk.B = Xb; gk.ldb = ld;
+        gk.C = W; gk.ldc = ld; gk.alpha = 2.0 / F.alpha;
+        gemm(h, gk);                                                           // (2/alpha) L Xbar_0
+        {
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+            scale_rows(W, ld, n, n, F.sig, h->stream);                         // Sigma L (Kbar + Kbar^T)
+        }
+        GemmArgs gl; gl.m = gl.n = gl.k = n; gl.A = Li; gl.lda = ld; gl.ta = 1; gl.triA = TRI_UPPER; gl.B = T1;
+        gl.ldb = ld; gl.Cin = W; gl.ldcin = ld; gl.C = Lb; gl.ldc = ld; gl.beta = 1.0;
+        gemm(h, gl);                                                           // Lbar
+        GemmArgs gp; gp.m = gp.n = gp.k = n; gp.A = L; gp.lda = ld; gp.ta = 1; gp.triA = TRI_UPPER; gp.B = Lb;
+        gp.ldb = ld; gp.C = T1; gp.ldc = ld;
+        gemm(h, gp);                                                           // L^T Lbar
+        {
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+            tril_half_diag(T1, ld, n, h->stream);                              // Phi
+        }
+        GemmArgs gq; gq.m = gq.n = gq.k = n; gq.A = T1; gq.lda = ld; gq.triA = TRI_LOWER; gq.B = Li; gq.ldb = ld;
+        gq.triB = TRI_LOWER; gq.C = W; gq.ldc = ld;
+        gemm(h, gq);                                                           // Phi L^{-1}
+        GemmArgs gm; gm.m = gm.n = gm.k = n; gm.A = Li; gm.lda = ld; gm.ta = 1; gm.triA = TRI_UPPER; gm.B = W;
+        gm.ldb = ld; gm.C = T1; gm.ldc = ld;
+        gemm(h, gm);                                                           // L^{-T} Phi L^{-1}
+        Timed t(h, K_HBM, 0, 48.0 * n * (double)n);
+        sym_average<double>(T1, ld, n, h->stream);                             // Mbar
+        copy_matrix(T1, ld, Hbar, ldhb, n, n, h->stream);
+        scale_rows(Hbar, ldhb, n, n, F.sig, h->stream);                        // Hbar = Sigma Mbar
+    } else {
+        cuda_check(h, cudaMemset2DAsync(Hbar, sizeof(double) * ldhb, 0, sizeof(double) * n, n, h->stream),
+                   "memset");
+    }
+    if (pos_weight != 0.0) {   // + pos_weight P_+^T = (pos_weight / 2)(I + L Y L^{-1})
+        GemmArgs g1; g1.m = g1.n = g1.k = n; g1.A = Y; g1.lda = ld; g1.B = Li; g1.ldb = ld; g1.triB = TRI_LOWER;
+        g1.C = W; g1.ldc = ld;
+        gemm(h, g1);                                                           // Y L^{-1}
+        GemmArgs g2; g2.m = g2.n = g2.k = n; g2.A = L; g2.lda = ld; g2.triA = TRI_LOWER; g2.B = W; g2.ldb = ld;
+        g2.Cin = Hbar; g2.ldcin = ldhb; g2.C = Hbar; g2.ldc = ldhb; g2.alpha = 0.5 * pos_weight; g2.beta = 1.0;
+        gemm(h, g2);
+        Timed t(h, K_HBM, 0, 16.0 * n);
+        add_diag<double>(Hbar, ldhb, n, 0.5 * pos_weight, h->stream);
+    }
+    cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+    release(h, mk);
+    return PSSD_OK;
+}
+}  // namespace
+
+extern "C" int pssd_sign_vjp_rev(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
+                                 const double *Sbar, int ldsb, double pos_weight, double *Hbar, int ldhb,
+                                 const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (Sbar && ldsb < n) return -7;
+    if (!std::isfinite(pos_weight)) return -8;
+    if (!Hbar) return -9;
+    if (ldhb < n) return -10;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o) || o.precision == PSSD_MIXED || o.method != PSSD_METHOD_ZOLO) return -11;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        Front F;
+        SignTape tape;
+        int st = front(h, n, sigma, H, ldh, o, info, F, nullptr, 0, &tape, !(o.flags & PSSD_FLAG_RECOMPUTE));
+        if (st) return st;
+        return sign_vjp_steps(h, F, tape, Sbar, ldsb, pos_weight, Hbar, ldhb);
+    });
+}
+
 extern "C" int pssd_sign_vjp(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh,
                              const double *Sbar, int ldsb, const double *lambar, double *Hbar, int ldhb,
                              const pssd_opts *opts, pssd_info *info)

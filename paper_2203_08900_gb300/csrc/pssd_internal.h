@@ -99,6 +99,7 @@ void dk_combine(const double *W, long long ldw, const double *lam, const double 
 // F = refinement correction of A ~ Z diag(lam) Z^T from S = Z^T A Z and Gm = Z^T Z - I (full, symmetric)
 void eig_refine_correction(const double *S, long long lds, const double *Gm, long long ldg, const double *lam, int n,
                            double omega, double *F, long long ldf, cudaStream_t s);
+void tril_half_diag(double *X, long long ldx, int n, cudaStream_t s);   // lower part, diagonal halved, upper zeroed
 void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
 template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
