@@ -124,3 +124,62 @@ def batch_sizes(count=512, k_lo=16, k_hi=1024, seed=0):
     rng = np.random.default_rng(seed)
     return np.clip(np.round(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi), count))),
                    k_lo, k_hi).astype(int)
+
+
+def haar_unitary(rng, k):
+    """Haar unitary k-by-k: QR of a complex Gaussian with the columns multiplied by
+    the phases of diag R."""
+    Z = (rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(Z)
+    d = np.diag(R)
+    return Q * (d / np.abs(d))[None, :]
+
+
+def bse2(k, dist=("uniform", 1.0, 10.0), seed=0, same_q=False):
+    """Complex Eq. (BSE2) form: P = Q1 diag(d1) Q1^H, R = Q2 diag(d2) Q2^H (Q1, Q2 Haar
+    unitary), A = (P + R)/2, B = (P - R)/2 (both Hermitian), H = [[A, B], [-B, -A]].
+    M = Sigma H = [[A, B], [B, A]] is unitarily similar to diag(P, R): Hermitian positive
+    definite for positive d; with Q1 = Q2 the eigenvalues are +-sqrt(d1_i d2_i).
+    Returns (H complex128 C order, d1, d2)."""
+    rng = np.random.default_rng(seed)
+    d1 = draw_d(rng, k, dist)
+    d2 = draw_d(rng, k, dist)
+    Q1 = haar_unitary(rng, k)
+    Q2 = Q1 if same_q else haar_unitary(rng, k)
+    P = (Q1 * d1[None, :]) @ Q1.conj().T
+    R = (Q2 * d2[None, :]) @ Q2.conj().T
+    P = 0.5 * (P + P.conj().T)
+    R = 0.5 * (R + R.conj().T)
+    A = 0.5 * (P + R)
+    B = 0.5 * (P - R)
+    H = np.block([[A, B], [-B, -A]])
+    return np.ascontiguousarray(H), d1, d2
+
+
+def bse2_blocks(k, d1, d2, rng, same_q=True):
+    """(A, B) of the Eq. (BSE2) form for given d1, d2 (Q1 = Q2 by default)."""
+    Q1 = haar_unitary(rng, k)
+    Q2 = Q1 if same_q else haar_unitary(rng, k)
+    P = (Q1 * d1[None, :]) @ Q1.conj().T
+    R = (Q2 * d2[None, :]) @ Q2.conj().T
+    P = 0.5 * (P + P.conj().T)
+    R = 0.5 * (R + R.conj().T)
+    return 0.5 * (P + R), 0.5 * (P - R)
+
+
+def bse1(k, dist=("uniform", 1.0, 10.0), coupling=0.5, seed=0):
+    """Complex Eq. (BSE1) form H = [[A, B], [-conj(B), -conj(A)]]: A = Q diag(d) Q^H
+    Hermitian (Q Haar unitary, d from dist), B complex symmetric (a symmetrised complex
+    Gaussian) scaled to ||B||_2 = coupling * min(d).  Then Sigma H = [[A, B], [conj(B),
+    conj(A)]] is Hermitian and, since ||B||_2 < lambda_min(A), positive definite.
+    Returns H (complex128, C order)."""
+    rng = np.random.default_rng(seed)
+    d = draw_d(rng, k, dist)
+    Q = haar_unitary(rng, k)
+    A = (Q * d[None, :]) @ Q.conj().T
+    A = 0.5 * (A + A.conj().T)
+    Z = rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))
+    B = 0.5 * (Z + Z.T)
+    B *= coupling * d.min() / np.linalg.norm(B, 2)
+    H = np.block([[A, B], [-B.conj(), -A.conj()]])
+    return np.ascontiguousarray(H)

@@ -394,6 +394,32 @@ int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch
                        long long ldcin, long long sCin, double *C, long long ldc, long long sC,
                        const double *kscale);
 
+/*
+ * Complex pseudo-Hermitian matrices (the Bethe-Salpeter forms, Eqs. BSE1 and BSE2: H = Sigma M
+ * with M Hermitian positive definite, e.g. [[A, B], [-conj(B), -conj(A)]] with A Hermitian and
+ * B complex symmetric, or [[A, B], [-B, -A]] with A, B Hermitian).  H is an n x n complex matrix,
+ * row-major, interleaved (re, im) doubles (the layout of cuDoubleComplex and torch.complex128),
+ * leading dimension ldh counted in complex elements; sigma as for pssd_sign (NULL:
+ * diag(I_{n/2}, -I_{n/2})).  The computation runs on the real embedding
+ * R(H) = [[Re H, -Im H], [Im H, Re H]] (2n x 2n), which is real definite pseudosymmetric with
+ * signature [sigma; sigma] and satisfies sign(R(H)) = R(sign(H)); 2n <= PSSD_MAX_N.
+ *
+ * pssd_zsign: S = sign(H) (complex n x n, ld lds in complex elements; S != H).
+ *   Returns -2..-5 as pssd_sign's checks of n, sigma, H, ldh; -6 (S), -7 (lds), -8 (options).
+ * pssd_zeig: V^{-1} H V = diag(D): D real (n, positive eigenvalues ascending, then negative ones
+ *   by ascending magnitude), V complex n x n (ld ldv in complex elements) with
+ *   V^H Sigma V = diag(sign(D)) (Eq. VSigmaOrth) and the largest-modulus entry of each column
+ *   real and positive.  Each eigenvalue of H appears twice in R(H); a pair gives one eigenvector
+ *   of H, and a group of 2q values within 1e-12 max|lambda| gives q eigenvectors by
+ *   Gram-Schmidt in the definite form x^H Sigma y of the group.
+ *   Returns -6 (V), -7 (ldv), -8 (D), -9 (options), or PSSD_ERR_BASIS if the doubled spectrum
+ *   cannot be paired.
+ */
+int pssd_zsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
+               const pssd_opts *opts, pssd_info *info);
+int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
+              double *D, const pssd_opts *opts, pssd_info *info);
+
 /* Test hook: the symmetric divide-and-conquer of Alg. 2 (Zolotarev sign of the
  * shifted subproblem, orthonormal split, recursion to Jacobi leaves of order <=
  * opts->leaf) on a symmetric m x m B (device, ld ldb), in the arithmetic of

@@ -560,3 +560,123 @@ def sign_vjp_block(H, G, tol: float = 1e-14):
     B[:n, :n] = H.T; B[n:, n:] = H.T; B[:n, n:] = G
     SB = newton_sign(B, tol=tol)
     return SB[:n, n:]
+
+
+# --------------------------------------------------------------------------
+# complex pseudo-Hermitian matrices (the BSE forms, Eqs. BSE1 and BSE2): the
+# definition layer in complex arithmetic, scalar loops (small n only)
+# --------------------------------------------------------------------------
+
+def zcholesky(M):
+    """M = L L^H for a Hermitian positive definite M (scalar loops, row by row);
+    L lower triangular with a real positive diagonal."""
+    M = np.array(M, dtype=np.complex128)
+    n = M.shape[0]
+    L = np.zeros((n, n), dtype=np.complex128)
+    for i in range(n):
+        for j in range(i + 1):
+            acc = M[i, j]
+            for k in range(j):
+                acc -= L[i, k] * np.conj(L[j, k])
+            if i == j:
+                d = acc.real
+                if not d > 0:
+                    raise NotDefinite("pivot %d is not positive" % i)
+                L[i, i] = math.sqrt(d)
+            else:
+                L[i, j] = acc / L[j, j]
+    return L
+
+
+def zupper_solve(U, B):
+    """X with U X = B for an upper triangular U (back substitution over rows)."""
+    U = np.asarray(U, dtype=np.complex128)
+    X = np.array(B, dtype=np.complex128)
+    n = U.shape[0]
+    for i in range(n - 1, -1, -1):
+        X[i] = (X[i] - U[i, i + 1:] @ X[i + 1:]) / U[i, i]
+    return X
+
+
+def zjacobi_eigh(A, max_sweeps: int = 60):
+    """Hermitian eigendecomposition by cyclic Jacobi: for each pair (p, q) with
+    a_pq = |a_pq| e^{i phi}, the unitary W = diag(1, e^{-i phi}) J (J the real
+    rotation that diagonalises [[a_pp, |a_pq|], [|a_pq|, a_qq]]) is applied as
+    A <- W^H A W on rows and columns p, q.  Eigenvalues ascending."""
+    A = np.array(A, dtype=np.complex128)
+    A = 0.5 * (A + A.conj().T)
+    n = A.shape[0]
+    U = np.eye(n, dtype=np.complex128)
+    for sweep in range(max_sweeps):
+        off = np.sum(np.abs(A - np.diag(np.diag(A))) ** 2)
+        if off <= 1e-30 * np.sum(np.abs(A) ** 2):
+            break
+        for p in range(n - 1):
+            for q in range(p + 1, n):
+                b = A[p, q]
+                ab = abs(b)
+                if ab == 0.0:
+                    continue
+                ph = b / ab                                   # e^{i phi}
+                tau = (A[q, q].real - A[p, p].real) / (2.0 * ab)
+                t = (1.0 if tau >= 0 else -1.0) / (abs(tau) + math.sqrt(1.0 + tau * tau))
+                c = 1.0 / math.sqrt(1.0 + t * t)
+                s = t * c
+                # W = [[c, s], [-s conj(ph), c conj(ph)]] on columns p, q
+                cp = A[:, p].copy(); cq = A[:, q].copy()
+                A[:, p] = c * cp - s * np.conj(ph) * cq
+                A[:, q] = s * cp + c * np.conj(ph) * cq
+                rp = A[p, :].copy(); rq = A[q, :].copy()
+                A[p, :] = c * rp - s * ph * rq
+                A[q, :] = s * rp + c * ph * rq
+                up = U[:, p].copy(); uq = U[:, q].copy()
+                U[:, p] = c * up - s * np.conj(ph) * uq
+                U[:, q] = s * up + c * np.conj(ph) * uq
+    else:
+        raise RuntimeError("complex Jacobi did not converge")
+    w = np.diag(A).real.copy()
+    idx = np.argsort(w, kind="stable")
+    return w[idx], np.ascontiguousarray(U[:, idx])
+
+
+def _phase_fix_columns(V):
+    """Each column multiplied by conj(v_max)/|v_max|, v_max its entry of largest
+    modulus (first on ties): that entry becomes real and positive."""
+    V = np.array(V, dtype=np.complex128)
+    for j in range(V.shape[1]):
+        i = int(np.argmax(np.abs(V[:, j])))
+        a = abs(V[i, j])
+        if a > 0:
+            V[:, j] *= np.conj(V[i, j]) / a
+    return V
+
+
+def zeig_def(H, sigma=None):
+    """Definition-level eigendecomposition of a definite complex pseudo-Hermitian H
+    (Sigma H Hermitian positive definite): M = Sigma H = L L^H (scalar Cholesky),
+    K = L^H Sigma L is Hermitian and similar to H (L^H H L^{-H} = K), so
+    lambda(H) = lambda(K) (complex Jacobi), and v = sqrt|lambda| L^{-H} u has
+    v^H Sigma v = sign(lambda) (Eq. VSigmaOrth, the complex case of Thm.
+    EVRealSigmaOrth).  Returns (lam, V) in the output convention, phases fixed."""
+    H = np.asarray(H, dtype=np.complex128)
+    n = H.shape[0]
+    s = signature(n, sigma)
+    M = s[:, None] * H
+    M = 0.5 * (M + M.conj().T)
+    L = zcholesky(M)
+    K = L.conj().T @ (s[:, None] * L)
+    w, U = zjacobi_eigh(K)
+    Y = zupper_solve(L.conj().T, U)                 # L^{-H} U
+    V = Y * np.sqrt(np.abs(w))[None, :]
+    lam, V = _order(w, V)
+    return lam, _phase_fix_columns(V)
+
+
+def zsign_def(H, sigma=None):
+    """sign(H) = V sign(Lambda) V^{-1} with V^{-1} = Sigma_hat V^H Sigma, i.e.
+    S = V V^H Sigma (Eq. signDef, complex case)."""
+    H = np.asarray(H, dtype=np.complex128)
+    n = H.shape[0]
+    s = signature(n, sigma)
+    _, V = zeig_def(H, sigma)
+    return (V @ V.conj().T) * s[None, :]

@@ -71,7 +71,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
            "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
-           "pssd_test_sym_eig", "pssd_sign_vjp_rev"]
+           "pssd_test_sym_eig", "pssd_sign_vjp_rev", "pssd_zsign", "pssd_zeig"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -106,6 +106,8 @@ def lib():
                                       ctypes.POINTER(Info)]
     L.pssd_sign_vjp_rev.argtypes = sig + [vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, ctypes.POINTER(Opts),
                                           ctypes.POINTER(Info)]
+    L.pssd_zsign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_zeig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     ll = ctypes.c_longlong
     L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
                                      vp, ll, ll, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
@@ -449,6 +451,44 @@ def sign_vjp_rev(H, Sbar=None, pos_weight=0.0, sigma=None, handle=None, **kw):
                                  ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return Hbar
+
+
+def _check_Hz(H):
+    if not (isinstance(H, torch.Tensor) and H.is_cuda and H.dtype == torch.complex128 and H.dim() == 2
+            and H.shape[0] == H.shape[1] and H.stride(1) == 1):
+        raise ValueError("H must be a square row-major complex128 CUDA tensor")
+    return H.shape[0], H.stride(0)
+
+
+def zsign(H, sigma=None, handle=None, **kw):
+    """sign(H) of a complex pseudo-Hermitian H (complex128 CUDA tensor; the BSE forms).
+    Returns (S, info)."""
+    n, ldh = _check_Hz(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    S = torch.empty_like(H)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_zsign(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
+                          S.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return S, info.as_dict()
+
+
+def zeig(H, sigma=None, handle=None, **kw):
+    """Full diagonalisation of a complex pseudo-Hermitian H: (D real, V complex, info) with
+    V^{-1} H V = diag(D) and V^H Sigma V = diag(sign(D))."""
+    n, ldh = _check_Hz(H)
+    h = _handle(handle)
+    keep, sp = _sigma(n, sigma)
+    V = torch.empty_like(H)
+    D = torch.empty(n, dtype=torch.float64, device=H.device)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_zeig(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(V.data_ptr()),
+                         V.stride(0), ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return D, V, info.as_dict()
 
 
 class SignFn(torch.autograd.Function):

@@ -761,6 +761,87 @@ void tril_half_diag(double *X, long long ldx, int n, cudaStream_t s)
     tril_half_diag_kernel<<<dim3(gx, n), 256, 0, s>>>(X, ldx, n); count_launch();
 }
 
+// Real embedding of a complex n x n matrix Z (interleaved re/im doubles, row-major, ld in
+// complex elements): R = [[Re Z, -Im Z], [Im Z, Re Z]] (2n x 2n, ld ldr).  Z -> R is an
+// injective real algebra homomorphism with R(Z^H) = R(Z)^T.
+__global__ void complex_embed_kernel(const double *Z, long long ldz, int n, double *R, long long ldr)
+{
+    const int i = blockIdx.y;
+    const double2 *z = reinterpret_cast<const double2 *>(Z) + (long long)i * ldz;
+    double *r0 = R + (long long)i * ldr, *r1 = R + (long long)(i + n) * ldr;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double2 v = z[j];
+        r0[j] = v.x; r0[j + n] = -v.y;
+        r1[j] = v.y; r1[j + n] = v.x;
+    }
+}
+
+void complex_embed(const double *Z, long long ldz, int n, double *R, long long ldr, cudaStream_t s)
+{
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    complex_embed_kernel<<<dim3(gx, n), 256, 0, s>>>(Z, ldz, n, R, ldr); count_launch();
+}
+
+// The inverse on the first block column: Z[i][j] = R[i][j] + i R[i + n][j] for j < m
+// (columns j of R taken in the order perm[0..m) when perm is given)
+__global__ void complex_extract_kernel(const double *R, long long ldr, int n, int m, const int *perm, double *Z,
+                                       long long ldz)
+{
+    const int i = blockIdx.y;
+    double2 *z = reinterpret_cast<double2 *>(Z) + (long long)i * ldz;
+    const double *r0 = R + (long long)i * ldr, *r1 = R + (long long)(i + n) * ldr;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const int c = perm ? perm[j] : j;
+        z[j] = make_double2(r0[c], r1[c]);
+    }
+}
+
+void complex_extract(const double *R, long long ldr, int n, int m, const int *perm, double *Z, long long ldz,
+                     cudaStream_t s)
+{
+    int gx = (m + 255) / 256; if (gx > 16) gx = 16;
+    complex_extract_kernel<<<dim3(gx, n), 256, 0, s>>>(R, ldr, n, m, perm, Z, ldz); count_launch();
+}
+
+// Column phase convention for complex eigenvectors: each column of Z (m x n, interleaved)
+// is multiplied by conj(z_max)/|z_max|, z_max its entry of largest modulus (first one on
+// ties), so that entry becomes real and positive.  One block per column.
+__global__ void complex_phase_fix_kernel(double *Z, long long ldz, int m, int n)
+{
+    __shared__ double bm[256];
+    __shared__ int bi[256];
+    const int c = blockIdx.x, t = threadIdx.x;
+    double2 *z = reinterpret_cast<double2 *>(Z);
+    double best = -1.0; int bidx = 0;
+    for (int i = t; i < m; i += blockDim.x) {
+        const double2 v = z[(long long)i * ldz + c];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bidx = i; }
+    }
+    bm[t] = best; bi[t] = bidx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o && (bm[t + o] > bm[t] || (bm[t + o] == bm[t] && bi[t + o] < bi[t]))) {
+            bm[t] = bm[t + o]; bi[t] = bi[t + o];
+        }
+        __syncthreads();
+    }
+    const double2 p = z[(long long)bi[0] * ldz + c];
+    const double a = sqrt(p.x * p.x + p.y * p.y);
+    if (!(a > 0.0)) return;
+    const double cr = p.x / a, ci = -p.y / a;     // conj(p) / |p|
+    for (int i = t; i < m; i += blockDim.x) {
+        double2 &v = z[(long long)i * ldz + c];
+        const double x = v.x * cr - v.y * ci, y = v.x * ci + v.y * cr;
+        v = make_double2(x, y);
+    }
+}
+
+void complex_phase_fix(double *Z, long long ldz, int m, int n, cudaStream_t s)
+{
+    complex_phase_fix_kernel<<<n, 256, 0, s>>>(Z, ldz, m, n); count_launch();
+}
+
 // X[i][j] *= r[i] (row scaling)
 __global__ void scale_rows_kernel(double *X, long long ldx, int m, int n, const double *r)
 {

@@ -32,6 +32,7 @@
 #include <string>
 #include <vector>
 #include <cfloat>
+#include <complex>
 
 #include "pssd.h"
 #include "pssd_internal.h"
@@ -1785,6 +1786,61 @@ int pssd_choose_r(double ell, double tau, int r_max)
     return choose_r_host(ell, tau, r_max);
 }
 
+}  // extern "C"
+
+namespace {
+// the body of pssd_sign (inside a guarded call): S = L^{-T} sign(K) L^T, mixed-precision
+// re-symmetrisation and Newton-Schulz, residuals
+int sign_core(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
+              const pssd_opts &o, pssd_info *info)
+{
+    Front F;
+    int st = front(h, n, sigma, H, ldh, o, info, F);
+    if (st) return st;
+    const long long ld = n, nsz = (long long)n * n;
+    double *T1 = dalloc(h, nsz);
+    GemmArgs a;   // T1 = Y L^T
+    a.m = a.n = a.k = n; a.A = F.Y; a.lda = ld; a.B = F.L; a.ldb = ld; a.tb = 1; a.triB = TRI_UPPER;
+    a.C = T1; a.ldc = ld;
+    gemm(h, a);
+    GemmArgs b;   // S = L^{-T} T1
+    b.m = b.n = b.k = n; b.A = F.Linv; b.lda = ld; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = ld;
+    b.C = S; b.ldc = lds;
+    gemm(h, b);
+    if (o.precision == PSSD_MIXED) {
+        // north star (1): J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
+        // Sigma-symmetric S stay Sigma-symmetric), in FP64-accurate arithmetic
+        {
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+            j_resym(S, lds, F.sig, n, h->stream);
+        }
+        double res; int its;
+        int st2 = ns_refine(h, S, n, 1e-14 * n, 3, &res, &its, false, lds);
+        if (st2) return st2;
+        if (info) info->ns_steps += its;
+    }
+    if (info)
+        info->comm_resid = comm_resid(h, n, H, ldh, F.normH, S, lds, nullptr, 0, F.sig,
+                                      (o.flags & PSSD_FLAG_RESIDUALS) != 0);
+    if (o.flags & 1) {   // residuals
+        double *S2 = dalloc(h, nsz);
+        GemmArgs c; c.m = c.n = c.k = n; c.A = S; c.lda = lds; c.B = S; c.ldb = lds; c.C = S2; c.ldc = ld;
+        gemm(h, c);
+        {
+            Timed t(h, K_HBM, 0, 16.0 * n);
+            add_diag(S2, ld, n, -1.0, h->stream);
+        }
+        double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+        double d2, y2;
+        frob_pair(h, nullptr, ld, S2, ld, n, n, part, &d2, &y2);
+        if (info) info->s2_resid = std::sqrt(y2);
+    }
+    return PSSD_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
               const pssd_opts *opts, pssd_info *info)
 {
@@ -1797,50 +1853,7 @@ int pssd_sign(pssd_handle h, int n, const signed char *sigma, const double *H, i
     pssd_opts o = opts ? *opts : defaults();
     if (opts_bad(o)) return -8;
     info_init(info);
-    return guarded(h, info, [&]() -> int {
-        Front F;
-        int st = front(h, n, sigma, H, ldh, o, info, F);
-        if (st) return st;
-        const long long ld = n, nsz = (long long)n * n;
-        double *T1 = dalloc(h, nsz);
-        GemmArgs a;   // T1 = Y L^T
-        a.m = a.n = a.k = n; a.A = F.Y; a.lda = ld; a.B = F.L; a.ldb = ld; a.tb = 1; a.triB = TRI_UPPER;
-        a.C = T1; a.ldc = ld;
-        gemm(h, a);
-        GemmArgs b;   // S = L^{-T} T1
-        b.m = b.n = b.k = n; b.A = F.Linv; b.lda = ld; b.ta = 1; b.triA = TRI_UPPER; b.B = T1; b.ldb = ld;
-        b.C = S; b.ldc = lds;
-        gemm(h, b);
-        if (o.precision == PSSD_MIXED) {
-            // north star (1): J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
-            // Sigma-symmetric S stay Sigma-symmetric), in FP64-accurate arithmetic
-            {
-                Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
-                j_resym(S, lds, F.sig, n, h->stream);
-            }
-            double res; int its;
-            int st2 = ns_refine(h, S, n, 1e-14 * n, 3, &res, &its, false, lds);
-            if (st2) return st2;
-            if (info) info->ns_steps += its;
-        }
-        if (info)
-            info->comm_resid = comm_resid(h, n, H, ldh, F.normH, S, lds, nullptr, 0, F.sig,
-                                          (o.flags & PSSD_FLAG_RESIDUALS) != 0);
-        if (o.flags & 1) {   // residuals
-            double *S2 = dalloc(h, nsz);
-            GemmArgs c; c.m = c.n = c.k = n; c.A = S; c.lda = lds; c.B = S; c.ldb = lds; c.C = S2; c.ldc = ld;
-            gemm(h, c);
-            {
-                Timed t(h, K_HBM, 0, 16.0 * n);
-                add_diag(S2, ld, n, -1.0, h->stream);
-            }
-            double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
-            double d2, y2;
-            frob_pair(h, nullptr, ld, S2, ld, n, n, part, &d2, &y2);
-            if (info) info->s2_resid = std::sqrt(y2);
-        }
-        return PSSD_OK;
-    });
+    return guarded(h, info, [&]() -> int { return sign_core(h, n, sigma, H, ldh, S, lds, o, info); });
 }
 
 int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, const double *S_in,
@@ -2892,6 +2905,181 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
 // arithmetic for the given precision mode (PSSD_FP64 or PSSD_FP64_EMULATED):
 // W (m x m, columns eigenvectors, unordered) and w (m eigenvalues), device
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Complex pseudo-Hermitian H = Sigma M (M Hermitian positive definite; the BSE forms,
+// Eqs. BSE1 and BSE2) through the real embedding R(Z) = [[Re Z, -Im Z], [Im Z, Re Z]]:
+// R is an injective real algebra homomorphism with R(Z^H) = R(Z)^T, so R(H) = R(Sigma) R(M)
+// is real definite pseudosymmetric with signature [sigma; sigma], sign(R(H)) = R(sign(H)),
+// and every eigenvalue of H appears twice in R(H) with the real eigenvectors [Re v; Im v]
+// and [-Im v; Re v] of an eigenvector v of H.
+// ---------------------------------------------------------------------------
+namespace {
+int zvalidate(int n, const signed char *sigma, const double *H, int ldh)
+{
+    if (n < 1 || 2LL * n > PSSD_MAX_N) return -2;
+    if (!sigma && (n % 2)) return -3;
+    if (sigma)
+        for (int i = 0; i < n; ++i) if (sigma[i] != 1 && sigma[i] != -1) return -3;
+    if (!H) return -4;
+    if (ldh < n) return -5;
+    return 0;
+}
+
+std::vector<signed char> embedded_signature(int n, const signed char *sigma)
+{
+    std::vector<signed char> s2(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) s2[i] = s2[i + n] = sigma ? sigma[i] : (i < n / 2 ? 1 : -1);
+    return s2;
+}
+}  // namespace
+
+extern "C" int pssd_zsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S,
+                          int lds, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = zvalidate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!S || S == H) return -6;
+    if (lds < n) return -7;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o)) return -8;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        const int m = 2 * n;
+        const long long msz = (long long)m * m;
+        double *R = dalloc(h, msz), *SR = dalloc(h, msz);
+        {
+            Timed t(h, K_HBM, 0, 48.0 * n * (double)n);
+            complex_embed(H, ldh, n, R, m, h->stream);
+        }
+        std::vector<signed char> s2 = embedded_signature(n, sigma);
+        int st = sign_core(h, m, s2.data(), R, m, SR, m, o, info);
+        if (st) return st;
+        if (info) info->p /= 2;
+        Timed t(h, K_HBM, 0, 32.0 * n * (double)n);
+        complex_extract(SR, m, n, n, nullptr, S, lds, h->stream);
+        return PSSD_OK;
+    });
+}
+
+extern "C" int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V,
+                         int ldv, double *D, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = zvalidate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!V) return -6;
+    if (ldv < n) return -7;
+    if (!D) return -8;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o)) return -9;
+    const int leaf = o.leaf > 0 ? std::min(o.leaf, 64) : 64;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        const int m = 2 * n;
+        const long long msz = (long long)m * m;
+        double *R = dalloc(h, msz), *VR = dalloc(h, msz), *DR = dalloc(h, m);
+        {
+            Timed t(h, K_HBM, 0, 48.0 * n * (double)n);
+            complex_embed(H, ldh, n, R, m, h->stream);
+        }
+        std::vector<signed char> s2 = embedded_signature(n, sigma);
+        int st = eig_core(h, m, s2.data(), R, m, VR, m, DR, o, info, leaf);
+        if (st) return st;
+        if (info) info->p /= 2;
+        std::vector<double> hd(m);
+        d2h_sync(h, hd.data(), DR, sizeof(double) * m);
+        // Each eigenvalue of H appears twice, adjacent in the library's order (positive ascending,
+        // then negative by ascending magnitude).  Groups of values within 1e-12 max|lambda| of
+        // their neighbour (extended to an even size) are one eigenspace of H: a pair gives one
+        // eigenvector from either real vector; a larger group of 2q gives q eigenvectors by
+        // Gram-Schmidt in the definite form s x^H Sigma y (s = the group's sign), pivoted on the
+        // largest remaining norm.
+        double scale = 0.0;
+        for (double x : hd) scale = std::max(scale, std::fabs(x));
+        const double tol = 1e-12 * scale;
+        std::vector<int> perm(n, 0);
+        std::vector<double> dout(n);
+        struct Group { int first, size, out; };
+        std::vector<Group> groups;                 // groups larger than a pair
+        int outpos = 0;
+        for (int i = 0; i < m;) {
+            int j = i + 1;
+            while (j < m && ((j - i) % 2 == 1 || std::fabs(hd[j] - hd[j - 1]) <= tol) &&
+                   (hd[j] > 0) == (hd[i] > 0))
+                ++j;
+            const int sz = j - i;
+            if (sz % 2) return PSSD_ERR_BASIS;
+            double mean = 0.0;
+            for (int t = i; t < j; ++t) mean += hd[t];
+            mean /= sz;
+            for (int q = 0; q < sz / 2; ++q) { perm[outpos + q] = i; dout[outpos + q] = mean; }
+            if (sz > 2) groups.push_back({i, sz, outpos});
+            outpos += sz / 2;
+            i = j;
+        }
+        if (outpos != n) return PSSD_ERR_BASIS;
+        int *dperm = ialloc(h, n);
+        h2d(h, dperm, perm.data(), sizeof(int) * n);
+        h2d(h, D, dout.data(), sizeof(double) * n);
+        {
+            Timed t(h, K_HBM, 0, 32.0 * n * (double)n);
+            complex_extract(VR, m, n, n, dperm, V, ldv, h->stream);
+        }
+        if (!groups.empty()) {
+            std::vector<double> hs(n);
+            for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+            for (const Group &g : groups) {
+                    const int i = g.first, sz = g.size, q = sz / 2, pos = g.out;
+                    const double sgn = hd[i] > 0 ? 1.0 : -1.0;
+                    // candidates w_t = VR[:n, c] + i VR[n:, c], c = i .. i + sz - 1
+                    std::vector<double> col((size_t)m);
+                    std::vector<std::vector<std::complex<double>>> w(sz, std::vector<std::complex<double>>(n));
+                    for (int t = 0; t < sz; ++t) {
+                        cuda_check(h, cudaMemcpy2DAsync(col.data(), sizeof(double), VR + i + t, sizeof(double) * m,
+                                                        sizeof(double), m, cudaMemcpyDeviceToHost, h->stream),
+                                   "cudaMemcpy2DAsync");
+                        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+                        for (int r = 0; r < n; ++r) w[t][r] = {col[r], col[r + n]};
+                    }
+                    auto form = [&](const std::vector<std::complex<double>> &x, const std::vector<std::complex<double>> &y) {
+                        std::complex<double> acc = 0.0;
+                        for (int r = 0; r < n; ++r) acc += std::conj(x[r]) * hs[r] * y[r];
+                        return sgn * acc;
+                    };
+                    std::vector<char> used(sz, 0);
+                    std::vector<double> out(2 * (size_t)n);
+                    for (int k = 0; k < q; ++k) {
+                        int best = -1; double bn = -1.0;
+                        for (int t = 0; t < sz; ++t)
+                            if (!used[t]) { const double nn = form(w[t], w[t]).real(); if (nn > bn) { bn = nn; best = t; } }
+                        if (best < 0 || !(bn > 0.0)) return PSSD_ERR_BASIS;
+                        used[best] = 1;
+                        const double f = 1.0 / std::sqrt(bn);
+                        for (auto &x : w[best]) x *= f;
+                        for (int t = 0; t < sz; ++t)
+                            if (!used[t]) {
+                                const std::complex<double> c = form(w[best], w[t]);
+                                for (int r = 0; r < n; ++r) w[t][r] -= c * w[best][r];
+                            }
+                        for (int r = 0; r < n; ++r) { out[2 * r] = w[best][r].real(); out[2 * r + 1] = w[best][r].imag(); }
+                        cuda_check(h, cudaMemcpy2DAsync(V + 2 * (size_t)(pos + k), sizeof(double) * 2 * ldv, out.data(),
+                                                        2 * sizeof(double), 2 * sizeof(double), n,
+                                                        cudaMemcpyHostToDevice, h->stream),
+                                   "cudaMemcpy2DAsync");
+                        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+                    }
+            }
+        }
+        {
+            Timed t(h, K_HBM, 0, 32.0 * n * (double)n);
+            complex_phase_fix(V, ldv, n, n, h->stream);
+        }
+        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
+        return PSSD_OK;
+    });
+}
+
 extern "C" int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb, double *W, int ldw, double *w,
                                  const pssd_opts *opts, pssd_info *info)
 {

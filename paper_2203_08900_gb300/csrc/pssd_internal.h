@@ -100,6 +100,11 @@ void dk_combine(const double *W, long long ldw, const double *lam, const double 
 void eig_refine_correction(const double *S, long long lds, const double *Gm, long long ldg, const double *lam, int n,
                            double omega, double *F, long long ldf, cudaStream_t s);
 void tril_half_diag(double *X, long long ldx, int n, cudaStream_t s);   // lower part, diagonal halved, upper zeroed
+// complex n x n (interleaved, ld in complex elements) <-> real embedding [[Re, -Im], [Im, Re]]
+void complex_embed(const double *Z, long long ldz, int n, double *R, long long ldr, cudaStream_t s);
+void complex_extract(const double *R, long long ldr, int n, int m, const int *perm, double *Z, long long ldz,
+                     cudaStream_t s);   // Z[:, j] = R[:n, perm[j]] + i R[n:, perm[j]]
+void complex_phase_fix(double *Z, long long ldz, int m, int n, cudaStream_t s);   // largest entry of each column real > 0
 void scale_rows(double *X, long long ldx, int m, int n, const double *r, cudaStream_t s);  // out[0] = sum x (one block, fixed order)
 template <class T>
 void mirror_lower(T *A, long long lda, long long sA, int n, int batch, cudaStream_t s);
