@@ -535,6 +535,48 @@ def main():
             "note": "pssd_casida_eig on the blocks A, B of the same H (1 warm-up); checks untimed"}
         del De, Ve
         del Ab, Bb
+        # config 5: the step-reversal adjoint of <G, S> + sum of positive eigenvalues at n = 2048
+        # (d ~ U[1,10], G symmetric N(0,1)), FP64: one warm-up, one timed backward (its forward included)
+        ka = 1024
+        Ha, _, _ = G.casida_torch(ka, ("uniform", 1.0, 10.0), seed=2048, device=dev)
+        ga = torch.Generator(device=dev); ga.manual_seed(3)
+        Ga = torch.randn(2 * ka, 2 * ka, dtype=torch.float64, device=dev, generator=ga)
+        Ga = 0.5 * (Ga + Ga.T)
+        P.sign_vjp_rev(Ha, Ga, pos_weight=1.0, handle=h)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Hbar = P.sign_vjp_rev(Ha, Ga, pos_weight=1.0, handle=h)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        line["adjoint_n2048"] = {"s_per_gradient": g0.elapsed_time(g1) / 1e3, "precision": "fp64",
+                                 "gradient_fro_norm": float(torch.linalg.norm(Hbar)),
+                                 "note": "pssd_sign_vjp_rev: forward Zolotarev sign with its record + reversed steps, "
+                                         "congruence and Cholesky; loss <G,S> + sum of positive eigenvalues"}
+        del Ha, Ga, Hbar
+        # config 4: 512 Casida matrices, k log-uniform in [16, 1024], d ~ U[0.5, 50], mixed precision,
+        # pssd_eig_batched: one warm-up, one timed call; max relative residual checked untimed
+        ks = G.batch_sizes(512, 16, 1024, seed=0)
+        Hs = [G.casida_torch(int(kk), ("uniform", 0.5, 50.0), seed=10000 + i, device=dev)[0].contiguous()
+              for i, kk in enumerate(ks)]
+        torch.cuda.synchronize()
+        P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
+        torch.cuda.synchronize()
+        lb0 = h.launch_count()
+        g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Ds, Vs, _ = P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tb = g0.elapsed_time(g1) / 1e3
+        with torch.no_grad():
+            resb = max(float(torch.linalg.norm(Hx @ Vx - Vx * Dx) / torch.linalg.norm(Hx))
+                       for Hx, Dx, Vx in zip(Hs, Ds, Vs))
+        line["batch_config4"] = {"s_per_step": tb, "instances_per_s": len(Hs) / tb, "instances": len(Hs),
+                                 "precision": "mixed", "max_rel_residual": resb,
+                                 "gpu_launches": h.launch_count() - lb0,
+                                 "note": "pssd_eig_batched (host work queue over 16 worker streams)"}
+        del Hs, Ds, Vs
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(n)
     if rank == 0:

@@ -417,6 +417,39 @@ __device__ __forceinline__ long long oz_fixed56(double v, int e)
     return (b >> 63) ? -(long long)f : (long long)f;
 }
 
+// float bit pattern of a small integer d (|d| <= 256) through the float 2^23 + 128: the
+// integer add lands d in the last mantissa bits and one float subtraction (exact, Sterbenz)
+// leaves float(d); its upper 16 bits are the BF16 pattern of d, exactly, since d has at most
+// 9 significant bits.  Full-rate integer and FP32 instructions instead of two conversions.
+__device__ __forceinline__ uint32_t oz_small_int_bits(int d)
+{
+    return __float_as_uint(__int_as_float(0x4B000080 + d) - 8388736.0f);
+}
+
+// the eight balanced base-128 digits of F (|F| <= 2^56) as float bit patterns, most
+// significant first: d_8 .. d_2 in [-64, 63], the rest d_1 (|d_1| <= 128).  F = hi 2^28 + lo
+// with lo in [0, 2^28): the four low digits come from lo in 32-bit arithmetic (leaving a carry
+// of 0 or 1, added to hi), the other four from hi -- the same digits as extracting from F.
+__device__ __forceinline__ void oz_digits(long long F, uint32_t *bits)
+{
+    int lo = (int)(F & 0x0FFFFFFFLL);
+    int hi = (int)(F >> 28);
+#pragma unroll
+    for (int t = OZ_S; t >= OZ_S - 3; --t) {
+        const int c = ((lo + 64) & 127) - 64;
+        lo = (lo - c) >> 7;
+        bits[t - 1] = oz_small_int_bits(c);
+    }
+    hi += lo;
+#pragma unroll
+    for (int t = OZ_S - 4; t >= 2; --t) {
+        const int c = ((hi + 64) & 127) - 64;
+        hi = (hi - c) >> 7;
+        bits[t - 1] = oz_small_int_bits(c);
+    }
+    bits[0] = oz_small_int_bits(hi);
+}
+
 // One operand of the preparation passes: op(X) is rows x k (trans: op(X)[r][p] = X[p][r]),
 // with structural zeros (tri), an optional inner scaling ks[p], rows padded to rows_pad.
 struct OzOperand {
@@ -536,19 +569,11 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand a, OzOperand b,
     uint32_t w[OZ_S][4];
 #pragma unroll
     for (int q = 0; q < 8; q += 2) {
-        long long fa = f[q], fb = f[q + 1];
-        uint16_t da[OZ_S], db[OZ_S];
+        uint32_t ba[OZ_S], bb[OZ_S];
+        oz_digits(f[q], ba);
+        oz_digits(f[q + 1], bb);
 #pragma unroll
-        for (int t = OZ_S; t >= 2; --t) {
-            const int ca = (int)((fa + 64) & 127) - 64, cb = (int)((fb + 64) & 127) - 64;
-            fa = (fa - ca) >> 7; fb = (fb - cb) >> 7;
-            da[t - 1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)ca));
-            db[t - 1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)cb));
-        }
-        da[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)fa));
-        db[0] = __bfloat16_as_ushort(__float2bfloat16_rn((float)fb));
-#pragma unroll
-        for (int t = 0; t < OZ_S; ++t) w[t][q >> 1] = (uint32_t)da[t] | ((uint32_t)db[t] << 16);
+        for (int t = 0; t < OZ_S; ++t) w[t][q >> 1] = __byte_perm(ba[t], bb[t], 0x7632);   // two upper halves
     }
 #pragma unroll
     for (int t = 0; t < OZ_S; ++t)
