@@ -1163,12 +1163,15 @@ void small_sym_eig(std::vector<double> A, int n, std::vector<double> &w, std::ve
 // after the last step: [theta_1 - beta_s, theta_s + beta_s] encloses the spectrum of B in
 // practice (the extreme Ritz values converge first, from inside).  Returns false if the
 // recurrence produced a non-finite value.
-bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::vector<double> &th,
-                   std::vector<double> &tau, double *resid)
+template <class F>
+bool lanczos_run(pssd_handle h, int m, F apply, uint64_t seed, std::vector<double> &th, std::vector<double> &tau,
+                 double *resid, double *rtop = nullptr)
 {
+    // apply(v, w): w = A v for the symmetric operator A (m-vectors on the device).
+    // rtop (optional): beta_s |z_s| of the largest Ritz value, the norm of its Ritz residual
     const int steps = std::min(m, 24);
     Mark mk = mark(h);
-    double *V = dalloc(h, 3 * (size_t)m), *ab = dalloc(h, 2 * (size_t)steps + 2), *tmp = dalloc(h, 32 * (size_t)m + 8);
+    double *V = dalloc(h, 3 * (size_t)m), *ab = dalloc(h, 2 * (size_t)steps + 2);
     double *vp = V, *vc = V + m, *w = V + 2 * m;
     double *al = ab, *be = ab + steps + 1;
     {
@@ -1177,8 +1180,8 @@ bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::ve
         normalize_vec(vc, vc, m, nullptr, h->stream);
     }
     for (int j = 0; j < steps; ++j) {
-        Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
-        gemv(B, m, 0, TRI_NONE, m, vc, w, tmp, h->stream);                       // w = B v_j
+        apply(vc, w);                                                             // w = A v_j
+        Timed t(h, K_GEMV, 0, 40.0 * m);
         dot_vec(vc, w, m, al + j, h->stream);                                     // alpha_j
         lanczos_update(w, vc, j ? vp : nullptr, al + j, j ? be + j - 1 : nullptr, m, h->stream);
         normalize_vec(w, vp, m, be + j, h->stream);                               // beta_j, v_{j+1}
@@ -1201,7 +1204,34 @@ bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::ve
     small_sym_eig(T, s, th, Z);
     tau.resize(s);
     for (int j = 0; j < s; ++j) tau[j] = Z[j] * Z[j];   // first component of eigenvector j
+    if (rtop) *rtop = *resid * std::fabs(Z[(size_t)(s - 1) * s + (s - 1)]);
     return true;
+}
+
+bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::vector<double> &th,
+                   std::vector<double> &tau, double *resid)
+{
+    Mark mk = mark(h);
+    double *tmp = dalloc(h, 32 * (size_t)m + 8);
+    const bool ok = lanczos_run(h, m, [&](const double *x, double *y) {
+        Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
+        gemv(B, m, 0, TRI_NONE, m, x, y, tmp, h->stream);
+    }, seed, th, tau, resid);
+    release(h, mk);
+    return ok;
+}
+
+// An estimate of lambda_max of a symmetric positive semidefinite operator (apply: y = A x)
+// from below: the largest Ritz value of 24 Lanczos steps (the extreme Ritz value converges
+// first and faster than the power method's Rayleigh quotient), or 60 power steps if the
+// recurrence fails.  Callers add their safety factors (reading R5).
+template <class F>
+double lmax_estimate(pssd_handle h, int n, F apply, uint64_t seed, double *v, double *w, double *dscal)
+{
+    std::vector<double> th, tau;
+    double res;
+    if (lanczos_run(h, n, apply, seed, th, tau, &res) && th.back() > 0.0) return th.back();
+    return power_max(h, n, apply, v, w, dscal, 60);
 }
 
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
@@ -1554,21 +1584,17 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         double *v = dalloc(h, n), *w = dalloc(h, n), *u = dalloc(h, n), *tmp = dalloc(h, 32 * (size_t)n + 8);
         double *M = F.M, *Li = F.Linv;
         cudaStream_t s = h->stream;
-        if (!(alpha > 0.0)) {
-            double rq = power_max(h, n, [&](double *x, double *y) {
+        if (!(alpha > 0.0))
+            alpha = 1.05 * lmax_estimate(h, n, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);
                 gemv(M, ld, 0, TRI_NONE, n, x, y, tmp, s);
-            }, v, w, tmp + 32 * (size_t)n, 60);
-            alpha = 1.05 * rq;
-        }
-        if (!(beta > 0.0)) {
-            double rq = power_max(h, n, [&](double *x, double *y) {
+            }, 0xa1fa0001ull, v, w, tmp + 32 * (size_t)n);
+        if (!(beta > 0.0))
+            beta = 0.9 / lmax_estimate(h, n, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);  // two triangular halves
                 gemv(Li, ld, 0, TRI_LOWER, n, x, u, tmp, s);     // u = L^{-1} x
                 gemv(Li, ld, 1, TRI_UPPER, n, u, y, tmp, s);     // y = L^{-T} u
-            }, v, w, tmp + 32 * (size_t)n, 60);
-            beta = 0.9 / rq;
-        }
+            }, 0xbe7a0001ull, v, w, tmp + 32 * (size_t)n);
         release(h, mk);
     }
     if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;
@@ -2514,27 +2540,24 @@ int casida_polar(pssd_handle h, CasFront &F, const pssd_opts &o, pssd_info *info
     double alpha = o.alpha, beta = o.beta;
     if (!(alpha > 0.0) || !(beta > 0.0)) {
         Mark mk = mark(h);
-        double *v = dalloc(h, k), *w = dalloc(h, k), *u = dalloc(h, k), *tmp = dalloc(h, 32 * (size_t)k + 8);
+        double *v = dalloc(h, k), *w = dalloc(h, 2 * (size_t)k), *u = dalloc(h, k), *tmp = dalloc(h, 32 * (size_t)k + 8);
         cudaStream_t s = h->stream;
         const double *C = F.C, *LPi = F.Li, *LRi = F.Li + ksz;
-        if (!(alpha > 0.0)) {
-            double rq = power_max(h, k, [&](double *x, double *y) {
+        if (!(alpha > 0.0))
+            alpha = 1.05 * std::sqrt(lmax_estimate(h, k, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 4.0 * k * (double)k, 16.0 * k * (double)k);
                 gemv(C, k, 0, TRI_NONE, k, x, u, tmp, s);           // u = C x
                 gemv(C, k, 1, TRI_NONE, k, u, y, tmp, s);           // y = C^T u
-            }, v, w, tmp + 32 * (size_t)k, 60);
-            alpha = 1.05 * std::sqrt(rq);
-        }
-        if (!(beta > 0.0)) {
-            double rq = power_max(h, k, [&](double *x, double *y) {
+            }, 0xa1fa0002ull, v, w, tmp + 32 * (size_t)k));
+        if (!(beta > 0.0))
+            beta = 0.9 / std::sqrt(lmax_estimate(h, k, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 4.0 * k * (double)k, 16.0 * k * (double)k);
+                double *z = w + k;                                   // second scratch vector
                 gemv(LRi, k, 1, TRI_UPPER, k, x, u, tmp, s);        // L_R^{-T} x
-                gemv(LPi, k, 0, TRI_LOWER, k, u, y, tmp, s);        // L_P^{-1} .
-                gemv(LPi, k, 1, TRI_UPPER, k, y, u, tmp, s);        // L_P^{-T} .
+                gemv(LPi, k, 0, TRI_LOWER, k, u, z, tmp, s);        // L_P^{-1} .
+                gemv(LPi, k, 1, TRI_UPPER, k, z, u, tmp, s);        // L_P^{-T} .
                 gemv(LRi, k, 0, TRI_LOWER, k, u, y, tmp, s);        // L_R^{-1} .
-            }, v, w, tmp + 32 * (size_t)k, 60);
-            beta = 0.9 / std::sqrt(rq);
-        }
+            }, 0xbe7a0002ull, v, w, tmp + 32 * (size_t)k));
         release(h, mk);
     }
     if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;

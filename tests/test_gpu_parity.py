@@ -203,3 +203,31 @@ def test_split_backerr_estimate_tracks_exact(P, precision):
     _, _, _, _, ex = P.split(Hd, precision=prec, flags=P.FLAG_RESIDUALS)
     assert 0 < ex["split_backerr"] <= 1e-12
     assert ex["split_backerr"] / 3 <= est["split_backerr"] <= 3 * ex["split_backerr"]
+
+
+@pytest.mark.parametrize("case", ["casida_log", "casida_unif", "example1"])
+def test_estimated_bounds_enclose_the_spectrum(P, case):
+    """Reading R5: alpha >= lambda_max(M), beta <= lambda_min(M) (M = sym(Sigma H)), from the
+    extreme Ritz values of 24 Lanczos steps with the safety factors 1.05 and 0.9, and the
+    estimated condition number within 1.2x of the exact one (so the r rule sees the same kappa
+    band); the structure-aware entry point: alpha >= sigma_max(C) = max|lambda(H)|,
+    beta <= min|lambda(H)|."""
+    sigma = None
+    if case == "casida_log":
+        H, _, _ = G.casida(300, ("loguniform", 1e-2, 1e2), seed=71)
+    elif case == "casida_unif":
+        H, _, _ = G.casida(300, ("uniform", 1.0, 10.0), seed=72)
+    else:
+        H, sigma = G.example1(500, 1e6, seed=73)
+    n = H.shape[0]
+    s = O.signature(n, sigma.astype(float) if sigma is not None else None)
+    M = s[:, None] * H
+    ev = np.linalg.eigvalsh(0.5 * (M + M.T))
+    _, info = P.sign(_dev(H), sigma=sigma)
+    assert ev[-1] <= info["alpha"] and info["beta"] <= ev[0]
+    assert (info["alpha"] / info["beta"]) <= 1.2 * (ev[-1] / ev[0])
+    if case != "example1":
+        k = n // 2
+        _, ic = P.casida_sign(_dev(H[:k, :k]), _dev(H[:k, k:]))
+        lam = np.abs(np.linalg.eigvals(H))
+        assert lam.max() <= ic["alpha"] and ic["beta"] <= lam.min()
