@@ -535,6 +535,42 @@ def main():
             "note": "pssd_casida_eig on the blocks A, B of the same H (1 warm-up); checks untimed"}
         del De, Ve
         del Ab, Bb
+        # the paper's Tab. ItRuntime on this GPU: Example 2 (n = 5000, A = Sigma Q D Q^T, Sigma random
+        # +-1, Q = orth(rand(n)), D equally spaced in [1, kappa]), one split per method and kappa,
+        # FP64-emulated; iterations, seconds and the split backward error ||Q+^T Sigma A Q-|| / ||A||
+        ne = 5000
+        ge = torch.Generator(device=dev); ge.manual_seed(0)
+        Qe, _ = torch.linalg.qr(torch.rand(ne, ne, dtype=torch.float64, device=dev, generator=ge))
+        sge = torch.where(torch.rand(ne, dtype=torch.float64, device=dev, generator=ge) < 0.5, 1.0, -1.0)
+        sig_e = sge.to(torch.int8).cpu().numpy()
+        table_m = {}
+        for kap in (1e2, 1e8, 1e12):
+            De = torch.linspace(1.0, kap, ne, dtype=torch.float64, device=dev)
+            Me = (Qe * De[None, :]) @ Qe.T
+            Ae = (sge[:, None] * (0.5 * (Me + Me.T))).contiguous()
+            del Me
+            for mname, mcode in (("zolo_pd", P.METHOD_ZOLO), ("sigma_dwh", P.METHOD_DWH), ("newton", P.METHOD_NEWTON)):
+                try:
+                    P.split(Ae, sigma=sig_e, handle=h, precision=P.PSSD_FP64_EMULATED, method=mcode)
+                    torch.cuda.synchronize()
+                    g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
+                    g0.record(stream)
+                    _, _, _, _, ie = P.split(Ae, sigma=sig_e, handle=h, precision=P.PSSD_FP64_EMULATED, method=mcode)
+                    g1.record(stream)
+                    torch.cuda.synchronize()
+                    _, _, _, _, ir = P.split(Ae, sigma=sig_e, handle=h, precision=P.PSSD_FP64_EMULATED, method=mcode,
+                                             flags=P.FLAG_RESIDUALS)
+                    table_m["%s_kappa%.0e" % (mname, kap)] = {
+                        "iterations": ie["iterations"], "seconds": g0.elapsed_time(g1) / 1e3,
+                        "split_backerr": ir["split_backerr"], "r_per_pass": ie["r_used"][:ie["passes"]]
+                        if mcode == P.METHOD_ZOLO else None}
+                except P.PssdError as err:
+                    table_m["%s_kappa%.0e" % (mname, kap)] = {"status": err.status}
+            del Ae, De
+        line["methods_example2_n5000"] = {"precision": "fp64e", "results": table_m,
+                                          "note": "Sec. 6 Example 2 recipe on the GPU; the paper's Tab. ItRuntime "
+                                                  "ran MATLAB on a laptop CPU (context, not a target)"}
+        del Qe
         # config 5: the step-reversal adjoint of <G, S> + sum of positive eigenvalues at n = 2048
         # (d ~ U[1,10], G symmetric N(0,1)), FP64: one warm-up, one timed backward (its forward included)
         ka = 1024
