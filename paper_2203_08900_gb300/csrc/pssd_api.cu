@@ -583,8 +583,16 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
             zs = rec.Z;
             tape->steps.push_back(rec);
         }
-        return polar ? zolo_step_polar<double>(h, X, Xn, m, r, c, a, chat, fail_index)
-                     : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index, G, step_ell, zs);
+        // The slice engine rounds each product relative to its operands' row and column maxima;
+        // a step with l < 1e-6 forms inverses whose entries span ~1/l^2, and their small parts
+        // (the directions of the eigenvalues near l) fall below the 56 bits kept per row.  Such
+        // steps run their products on the FP64 pipe (the later steps' l is far larger).
+        const int saved_mode = h->dmode;
+        if (saved_mode != GM_F64 && step_ell < 1e-6) h->dmode = GM_F64;
+        const int st = polar ? zolo_step_polar<double>(h, X, Xn, m, r, c, a, chat, fail_index)
+                             : zolo_step<double>(h, X, Xn, m, r, c, a, chat, fail_index, G, step_ell, zs);
+        h->dmode = saved_mode;
+        return st;
     };
     const long long ld = m;
     double *X = X0;
@@ -645,7 +653,10 @@ int dwh_sign(pssd_handle h, double *X0, int m, double ell, double *bufA, double 
         double c[2], a[1], chat, ell1;
         if (zolo_coeffs_host(ell, 1, c, a, &chat, &ell1)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         double *Xn = (X == bufA) ? bufB : bufA;
+        const int saved_mode = h->dmode;   // as in zolo_sign: steps with l < 1e-6 on the FP64 pipe
+        if (saved_mode != GM_F64 && ell < 1e-6) h->dmode = GM_F64;
         int st = zolo_step<double>(h, X, Xn, m, 1, c, a, chat, fail_index, nullptr, ell);
+        h->dmode = saved_mode;
         if (st) { release(h, mk); return st; }
         double d2, y2;
         frob_pair(h, X, ld, Xn, ld, m, m, part, &d2, &y2);

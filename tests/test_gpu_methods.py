@@ -75,3 +75,21 @@ def test_methods_drive_the_split(P, method):
     ev = np.sort(np.linalg.eigvalsh(A11.cpu().numpy()))
     assert np.max(np.abs(ev - lam[:p])) <= 1e-10 * np.max(np.abs(lam))
     assert 0 <= info["split_backerr"] <= 1e-12
+
+
+@pytest.mark.parametrize("kappa", [1e8, 1e12])
+def test_fp64e_extreme_condition(P, kappa):
+    """Example-1 inputs at kappa = 1e8 and 1e12 (Sec. 6.1; Tab. ItRuntime goes to 1e12): the
+    FP64-emulated split meets the FP64 path's backward error.  The first Zolotarev step's
+    shifted inverses span ~1/l^2 in magnitude, below the slice engine's per-row precision,
+    so steps with l < 1e-6 run on the FP64 pipe; without that the kappa = 1e12 split broke down."""
+    import torch
+    A, sig = G.example1(600, kappa, seed=31)
+    Ad = torch.from_numpy(A).cuda()
+    errs = {}
+    for name, pr in (("fp64", P.PSSD_FP64), ("fp64e", P.PSSD_FP64_EMULATED)):
+        for m in (P.METHOD_ZOLO, P.METHOD_DWH):
+            _, _, _, _, info = P.split(Ad, sigma=sig, precision=pr, method=m, flags=P.FLAG_RESIDUALS)
+            errs[(name, m)] = info["split_backerr"]
+    for m in (P.METHOD_ZOLO, P.METHOD_DWH):
+        assert errs[("fp64e", m)] <= max(1e-11, 10 * errs[("fp64", m)]), errs
