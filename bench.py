@@ -438,7 +438,7 @@ def main():
                        "d2h_GBps": db / (fb.elapsed_time(f1) / 1e3) / 1e9,
                        "note": "pinned host buffers; copy rates from events around the copies"}
         del Q2, B11, B22, Hd
-    if rank == 0 and not args.no_compare:
+    if rank == 0 and ws == 1 and not args.no_compare:   # the comparison arms: single-process runs only
         # the other precision modes on the same input, same handle (workspace already grown)
         for name in ("fp64e", "fp64"):
             if name == args.precision:
