@@ -410,8 +410,9 @@ int pssd_test_gemm_f64(pssd_handle h, int engine, int m, int n, int k, int batch
  *   by ascending magnitude), V complex n x n (ld ldv in complex elements) with
  *   V^H Sigma V = diag(sign(D)) (Eq. VSigmaOrth) and the largest-modulus entry of each column
  *   real and positive.  Each eigenvalue of H appears twice in R(H); a pair gives one eigenvector
- *   of H, and a group of 2q values within 1e-12 max|lambda| gives q eigenvectors by
- *   Gram-Schmidt in the definite form x^H Sigma y of the group.
+ *   of H, and a group of 2q values within 1e-12 max|lambda| gives q eigenvectors: q random
+ *   vectors of the group's real eigenspace, orthonormalised in the group's definite form
+ *   s x^H Sigma y by the inverse square root of their (embedded) Gram matrix.
  *   Returns -6 (V), -7 (ldv), -8 (D), -9 (options), or PSSD_ERR_BASIS if the doubled spectrum
  *   cannot be paired.
  */

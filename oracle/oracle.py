@@ -609,7 +609,8 @@ def zjacobi_eigh(A, max_sweeps: int = 60):
     U = np.eye(n, dtype=np.complex128)
     for sweep in range(max_sweeps):
         off = np.sum(np.abs(A - np.diag(np.diag(A))) ** 2)
-        if off <= 1e-30 * np.sum(np.abs(A) ** 2):
+        # the off-diagonal norm cannot fall below rounding, about u sqrt(n) ||A||_F
+        if off <= (4.0 * n * U_FP64) ** 2 * np.sum(np.abs(A) ** 2):
             break
         for p in range(n - 1):
             for q in range(p + 1, n):

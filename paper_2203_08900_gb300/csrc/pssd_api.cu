@@ -32,7 +32,6 @@
 #include <string>
 #include <vector>
 #include <cfloat>
-#include <complex>
 
 #include "pssd.h"
 #include "pssd_internal.h"
@@ -3026,9 +3025,7 @@ extern "C" int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const d
         // Each eigenvalue of H appears twice, adjacent in the library's order (positive ascending,
         // then negative by ascending magnitude).  Groups of values within 1e-12 max|lambda| of
         // their neighbour (extended to an even size) are one eigenspace of H: a pair gives one
-        // eigenvector from either real vector; a larger group of 2q gives q eigenvectors by
-        // Gram-Schmidt in the definite form s x^H Sigma y (s = the group's sign), pivoted on the
-        // largest remaining norm.
+        // eigenvector from either real vector; a larger group of 2q gives q eigenvectors (below).
         double scale = 0.0;
         for (double x : hd) scale = std::max(scale, std::fabs(x));
         const double tol = 1e-12 * scale;
@@ -3061,48 +3058,76 @@ extern "C" int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const d
             complex_extract(VR, m, n, n, dperm, V, ldv, h->stream);
         }
         if (!groups.empty()) {
-            std::vector<double> hs(n);
-            for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+            // q eigenvectors of a group of 2q real ones, on the device: Y = R_g Omega (q random
+            // vectors of the group's real eigenspace; their complex versions are C-independent
+            // with probability 1), Y_e = [Y, J Y] with J [a; b] = [-b; a] (multiplication by i),
+            // G_e = s Y_e^T [Sigma; Sigma] Y_e = R(s Y_c^H Sigma Y_c) (the embedding of the complex
+            // Gram matrix, positive definite in the group's definite form), and
+            // Z_e = Y_e G_e^{-1/2} = R(Y_c G^{-1/2}): the inverse square root of an embedded matrix
+            // is the embedding of the inverse square root, so Z_e's first block column is the
+            // complex basis, with Z^H Sigma Z = s I.
+            std::vector<double> hs2(m);
+            for (int i = 0; i < n; ++i) hs2[i] = hs2[i + n] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+            double *sig2 = dalloc(h, m);
+            h2d(h, sig2, hs2.data(), sizeof(double) * m);
             for (const Group &g : groups) {
-                    const int i = g.first, sz = g.size, q = sz / 2, pos = g.out;
-                    const double sgn = hd[i] > 0 ? 1.0 : -1.0;
-                    // candidates w_t = VR[:n, c] + i VR[n:, c], c = i .. i + sz - 1
-                    std::vector<double> col((size_t)m);
-                    std::vector<std::vector<std::complex<double>>> w(sz, std::vector<std::complex<double>>(n));
-                    for (int t = 0; t < sz; ++t) {
-                        cuda_check(h, cudaMemcpy2DAsync(col.data(), sizeof(double), VR + i + t, sizeof(double) * m,
-                                                        sizeof(double), m, cudaMemcpyDeviceToHost, h->stream),
-                                   "cudaMemcpy2DAsync");
-                        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
-                        for (int r = 0; r < n; ++r) w[t][r] = {col[r], col[r + n]};
-                    }
-                    auto form = [&](const std::vector<std::complex<double>> &x, const std::vector<std::complex<double>> &y) {
-                        std::complex<double> acc = 0.0;
-                        for (int r = 0; r < n; ++r) acc += std::conj(x[r]) * hs[r] * y[r];
-                        return sgn * acc;
-                    };
-                    std::vector<char> used(sz, 0);
-                    std::vector<double> out(2 * (size_t)n);
-                    for (int k = 0; k < q; ++k) {
-                        int best = -1; double bn = -1.0;
-                        for (int t = 0; t < sz; ++t)
-                            if (!used[t]) { const double nn = form(w[t], w[t]).real(); if (nn > bn) { bn = nn; best = t; } }
-                        if (best < 0 || !(bn > 0.0)) return PSSD_ERR_BASIS;
-                        used[best] = 1;
-                        const double f = 1.0 / std::sqrt(bn);
-                        for (auto &x : w[best]) x *= f;
-                        for (int t = 0; t < sz; ++t)
-                            if (!used[t]) {
-                                const std::complex<double> c = form(w[best], w[t]);
-                                for (int r = 0; r < n; ++r) w[t][r] -= c * w[best][r];
-                            }
-                        for (int r = 0; r < n; ++r) { out[2 * r] = w[best][r].real(); out[2 * r + 1] = w[best][r].imag(); }
-                        cuda_check(h, cudaMemcpy2DAsync(V + 2 * (size_t)(pos + k), sizeof(double) * 2 * ldv, out.data(),
-                                                        2 * sizeof(double), 2 * sizeof(double), n,
-                                                        cudaMemcpyHostToDevice, h->stream),
-                                   "cudaMemcpy2DAsync");
-                        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
-                    }
+                const int i = g.first, sz = g.size, q = sz / 2, q2 = sz, pos = g.out;
+                const double sgn = hd[i] > 0 ? 1.0 : -1.0;
+                Mark mg = mark(h);
+                double *Om = dalloc(h, (size_t)sz * q), *Ye = dalloc(h, (size_t)m * q2), *Ze = dalloc(h, (size_t)m * q2);
+                double *Ge = dalloc(h, (size_t)q2 * q2), *Qe = dalloc(h, (size_t)q2 * q2), *Te = dalloc(h, (size_t)q2 * q2);
+                double *Fe = dalloc(h, (size_t)q2 * q2), *le = dalloc(h, q2);
+                {
+                    Timed t(h, K_HBM, 0, 8.0 * sz * q);
+                    fill_gaussian(Om, q, sz, q, 0x2e16ull + (uint64_t)i, h->stream);
+                }
+                GemmArgs ga; ga.m = m; ga.n = q; ga.k = sz; ga.A = VR + i; ga.lda = m; ga.B = Om; ga.ldb = q;
+                ga.C = Ye; ga.ldc = q2;
+                gemm(h, ga);                                                   // Y = R_g Omega
+                {
+                    Timed t(h, K_HBM, 0, 32.0 * n * q);
+                    scale_copy<double, double>(Ye + (size_t)n * q2, q2, Ye + q, q2, n, q, -1.0, h->stream);
+                    scale_copy<double, double>(Ye, q2, Ye + (size_t)n * q2 + q, q2, n, q, 1.0, h->stream);
+                }
+                GemmArgs gg; gg.m = gg.n = q2; gg.k = m; gg.A = Ye; gg.lda = q2; gg.ta = 1; gg.B = Ye; gg.ldb = q2;
+                gg.kscale = sig2; gg.alpha = sgn; gg.C = Ge; gg.ldc = q2;
+                gemm(h, gg);                                                   // G_e
+                {
+                    Timed t(h, K_HBM, 0, 16.0 * q2 * q2);
+                    sym_average<double>(Ge, q2, q2, h->stream);
+                }
+                if (q2 <= 64) {
+                    Timed t(h, K_JACOBI, 0);
+                    jacobi_leaf(Ge, q2, q2, Qe, q2, le, nullptr, h->stream);
+                } else {
+                    int md = 0;
+                    int st2 = sym_eig(h, Ge, q2, Qe, le, 64, 1, &md, 0x2e17ull + (uint64_t)i);
+                    if (st2) return st2;
+                }
+                std::vector<double> hl(q2);
+                d2h_sync(h, hl.data(), le, sizeof(double) * q2);
+                for (double &x : hl) {
+                    if (!(x > 0.0) || !std::isfinite(x)) return PSSD_ERR_BASIS;
+                    x = 1.0 / std::sqrt(x);
+                }
+                h2d(h, le, hl.data(), sizeof(double) * q2);
+                {
+                    Timed t(h, K_HBM, 0, 32.0 * q2 * q2);
+                    copy_matrix(Qe, q2, Te, q2, q2, q2, h->stream);
+                    scale_columns(Te, q2, q2, q2, le, 0, h->stream);           // Q diag(l^{-1/2})
+                }
+                GemmArgs gf; gf.m = gf.n = gf.k = q2; gf.A = Te; gf.lda = q2; gf.B = Qe; gf.ldb = q2; gf.tb = 1;
+                gf.C = Fe; gf.ldc = q2;
+                gemm(h, gf);                                                   // G_e^{-1/2}
+                GemmArgs gz; gz.m = m; gz.n = q2; gz.k = q2; gz.A = Ye; gz.lda = q2; gz.B = Fe; gz.ldb = q2;
+                gz.C = Ze; gz.ldc = q2;
+                gemm(h, gz);                                                   // Z_e = Y_e G_e^{-1/2}
+                {
+                    Timed t(h, K_HBM, 0, 32.0 * n * q);
+                    complex_extract(Ze, q2, n, q, nullptr, V + 2 * (size_t)pos, ldv, h->stream);
+                }
+                cuda_check(h, cudaStreamSynchronize(h->stream), "sync");      // hl goes out of scope
+                release(h, mg);
             }
         }
         {

@@ -74,13 +74,15 @@ def test_zeig_matches_oracle(P, form, k, precision):
         assert np.max(np.abs(V - Vref)) <= 1e-7 * np.max(np.abs(Vref))
 
 
-def test_zeig_repeated_eigenvalues(P):
-    """BSE2 with Q1 = Q2 and d1 d2 taking 5 values, each 6 times: lambda = +-omega with
-    multiplicity 6; each eigenvalue's spectral projector V_g sign(lambda) V_g^H Sigma
-    against the oracle's (unique, unlike the basis)."""
-    k = 30
+@pytest.mark.parametrize("values,mult", [((0.4, 1.0, 2.5, 4.0, 7.0), 6), ((0.8, 3.0), 36)])
+def test_zeig_repeated_eigenvalues(P, values, mult):
+    """BSE2 with Q1 = Q2 and d1 d2 taking a few values, each `mult` times: lambda = +-omega
+    with that multiplicity (groups of 2 mult real values; 72 > 64 takes the recursive
+    symmetric eigensolver for the group's Gram matrix); each eigenvalue's spectral projector
+    V_g sign(lambda) V_g^H Sigma against the oracle's (unique, unlike the basis)."""
+    om = np.repeat(np.array(values), mult)
+    k = len(om)
     rng = np.random.default_rng(9)
-    om = np.repeat(np.array([0.4, 1.0, 2.5, 4.0, 7.0]), 6)
     d1 = np.exp(rng.uniform(np.log(0.5), np.log(2.0), k)) * om
     d2 = om * om / d1
     A, B = G.bse2_blocks(k, d1, d2, rng, same_q=True)
@@ -97,7 +99,7 @@ def test_zeig_repeated_eigenvalues(P):
         for v in np.unique(np.round(lam, 9)):
             g = np.abs(D - v) <= 1e-8 * om.max()
             gr = np.abs(lam - v) <= 1e-8 * om.max()
-            assert g.sum() == gr.sum() == 6
+            assert g.sum() == gr.sum() == mult
             sg = np.sign(v)
             Pg = sg * (V[:, g] @ V[:, g].conj().T) * s[None, :]
             Pr = sg * (Vref[:, gr] @ Vref[:, gr].conj().T) * s[None, :]
