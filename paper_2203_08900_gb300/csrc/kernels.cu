@@ -310,9 +310,67 @@ __device__ __forceinline__ void leaf_diag_block(T *Lb, T *Xb, int ls, int w, T *
     }
 }
 
+// FP32 variant of leaf_diag_block for one warp: lane i holds row i of the block in
+// registers; column j's scaled entries go through a shared-memory buffer (double-buffered by
+// j), and each lane loads the ones it needs before its updates, so the loads pipeline.  (In
+// FP64 one warp is limited to its sub-partition's share of the narrow FP64 pipe; the four-warp
+// version above is faster there.)
+__device__ __forceinline__ void leaf_diag_block_warp(float *Lb, float *Xb, int ls, int w, float *rv, int lane,
+                                                     int *info, int z, int gpiv, int *bad, float *colbuf)
+{
+    float d[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) d[c] = (lane < w && c <= lane) ? Lb[lane * ls + c] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < w) {
+            float pj = __shfl_sync(0xffffffffu, d[j], j);
+            if (!(pj > 0.f) || !isfinite(pj)) {
+                if (lane == 0 && !*bad) { *bad = 1; if (info[z] == 0) info[z] = gpiv + j + 1; }
+                pj = 1.f;
+            }
+            float piv, r;
+            LeafPivot<float>::get(pj, piv, r);
+            const float lij = (lane == j) ? piv : ((lane > j) ? d[j] * r : d[j]);
+            d[j] = lij;
+            float *cb = colbuf + (j & 1) * 32;
+            cb[lane] = lij;
+            if (lane == 0) rv[j] = r;
+            __syncwarp();
+            float lc[32];
+#pragma unroll
+            for (int c = j + 1; c < 32; ++c) lc[c] = cb[c];
+#pragma unroll
+            for (int c = j + 1; c < 32; ++c)
+                if (lane >= c) d[c] -= lij * lc[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        if (lane < w && c <= lane) Lb[lane * ls + c] = d[c];
+    __syncwarp();
+    float x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float v = 0.f;
+        if (k < w) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m < k; ++m) acc += Lb[k * ls + m] * x[m];
+            v = (k == lane) ? rv[k] : ((k > lane) ? -acc * rv[k] : 0.f);
+        }
+        x[k] = v;
+    }
+    if (lane < w) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < w && k >= lane) Xb[k * ls + lane] = x[k];
+    }
+}
+
 // The s x s diagonal block at (off, off) of batch matrix blockIdx.x, in shared memory (row
 // stride s + 1), factorised right-looking by blocks of 32 columns with 8 warps:
-//   1. warps 0-3 factorise the diagonal block and invert it (leaf_diag_block);
+//   1. warps 0-3 (FP64) or warp 0 (FP32) factorise the diagonal block and invert it;
 //   2. panel L_21 = A_21 X_D^T: a warp per row of A_21, lane c holding row c of X_D in
 //      registers, the row of A_21 read as shared-memory broadcasts;
 //   3. trailing update A_22 -= L_21 L_21^T: lane j holding rows j, j + 32, j + 64 of L_21 in
@@ -332,6 +390,7 @@ __global__ void __launch_bounds__(256) chol_leaf_kernel(T *A, long long lda, lon
     T *W = X + (size_t)s * ls;                // s x 33: the panel, then block products of the inverse
     T *rv = W + (size_t)s * 33;               // 1 / L_jj
     __shared__ int bad;
+    __shared__ T colbuf[64];                  // the FP32 diagonal block's column buffer
     const int z = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     A += (long long)z * sA + (long long)off * lda + off;
     Rinv += (long long)z * sR + (long long)off * ldr + off;
@@ -345,7 +404,13 @@ __global__ void __launch_bounds__(256) chol_leaf_kernel(T *A, long long lda, lon
     const int nb = (s + 31) >> 5;
     for (int kb = 0; kb < nb; ++kb) {
         const int o = kb * 32, w = min(32, s - o), o2 = o + w, rows = s - o2;
-        if (warp < 4) leaf_diag_block<T>(L + o * ls + o, X + o * ls + o, ls, w, rv + o, tid, info, z, off + o, &bad);
+        if constexpr (sizeof(T) == 4) {
+            if (warp == 0)
+                leaf_diag_block_warp((float *)(L + o * ls + o), (float *)(X + o * ls + o), ls, w, (float *)(rv + o), lane,
+                                     info, z, off + o, &bad, (float *)colbuf);
+        } else {
+            if (warp < 4) leaf_diag_block<T>(L + o * ls + o, X + o * ls + o, ls, w, rv + o, tid, info, z, off + o, &bad);
+        }
         __syncthreads();
         if (rows > 0) {
             {   // W[i][c] = sum_{m <= c} A[o2 + i][o + m] X_D[c][m]

@@ -319,23 +319,30 @@ __global__ void __launch_bounds__(256) tf32_split_kernel(const float *X, long lo
         }
     }
     __syncthreads();
+    // each thread: one row of the tile and four consecutive k -- one 16-byte chunk of the
+    // swizzled layout -- written as one 16-byte store for the hi parts and one for the lo parts
     const int kblocks = k_pad / 16, tiles = rows_pad / tile_rows;
-    for (int yy = ty; yy < 32; yy += 8) {
-        const int r = r0 + yy, p = p0 + tx;
-        if (r >= rows_pad || p >= k_pad) continue;
-        float v = (r < rows && p < k) ? T[yy][tx] : 0.f;
+    const int yy = threadIdx.x >> 3, q4 = (threadIdx.x & 7) * 4;
+    const int r = r0 + yy, pq = p0 + q4;
+    if (r >= rows_pad || pq >= k_pad) return;      // k_pad is a multiple of 16: the four p all fit
+    float hv[4], lv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int p = pq + t;
+        float v = (r < rows && p < k) ? T[yy][q4 + t] : 0.f;
         if (tri == TRI_LOWER && p > r) v = 0.f;
         if (tri == TRI_UPPER && p < r) v = 0.f;
         if (ks && p < k) v *= ks[p];
         uint32_t u;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-        const float h = __uint_as_float(u);
-        const int rr = r % tile_rows, kk = p & 15;
-        const long long blk = ((long long)z * tiles + r / tile_rows) * kblocks + (p >> 4);
-        float *o = out + blk * (2 * tile_rows * 16) + rr * 16 + ((((kk >> 2) ^ (rr >> 1)) & 3) << 2) + (kk & 3);
-        o[0] = h;
-        o[tile_rows * 16] = v - h;
+        hv[t] = __uint_as_float(u);
+        lv[t] = v - hv[t];
     }
+    const int rr = r % tile_rows, kk = pq & 15;
+    const long long blk = ((long long)z * tiles + r / tile_rows) * kblocks + (pq >> 4);
+    float *o = out + blk * (2 * tile_rows * 16) + rr * 16 + ((((kk >> 2) ^ (rr >> 1)) & 3) << 2);
+    *reinterpret_cast<float4 *>(o) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4 *>(o + tile_rows * 16) = make_float4(lv[0], lv[1], lv[2], lv[3]);
 }
 
 }  // namespace
