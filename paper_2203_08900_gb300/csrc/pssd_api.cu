@@ -68,6 +68,10 @@ struct pssd_handle_s {
     size_t depth = 0;       // bytes of workspace live in the current call (stack discipline)
     size_t peak = 0;        // largest depth reached since creation or pssd_set_workspace
     long long wait_limit = 0;   // pipeline wait bound of the tensor-core kernels in this call (0 = default)
+    cudaStream_t side = nullptr;               // the symmetric recursion's Jacobi leaves (created on first use)
+    std::vector<cudaEvent_t> leaf_pending;     // leaves launched on `side` that the main stream has not joined
+    std::vector<cudaEvent_t> sync_events;      // events without timing for the joins (pooled)
+    size_t sync_used = 0;
 };
 
 namespace {
@@ -168,18 +172,38 @@ cudaEvent_t get_event(pssd_handle h)
 }
 
 // one timed region: algorithmic FLOPs (contractions) or algorithmic HBM bytes
-// (memory-bound passes: the bytes the pass must read and write at least)
+// (memory-bound passes: the bytes the pass must read and write at least), on the handle's
+// stream or on another stream of the handle
 struct Timed {
-    pssd_handle h; int kind; double flops, bytes; cudaEvent_t a = nullptr, b = nullptr;
-    Timed(pssd_handle h_, int kind_, double flops_, double bytes_ = 0.0) : h(h_), kind(kind_), flops(flops_), bytes(bytes_)
+    pssd_handle h; int kind; double flops, bytes; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
+    Timed(pssd_handle h_, int kind_, double flops_, double bytes_ = 0.0, cudaStream_t st_ = nullptr)
+        : h(h_), kind(kind_), flops(flops_), bytes(bytes_), st(st_ ? st_ : h_->stream)
     {
-        if (h->prof) { a = get_event(h); b = get_event(h); cudaEventRecord(a, h->stream); }
+        if (h->prof) { a = get_event(h); b = get_event(h); cudaEventRecord(a, st); }
     }
     ~Timed()
     {
-        if (h->prof) { cudaEventRecord(b, h->stream); h->events.push_back({a, b, kind, flops, bytes}); }
+        if (h->prof) { cudaEventRecord(b, st); h->events.push_back({a, b, kind, flops, bytes}); }
     }
 };
+
+// an event for ordering between the handle's streams (pooled for the handle's lifetime)
+cudaEvent_t sync_event(pssd_handle h)
+{
+    if (h->sync_used == h->sync_events.size()) {
+        cudaEvent_t e;
+        cuda_check(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        h->sync_events.push_back(e);
+    }
+    return h->sync_events[h->sync_used++];
+}
+
+// the handle's main stream waits for every leaf launched on the side stream so far
+void join_leaves(pssd_handle h)
+{
+    for (cudaEvent_t e : h->leaf_pending) cuda_check(h, cudaStreamWaitEvent(h->stream, e, 0), "cudaStreamWaitEvent");
+    h->leaf_pending.clear();
+}
 
 void prof_collect(pssd_handle h)
 {
@@ -1247,13 +1271,24 @@ double lmax_estimate(pssd_handle h, int n, F apply, uint64_t seed, double *v, do
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
 // and Jacobi leaves: W (m x m, ld m) eigenvectors as columns, w eigenvalues
 // (device).  B is preserved.
-int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int leaf, int depth, int *maxdepth,
-            uint64_t seed)
+int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, int leaf, int depth, int *maxdepth,
+                 uint64_t seed)
 {
     if (depth > *maxdepth) *maxdepth = depth;
     if (m <= leaf) {
-        Timed t(h, K_JACOBI, 0);
-        jacobi_leaf(const_cast<double *>(B), m, m, W, m, w, nullptr, h->stream);
+        // a Jacobi leaf is one CTA: it runs on the side stream, after the main stream has
+        // produced B, while the recursion goes on with the sibling; the parent joins it before
+        // forming its eigenvectors (B, W and w belong to the parent until then)
+        if (!h->side) cuda_check(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        cudaEvent_t ready = sync_event(h), done = sync_event(h);
+        cuda_check(h, cudaEventRecord(ready, h->stream), "cudaEventRecord");
+        cuda_check(h, cudaStreamWaitEvent(h->side, ready, 0), "cudaStreamWaitEvent");
+        {
+            Timed t(h, K_JACOBI, 0, 0.0, h->side);
+            jacobi_leaf(const_cast<double *>(B), m, m, W, m, w, nullptr, h->side);
+        }
+        cuda_check(h, cudaEventRecord(done, h->side), "cudaEventRecord");
+        h->leaf_pending.push_back(done);
         return PSSD_OK;
     }
     const long long ld = m, msz = (long long)m * m;
@@ -1410,9 +1445,10 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
         if (st) { release(h, mk); continue; }
         // recurse
         double *Wp = dalloc(h, (size_t)p * p), *Wm = dalloc(h, (size_t)(m - p) * (m - p));
-        st = sym_eig(h, Bp, p, Wp, w, leaf, depth + 1, maxdepth, seed * 3 + 1);
-        if (!st) st = sym_eig(h, Bm, m - p, Wm, w + p, leaf, depth + 1, maxdepth, seed * 3 + 2);
+        st = sym_eig_node(h, Bp, p, Wp, w, leaf, depth + 1, maxdepth, seed * 3 + 1);
+        if (!st) st = sym_eig_node(h, Bm, m - p, Wm, w + p, leaf, depth + 1, maxdepth, seed * 3 + 2);
         if (st) { release(h, outer); return st; }
+        join_leaves(h);
         {   // W = [U_+ W_+, U_- W_-]
             GemmArgs g; g.m = m; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Wp; g.ldb = p; g.C = W; g.ldc = ld;
             gemm(h, g);
@@ -1425,6 +1461,15 @@ int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int lea
     }
     release(h, outer);
     return PSSD_OK;
+}
+
+// Alg. 2 from the outside: the recursion, then the main stream joins its last leaves
+int sym_eig(pssd_handle h, const double *B, int m, double *W, double *w, int leaf, int depth, int *maxdepth,
+            uint64_t seed)
+{
+    const int st = sym_eig_node(h, B, m, W, w, leaf, depth, maxdepth, seed);
+    join_leaves(h);
+    return st;
 }
 
 // One step of iterative refinement of an approximate eigendecomposition A ~ Z diag(d) Z^T
@@ -1734,6 +1779,9 @@ int guarded(pssd_handle h, pssd_info *info, F body)
         st = f.code;
     }
     if (!outer_err) h->derr = nullptr;
+    if (h->side) cudaStreamSynchronize(h->side);   // leaves still running on an error path
+    h->leaf_pending.clear();
+    h->sync_used = 0;
     cudaStreamSynchronize(h->stream);
     prof_collect(h);
     release(h, mk);
@@ -1769,13 +1817,19 @@ int pssd_destroy(pssd_handle h)
 {
     if (!h) return -1;
     cudaStreamSynchronize(h->stream);
+    auto drop_side = [](pssd_handle x) {
+        if (x->side) { cudaStreamSynchronize(x->side); cudaStreamDestroy(x->side); }
+        for (auto &e : x->sync_events) cudaEventDestroy(e);
+    };
     for (auto *w : h->workers) {
         cudaStreamSynchronize(w->stream);
+        drop_side(w);
         for (auto &c : w->chunks) if (c.owned) cudaFree(c.base);
         for (auto &e : w->free_events) cudaEventDestroy(e);
         cudaStreamDestroy(w->stream);
         delete w;
     }
+    drop_side(h);
     for (auto &c : h->chunks) if (c.owned) cudaFree(c.base);
     for (auto &e : h->free_events) cudaEventDestroy(e);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
