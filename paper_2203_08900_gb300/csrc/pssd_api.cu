@@ -584,8 +584,10 @@ struct SignTape {
 // the iteration computes its orthogonal polar factor (the sign of [[0, X0], [X0^T, 0]]).
 int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_restarts, double tau,
               double *bufA, double *bufB, double **Yout, pssd_info *info, int *fail_index, bool polar = false,
-              const double *G0 = nullptr, SignTape *tape = nullptr)
+              const double *G0 = nullptr, SignTape *tape = nullptr, double accept_s2 = 0.0)
 {
+    // accept_s2 > 0 (symmetric case): when the stopping test fails, X_2 is still taken if
+    // ||X_2^2 - I||_F <= accept_s2 (one product), instead of restarting
     // G0: X0^2 (lower) when the caller has formed it (symmetric case, first step only)
     // tape: record every step for the adjoint (symmetric case)
     double step_ell = 1.0;   // lower bound of the step being taken
@@ -650,6 +652,20 @@ int zolo_sign(pssd_handle h, double *X0, int m, double ell, int r_opt, int max_r
         }
         if (!std::isfinite(crit)) { release(h, mk); return PSSD_ERR_NONFINITE; }
         if (crit <= std::pow(U64, 1.0 / (2 * r + 1))) { *Yout = X2; release(h, mk); return PSSD_OK; }
+        if (accept_s2 > 0.0 && !polar) {
+            Mark ms = mark(h);
+            double *Q2 = dalloc(h, (size_t)m * m);
+            GemmArgs g; g.m = g.n = g.k = m; g.A = X2; g.lda = ld; g.B = X2; g.ldb = ld; g.C = Q2; g.ldc = ld;
+            gemm(h, g);                                                   // X_2^2
+            {
+                Timed t(h, K_HBM, 0, 8.0 * m);
+                add_diag<double>(Q2, ld, m, -1.0, h->stream);
+            }
+            double e2, q2;
+            frob_pair(h, nullptr, ld, Q2, ld, m, m, part, &e2, &q2);
+            release(h, ms);
+            if (std::sqrt(q2) <= accept_s2) { *Yout = X2; release(h, mk); return PSSD_OK; }
+        }
         if (pass >= max_restarts) { *Yout = X2; release(h, mk); return PSSD_ERR_NO_CONVERGENCE; }
         // restart (reading R6): A <- X_2, alpha = 1, beta = l_2
         ell = ell2;
@@ -1425,7 +1441,9 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
         double *bA = dalloc(h, msz), *bB = dalloc(h, msz);
         double *Y = nullptr;
         int fi;
-        int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi, false, G0);
+        // Alg. 2's iteration: X_2 is accepted once it meets the involution bound 1e-12 m
+        // (the stopping test of Alg. 8 compares X_2 with the unconverged X_1; reading R6)
+        int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi, false, G0, nullptr, 1e-12 * m);
         if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE || st == PSSD_ERR_NONFINITE) {
             release(h, mk);
             continue;
