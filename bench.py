@@ -247,6 +247,7 @@ def run_batch(args):
     clocks.start()
     h.profile_reset()
     l0 = h.launch_count()
+    ph0 = P.launch_count_phases()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -271,7 +272,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": "batch of %d Casida matrices, k log-uniform [16,1024], d ~ U[0.5,50]"
                        % args.batch_count, "sum_n3": n3, "precision": args.precision},
-            "max_rel_residual": res, "gpu_launches": h.launch_count() - l0, "clocks": ck}
+            "max_rel_residual": res, "gpu_launches": h.launch_count() - l0,
+            "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()}, "clocks": ck}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -599,6 +601,7 @@ def main():
         P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
         torch.cuda.synchronize()
         lb0 = h.launch_count()
+        ph0 = P.launch_count_phases()
         g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         Ds, Vs, _ = P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
@@ -611,6 +614,7 @@ def main():
         line["batch_config4"] = {"s_per_step": tb, "instances_per_s": len(Hs) / tb, "instances": len(Hs),
                                  "precision": "mixed", "max_rel_residual": resb,
                                  "gpu_launches": h.launch_count() - lb0,
+                                 "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()},
                                  "note": "pssd_eig_batched (host work queue over 16 worker streams)"}
         del Hs, Ds, Vs
     if rank == 0 and not args.no_cpu_baseline:

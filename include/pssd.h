@@ -421,6 +421,24 @@ int pssd_zsign(pssd_handle h, int n, const signed char *sigma, const double *H, 
 int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
               double *D, const pssd_opts *opts, pssd_info *info);
 
+/* Test hook: the Krylov loops the library runs for the bounds of Alg. 8 (largest
+ * eigenvalue of M and of L^{-T} L^{-1}), the shift search of Alg. 2 (Lanczos
+ * quadrature nodes) and the screening of a shift (power iteration on R^{-T} R^{-1}).
+ * op: PSSD_KRYLOV_SYM (y = A x, A symmetric, full storage) or PSSD_KRYLOV_TRI_PAIR
+ * (y = A^T (A x) with A lower triangular; entries above the diagonal are not read).
+ * A: device, m x m, row-major, ld lda.  power = 0: `steps` Lanczos steps from the
+ * normalised seeded Gaussian vector, out[j] = alpha_j (j < steps), out[steps + 1 + j]
+ * = beta_j (device, 2 steps + 2 doubles).  power > 0: that many normalised power
+ * steps from the Gaussian vector of seed 0x5eed, then out[0] = v^T op(A) v.
+ * fused = 0: one launch per vector operation; fused = 1: the whole loop in one
+ * thread-block-cluster launch (m <= 1024).  v0 (device, m, or NULL) receives the
+ * starting vector before normalisation.  Returns 0 or a negative argument index
+ * (-6: power outside [0, 1000], or power = 0 with steps outside [1, m]). */
+#define PSSD_KRYLOV_SYM 0
+#define PSSD_KRYLOV_TRI_PAIR 1
+int pssd_test_krylov(pssd_handle h, int op, int m, const double *A, int lda, int steps, int power,
+                     unsigned long long seed, int fused, double *out, double *v0);
+
 /* Test hook: the symmetric divide-and-conquer of Alg. 2 (Zolotarev sign of the
  * shifted subproblem, orthonormal split, recursion to Jacobi leaves of order <=
  * opts->leaf) on a symmetric m x m B (device, ld ldb), in the arithmetic of
@@ -463,6 +481,35 @@ int pssd_profile_read(pssd_handle h, int kind, double *total_ms, long long *laun
 /* Number of kernels the library has launched in this process (all handles;
  * one count per launch).  -1 if h is NULL. */
 long long pssd_launch_count(pssd_handle h);
+/* The same count split by the phase of the solve that launched each kernel
+ * (per host thread: the batched entry point's workers count in the phases of
+ * their own instances).  Phases, in index order:
+ *   PSSD_PHASE_OTHER    everything not listed below
+ *   PSSD_PHASE_FRONT    structure check M = Sigma H, Cholesky of M, K (Sec. 4, Eq. SignCong)
+ *   PSSD_PHASE_BOUNDS   the bounds alpha, beta of the top-level sign (Alg. 8, input)
+ *   PSSD_PHASE_SIGN     the top-level sign iteration (Alg. 8; mixed: FP32 steps + refinement)
+ *   PSSD_PHASE_SPLIT    the top-level split (Alg. 3 / Alg. 6: basis, projected blocks)
+ *   PSSD_PHASE_SHIFT    recursion nodes: shift search and screening (Alg. 2, "find shift")
+ *   PSSD_PHASE_NODE_SIGN  recursion nodes: sign of B - sigma I (Alg. 2 with Alg. 8)
+ *   PSSD_PHASE_NODE_SPLIT recursion nodes: orthogonal split (Alg. 2 with Alg. 4)
+ *   PSSD_PHASE_ASSEMBLE eigenvector products V <- V diag(V1, V2) and the final scaling
+ *   PSSD_PHASE_LEAF     Jacobi leaves of the recursion
+ *   PSSD_PHASE_REFINE   the refinement step of the symmetric eigendecomposition
+ * Writes min(n, PSSD_PHASE_COUNT) counts to `counts` (host array; may be NULL
+ * when n = 0) and returns PSSD_PHASE_COUNT. */
+#define PSSD_PHASE_OTHER 0
+#define PSSD_PHASE_FRONT 1
+#define PSSD_PHASE_BOUNDS 2
+#define PSSD_PHASE_SIGN 3
+#define PSSD_PHASE_SPLIT 4
+#define PSSD_PHASE_SHIFT 5
+#define PSSD_PHASE_NODE_SIGN 6
+#define PSSD_PHASE_NODE_SPLIT 7
+#define PSSD_PHASE_ASSEMBLE 8
+#define PSSD_PHASE_LEAF 9
+#define PSSD_PHASE_REFINE 10
+#define PSSD_PHASE_COUNT 11
+int pssd_launch_count_phases(long long *counts, int n);
 /* Number of device allocations (cudaMalloc calls) the library has made in this
  * process (all handles, workspace growth included). */
 long long pssd_device_alloc_count(void);

@@ -71,7 +71,8 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_sign_noalloc", "pssd_sign_vjp", "pssd_eig_batched", "pssd_test_gemm_f32",
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
            "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
-           "pssd_test_sym_eig", "pssd_sign_vjp_rev", "pssd_zsign", "pssd_zeig"]
+           "pssd_test_sym_eig", "pssd_sign_vjp_rev", "pssd_zsign", "pssd_zeig", "pssd_launch_count_phases",
+           "pssd_test_krylov"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -128,6 +129,9 @@ def lib():
                                     ctypes.POINTER(Info)]
     L.pssd_device_alloc_count.argtypes = []
     L.pssd_device_alloc_count.restype = ctypes.c_longlong
+    L.pssd_launch_count_phases.argtypes = [vp, ctypes.c_int]
+    L.pssd_test_krylov.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_ulonglong, ctypes.c_int, vp, vp]
     L.pssd_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]
     L.pssd_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
     L.pssd_workspace_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -138,6 +142,19 @@ def lib():
 def device_alloc_count() -> int:
     """Device allocations (cudaMalloc calls) the library has made in this process."""
     return int(lib().pssd_device_alloc_count())
+
+
+PHASES = ["other", "front", "bounds", "sign", "split", "shift", "node_sign", "node_split", "assemble", "leaf",
+          "refine"]
+
+
+def launch_count_phases() -> dict:
+    """Kernels launched by the library in this process, by phase of the solve (PSSD_PHASE_*)."""
+    L = lib()
+    n = L.pssd_launch_count_phases(None, 0)
+    buf = (ctypes.c_longlong * n)()
+    L.pssd_launch_count_phases(buf, n)
+    return {PHASES[i] if i < len(PHASES) else str(i): int(buf[i]) for i in range(n)}
 
 
 def zolo_coeffs(ell: float, r: int):
@@ -569,6 +586,22 @@ def test_sym_eig(B, handle=None, **kw):
                                  W.stride(0), ctypes.c_void_p(w.data_ptr()), ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return w, W, info.as_dict()
+
+
+def test_krylov(A, op=0, steps=24, power=0, seed=1, fused=True, handle=None):
+    """Test hook: the library's Krylov loops on a float64 CUDA matrix A (op 0: A x with A
+    symmetric; op 1: A^T (A x) with A lower triangular), step by step or in one cluster
+    launch.  Returns (out, v0): Lanczos alphas/betas (2 steps + 2 entries: alpha_j at j,
+    beta_j at steps + 1 + j) or [v^T op(A) v] after `power` power steps, and the
+    starting vector before normalisation."""
+    m, lda = _check_H(A)
+    h = _handle(handle)
+    out = torch.zeros(2 * steps + 2 if power == 0 else 1, dtype=torch.float64, device=A.device)
+    v0 = torch.empty(m, dtype=torch.float64, device=A.device)
+    st = lib().pssd_test_krylov(h._h, op, m, ctypes.c_void_p(A.data_ptr()), lda, steps, power, seed,
+                                1 if fused else 0, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(v0.data_ptr()))
+    h._check(st)
+    return out, v0
 
 
 def test_gemm_f32(A, B, use_tc=True, ta=0, tb=0, triA=0, triB=0, lowerC=0, alpha=1.0, beta=0.0, Cin=None,

@@ -15,6 +15,8 @@
 
 #include "pssd_internal.h"
 
+#include <cooperative_groups.h>
+
 #include <math.h>
 
 #include <type_traits>
@@ -22,6 +24,8 @@
 namespace pssd {
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_phase_launches[PH_COUNT];
+thread_local int g_phase = PH_OTHER;
 
 bool ensure_dynamic_smem(const void *func, int bytes)
 {
@@ -1132,16 +1136,20 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return x ^ (x >> 31);
 }
 
+// entry `idx` of the seeded Gaussian stream (Box-Muller on two splitmix64 draws)
+__device__ __forceinline__ double gauss_at(uint64_t seed, uint64_t idx)
+{
+    uint64_t h1 = splitmix64(seed ^ (idx * 2 + 1)), h2 = splitmix64(seed + idx * 2 + 0x1234567ull);
+    double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
 __global__ void fill_gaussian_kernel(double *X, long long ldx, int m, int n, uint64_t seed)
 {
     for (int i = blockIdx.y; i < m; i += gridDim.y)
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-            uint64_t idx = (uint64_t)i * (uint64_t)n + (uint64_t)j;
-            uint64_t h1 = splitmix64(seed ^ (idx * 2 + 1)), h2 = splitmix64(seed + idx * 2 + 0x1234567ull);
-            double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-            double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
-            X[(long long)i * ldx + j] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-        }
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+            X[(long long)i * ldx + j] = gauss_at(seed, (uint64_t)i * (uint64_t)n + (uint64_t)j);
 }
 
 void fill_gaussian(double *X, long long ldx, int m, int n, uint64_t seed, cudaStream_t s)
@@ -1325,6 +1333,213 @@ __global__ void dot_kernel(const double *x, const double *y, int n, double *out)
 void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s)
 {
     dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out); count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Krylov loops in one launch.  Step by step, a Lanczos step takes four launches
+// (product, alpha, three-term update, beta with the new vector) and a power
+// step three or four; the recursion's nodes, the bounds of small inputs and
+// the shift screening run such loops hundreds of times on operators whose
+// matrix sits in L2.  Here one cluster of KRY_CLUSTER CTAs runs a whole loop.
+// CTA c owns rows [c R, (c + 1) R) of the operator, R = ceil(m / KRY_CLUSTER);
+// every CTA keeps the whole current and previous vectors in shared memory.  A
+// dot product is summed per CTA (warps, then warps in order), then across the
+// cluster through distributed shared memory in rank order, so every CTA holds
+// the same scalar to the bit.  A new vector is all-gathered by each CTA storing
+// its rows into every CTA's buffer.  Each exchange ends at a cluster barrier, a
+// hardware barrier that every thread of every CTA reaches equally often (all
+// loop bounds are uniform across the cluster): no thread waits on a flag.
+// ---------------------------------------------------------------------------
+constexpr int KRY_CLUSTER = 8, KRY_THREADS = 1024, KRY_WARPS = KRY_THREADS / 32;
+constexpr int KRY_ROWS = KRY_MAX_M / KRY_CLUSTER;      // rows (and columns) owned by a CTA, at most
+constexpr int KRY_GROUPS = KRY_THREADS / KRY_ROWS;     // row groups of the transposed product
+constexpr int KRY_SMEM = (4 * KRY_MAX_M + KRY_ROWS + KRY_GROUPS * KRY_ROWS) * (int)sizeof(double);
+static_assert(KRY_THREADS % KRY_ROWS == 0 && KRY_SMEM <= 48 * 1024, "Krylov kernel layout");
+
+namespace cg = cooperative_groups;
+
+// sum of x over the CTA, returned to every thread
+__device__ double kry_block_sum(double x, double *red, double *bc)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < KRY_WARPS; ++w) s += red[w];
+        *bc = s;
+    }
+    __syncthreads();
+    return *bc;
+}
+
+// sum over the cluster of the CTAs' partial sums `part`, returned to every thread of
+// every CTA.  Two slots alternate: a slot is rewritten only after another cluster
+// barrier, by which time every CTA has read it.
+__device__ double kry_cluster_sum(cg::cluster_group &cl, double part, double *slot, int &turn, double *bc)
+{
+    double *my = slot + turn;
+    turn ^= 1;
+    if (threadIdx.x == 0) *my = part;
+    cl.sync();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int c = 0; c < KRY_CLUSTER; ++c) s += *cl.map_shared_rank(my, c);
+        *bc = s;
+    }
+    __syncthreads();
+    return *bc;
+}
+
+// rows r0 .. r0 + nr - 1 of A x (tri: of L x, L lower triangular) -> wl; one warp per row
+__device__ void kry_rows(const double *__restrict__ A, long long lda, bool tri, const double *x, double *wl,
+                         int r0, int nr, int m)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < nr; i += KRY_WARPS) {
+        const double *row = A + (long long)(r0 + i) * lda;
+        const int len = tri ? r0 + i + 1 : m;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int k = lane;
+        for (; k + 224 < len; k += 256) {   // eight independent loads in flight per lane
+            double r[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) r[q] = __ldg(row + k + 32 * q);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = fma(r[q], x[k + 32 * q], a[q]);
+        }
+        if (k + 96 < len) {
+            double r[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r[q] = __ldg(row + k + 32 * q);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = fma(r[q], x[k + 32 * q], a[q]);
+            k += 128;
+        }
+        for (; k < len; k += 32) a[0] = fma(__ldg(row + k), x[k], a[0]);
+        double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) wl[i] = s;
+    }
+    __syncthreads();
+}
+
+// entries r0 .. r0 + nr - 1 of L^T u (L lower triangular) -> wl: thread (g, c) sums
+// L[p][r0 + c] u[p] over p = r0 + g, r0 + g + KRY_GROUPS, ... (a warp reads 32
+// consecutive entries of a row), then the groups' sums are added in order
+__device__ void kry_tri_t_cols(const double *__restrict__ A, long long lda, const double *u, double *wl,
+                               double *colp, int r0, int nr, int m)
+{
+    const int c = threadIdx.x % KRY_ROWS, g = threadIdx.x / KRY_ROWS;
+    double acc = 0.0;
+    if (c < nr) {
+        const int col = r0 + c;
+        for (int p = max(r0 + g, col - (col - r0 - g) % KRY_GROUPS); p < m; p += KRY_GROUPS)
+            if (p >= col) acc = fma(__ldg(A + (long long)p * lda + col), u[p], acc);
+    }
+    colp[g * KRY_ROWS + c] = acc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += KRY_THREADS) {
+        double s = 0.0;
+        for (int q = 0; q < KRY_GROUPS; ++q) s += colp[q * KRY_ROWS + i];
+        wl[i] = s;
+    }
+    __syncthreads();
+}
+
+// scale * src[0 .. nr) -> dst[r0 .. r0 + nr) in every CTA of the cluster, then a cluster barrier
+__device__ void kry_gather(cg::cluster_group &cl, const double *src, double scale, double *dst, int r0, int nr)
+{
+    for (int c = 0; c < KRY_CLUSTER; ++c) {
+        double *rd = cl.map_shared_rank(dst, c);
+        for (int i = threadIdx.x; i < nr; i += KRY_THREADS) rd[r0 + i] = src[i] * scale;
+    }
+    cl.sync();
+}
+
+template <int OP>
+__global__ void __cluster_dims__(KRY_CLUSTER, 1, 1) __launch_bounds__(KRY_THREADS, 1)
+krylov_cluster_kernel(const double *__restrict__ A, long long lda, int m, int steps, int power, uint64_t seed,
+                      double *out)
+{
+    extern __shared__ __align__(16) double kry_sm[];
+    __shared__ double red[KRY_WARPS], slot[2], bc;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int R = (m + KRY_CLUSTER - 1) / KRY_CLUSTER;
+    const int r0 = min(m, rank * R), nr = min(m, r0 + R) - r0;
+    double *cur = kry_sm, *prv = cur + KRY_MAX_M, *nxt = prv + KRY_MAX_M, *ub = nxt + KRY_MAX_M;
+    double *wl = ub + KRY_MAX_M, *colp = wl + KRY_ROWS;
+    int turn = 0;
+    // the starting vector, whole in every CTA (same entries, same summation order)
+    double sq = 0.0;
+    for (int i = threadIdx.x; i < m; i += KRY_THREADS) {
+        const double g = gauss_at(seed, (uint64_t)i);
+        cur[i] = g;
+        prv[i] = 0.0;
+        sq += g * g;
+    }
+    sq = kry_block_sum(sq, red, &bc);
+    const double inv0 = sq > 0.0 ? 1.0 / sqrt(sq) : 0.0;
+    for (int i = threadIdx.x; i < m; i += KRY_THREADS) cur[i] *= inv0;
+    cl.sync();   // every CTA has started (its shared memory exists) before the first remote access
+    auto apply = [&](const double *x) {   // the CTA's rows of op(A) x -> wl
+        if (OP == KRY_SYM) {
+            kry_rows(A, lda, false, x, wl, r0, nr, m);
+        } else {
+            kry_rows(A, lda, true, x, wl, r0, nr, m);         // u = L x, own rows
+            kry_gather(cl, wl, 1.0, ub, r0, nr);               // u whole in every CTA
+            kry_tri_t_cols(A, lda, ub, wl, colp, r0, nr, m);   // L^T u, own entries
+        }
+    };
+    if (power == 0) {
+        double beta_prev = 0.0;
+        for (int j = 0; j < steps; ++j) {
+            apply(cur);
+            double pa = 0.0;
+            for (int i = threadIdx.x; i < nr; i += KRY_THREADS) pa += cur[r0 + i] * wl[i];
+            const double alpha = kry_cluster_sum(cl, kry_block_sum(pa, red, &bc), slot, turn, &bc);
+            double pb = 0.0;
+            for (int i = threadIdx.x; i < nr; i += KRY_THREADS) {
+                const double w = wl[i] - alpha * cur[r0 + i] - beta_prev * prv[r0 + i];
+                wl[i] = w;
+                pb += w * w;
+            }
+            const double beta = sqrt(kry_cluster_sum(cl, kry_block_sum(pb, red, &bc), slot, turn, &bc));
+            if (rank == 0 && threadIdx.x == 0) { out[j] = alpha; out[steps + 1 + j] = beta; }
+            kry_gather(cl, wl, beta > 0.0 ? 1.0 / beta : 0.0, nxt, r0, nr);
+            double *t = prv; prv = cur; cur = nxt; nxt = t;
+            beta_prev = beta;
+        }
+    } else {
+        for (int it = 0; it < power; ++it) {
+            apply(cur);
+            double pb = 0.0;
+            for (int i = threadIdx.x; i < nr; i += KRY_THREADS) pb += wl[i] * wl[i];
+            const double nrm = sqrt(kry_cluster_sum(cl, kry_block_sum(pb, red, &bc), slot, turn, &bc));
+            kry_gather(cl, wl, nrm > 0.0 ? 1.0 / nrm : 0.0, nxt, r0, nr);
+            double *t = cur; cur = nxt; nxt = t;
+        }
+        apply(cur);
+        double pa = 0.0;
+        for (int i = threadIdx.x; i < nr; i += KRY_THREADS) pa += cur[r0 + i] * wl[i];
+        const double rq = kry_cluster_sum(cl, kry_block_sum(pa, red, &bc), slot, turn, &bc);
+        if (rank == 0 && threadIdx.x == 0) out[0] = rq;
+    }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+bool krylov_cluster(const double *A, long long lda, int op, int m, int steps, int power, uint64_t seed, double *out,
+                    cudaStream_t s)
+{
+    if (m < 1 || m > KRY_MAX_M || steps < 0 || power < 0) return false;
+    if (op == KRY_SYM)
+        krylov_cluster_kernel<KRY_SYM><<<KRY_CLUSTER, KRY_THREADS, KRY_SMEM, s>>>(A, lda, m, steps, power, seed, out);
+    else
+        krylov_cluster_kernel<KRY_TRI_PAIR><<<KRY_CLUSTER, KRY_THREADS, KRY_SMEM, s>>>(A, lda, m, steps, power, seed,
+                                                                                      out);
+    count_launch();
+    return true;
 }
 
 __global__ void scale_columns_kernel(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs)

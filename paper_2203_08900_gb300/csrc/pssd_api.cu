@@ -912,25 +912,47 @@ int ns_refine(pssd_handle h, double *Y, int m, double tol, int max_it, double *r
     return PSSD_OK;
 }
 
-// power iteration estimate of lambda_max of an SPD operator given by `apply`
+// The operator of a Krylov loop in the form the one-launch cluster kernel takes
+// (krylov_cluster: y = A x, or y = L^T (L x) for lower triangular L); A = null: none,
+// the loop then runs step by step through its `apply` callback.
+struct KryFused {
+    const double *A = nullptr;
+    long long lda = 0;
+    int op = KRY_SYM;
+    bool usable(int m) const { return A && m >= 1 && m <= KRY_MAX_M; }
+};
+
+// power iteration estimate of lambda_max of an SPD operator given by `apply` (or by `kf`:
+// the same iteration in one launch, the same starting vector)
 template <class F>
-double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *dscal, int iters)
+void power_device(pssd_handle h, int n, F apply, double *v, double *w, double *dscal, int iters,
+                  const KryFused *kf = nullptr)
 {
-    {
-        Timed t(h, K_HBM, 0, 24.0 * n);
-        fill_gaussian(v, n, 1, n, 0x5eedull, h->stream);
-        normalize_vec(v, v, n, nullptr, h->stream);
-    }
-    for (int it = 0; it < iters; ++it) {
+    if (kf && kf->usable(n) && iters > 0) {
+        Timed t(h, K_GEMV, (iters + 1) * 2.0 * n * (double)n, (iters + 1) * 8.0 * n * (double)n);
+        krylov_cluster(kf->A, kf->lda, kf->op, n, 0, iters, 0x5eedull, dscal, h->stream);
+    } else {
+        {
+            Timed t(h, K_HBM, 0, 24.0 * n);
+            fill_gaussian(v, n, 1, n, 0x5eedull, h->stream);
+            normalize_vec(v, v, n, nullptr, h->stream);
+        }
+        for (int it = 0; it < iters; ++it) {
+            apply(v, w);
+            Timed t(h, K_GEMV, 0, 16.0 * n);
+            normalize_vec(w, v, n, nullptr, h->stream);
+        }
         apply(v, w);
-        Timed t(h, K_GEMV, 0, 16.0 * n);
-        normalize_vec(w, v, n, nullptr, h->stream);
-    }
-    apply(v, w);
-    {
         Timed t(h, K_GEMV, 0, 16.0 * n);
         dot_vec(v, w, n, dscal, h->stream);
     }
+}
+
+template <class F>
+double power_max(pssd_handle h, int n, F apply, double *v, double *w, double *dscal, int iters,
+                 const KryFused *kf = nullptr)
+{
+    power_device(h, n, apply, v, w, dscal, iters, kf);
     double rq;
     d2h_sync(h, &rq, dscal, sizeof(double));
     return rq;
@@ -1213,15 +1235,18 @@ void small_sym_eig(std::vector<double> A, int n, std::vector<double> &w, std::ve
 // after the last step: [theta_1 - beta_s, theta_s + beta_s] encloses the spectrum of B in
 // practice (the extreme Ritz values converge first, from inside).  Returns false if the
 // recurrence produced a non-finite value.
+// `steps` Lanczos steps from the seeded Gaussian vector: ab[j] = alpha_j, ab[steps + 1 + j] =
+// beta_j (device), step by step through `apply`, or in one launch through `kf` when m fits it
 template <class F>
-bool lanczos_run(pssd_handle h, int m, F apply, uint64_t seed, std::vector<double> &th, std::vector<double> &tau,
-                 double *resid, double *rtop = nullptr)
+void lanczos_device(pssd_handle h, int m, F apply, uint64_t seed, int steps, double *ab, const KryFused *kf)
 {
-    // apply(v, w): w = A v for the symmetric operator A (m-vectors on the device).
-    // rtop (optional): beta_s |z_s| of the largest Ritz value, the norm of its Ritz residual
-    const int steps = std::min(m, 24);
+    if (kf && kf->usable(m)) {
+        Timed t(h, K_GEMV, steps * 2.0 * m * (double)m, steps * 8.0 * m * (double)m);
+        krylov_cluster(kf->A, kf->lda, kf->op, m, steps, 0, seed, ab, h->stream);
+        return;
+    }
     Mark mk = mark(h);
-    double *V = dalloc(h, 3 * (size_t)m), *ab = dalloc(h, 2 * (size_t)steps + 2);
+    double *V = dalloc(h, 3 * (size_t)m);
     double *vp = V, *vc = V + m, *w = V + 2 * m;
     double *al = ab, *be = ab + steps + 1;
     {
@@ -1230,13 +1255,27 @@ bool lanczos_run(pssd_handle h, int m, F apply, uint64_t seed, std::vector<doubl
         normalize_vec(vc, vc, m, nullptr, h->stream);
     }
     for (int j = 0; j < steps; ++j) {
-        apply(vc, w);                                                             // w = A v_j
+        apply(vc, w);                                                         // w = A v_j
         Timed t(h, K_GEMV, 0, 40.0 * m);
-        dot_vec(vc, w, m, al + j, h->stream);                                     // alpha_j
+        dot_vec(vc, w, m, al + j, h->stream);                                 // alpha_j
         lanczos_update(w, vc, j ? vp : nullptr, al + j, j ? be + j - 1 : nullptr, m, h->stream);
-        normalize_vec(w, vp, m, be + j, h->stream);                               // beta_j, v_{j+1}
+        normalize_vec(w, vp, m, be + j, h->stream);                           // beta_j, v_{j+1}
         std::swap(vp, vc);
     }
+    release(h, mk);
+}
+
+template <class F>
+bool lanczos_run(pssd_handle h, int m, F apply, uint64_t seed, std::vector<double> &th, std::vector<double> &tau,
+                 double *resid, double *rtop = nullptr, const KryFused *kf = nullptr)
+{
+    // apply(v, w): w = A v for the symmetric operator A (m-vectors on the device); kf: the
+    // same operator for the one-launch loop (used when m fits it).
+    // rtop (optional): beta_s |z_s| of the largest Ritz value, the norm of its Ritz residual
+    const int steps = std::min(m, 24);
+    Mark mk = mark(h);
+    double *ab = dalloc(h, 2 * (size_t)steps + 2);
+    lanczos_device(h, m, apply, seed, steps, ab, kf);
     std::vector<double> hab(2 * (size_t)steps + 2);
     d2h_sync(h, hab.data(), ab, hab.size() * sizeof(double));
     release(h, mk);
@@ -1263,10 +1302,11 @@ bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::ve
 {
     Mark mk = mark(h);
     double *tmp = dalloc(h, 32 * (size_t)m + 8);
+    KryFused kf; kf.A = B; kf.lda = m; kf.op = KRY_SYM;
     const bool ok = lanczos_run(h, m, [&](const double *x, double *y) {
         Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
         gemv(B, m, 0, TRI_NONE, m, x, y, tmp, h->stream);
-    }, seed, th, tau, resid);
+    }, seed, th, tau, resid, nullptr, &kf);
     release(h, mk);
     return ok;
 }
@@ -1276,12 +1316,13 @@ bool lanczos_nodes(pssd_handle h, const double *B, int m, uint64_t seed, std::ve
 // first and faster than the power method's Rayleigh quotient), or 60 power steps if the
 // recurrence fails.  Callers add their safety factors (reading R5).
 template <class F>
-double lmax_estimate(pssd_handle h, int n, F apply, uint64_t seed, double *v, double *w, double *dscal)
+double lmax_estimate(pssd_handle h, int n, F apply, uint64_t seed, double *v, double *w, double *dscal,
+                     const KryFused *kf = nullptr)
 {
     std::vector<double> th, tau;
     double res;
-    if (lanczos_run(h, n, apply, seed, th, tau, &res) && th.back() > 0.0) return th.back();
-    return power_max(h, n, apply, v, w, dscal, 60);
+    if (lanczos_run(h, n, apply, seed, th, tau, &res, nullptr, kf) && th.back() > 0.0) return th.back();
+    return power_max(h, n, apply, v, w, dscal, 60, kf);
 }
 
 // symmetric eigendecomposition of B (m x m) by Alg. 2 with Zolotarev signs
@@ -1291,6 +1332,7 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
                  uint64_t seed)
 {
     if (depth > *maxdepth) *maxdepth = depth;
+    PhaseScope phase(m <= leaf ? PH_LEAF : PH_SHIFT);
     if (m <= leaf) {
         // a Jacobi leaf is one CTA: it runs on the side stream, after the main stream has
         // produced B, while the recursion goes on with the sibling; the parent joins it before
@@ -1396,11 +1438,12 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
         int fi;
         double xm = 0.0;
         if (!chol_inv<double>(h, Rc, m, ld, 0, 1, Ri, 0, &fi)) {
+            KryFused kf; kf.A = Ri; kf.lda = ld; kf.op = KRY_TRI_PAIR;
             const double rq = power_max(h, m, [&](double *x, double *y) {
                 Timed t(h, K_GEMV, 2.0 * m * (double)m, 8.0 * m * (double)m);
                 gemv(Ri, ld, 0, TRI_LOWER, m, x, u, tmp, h->stream);      // R^{-1} x
                 gemv(Ri, ld, 1, TRI_UPPER, m, u, y, tmp, h->stream);      // R^{-T} .
-            }, v, vw, tmp + 32 * (size_t)m, 20);
+            }, v, vw, tmp + 32 * (size_t)m, 20, &kf);
             if (rq > 0.0 && std::isfinite(rq)) xm = 1.0 / std::sqrt(rq);
         }
         release(h, ms);
@@ -1433,6 +1476,7 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
             X0 = Xb; G0 = Gb; ell = std::max(1e-10, 0.3 * best_x);
         } else {
             if (ci >= cands.size()) { release(h, outer); return PSSD_ERR_BASIS; }
+            g_phase = PH_SHIFT;
             double alpha;
             if (!prepare(cands[ci++], Xa, Ga, alpha)) return identity();
             X0 = Xa; G0 = Ga; ell = 1e-10;   // conservative lower bound on |lambda(X0)|
@@ -1443,12 +1487,14 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
         int fi;
         // Alg. 2's iteration: X_2 is accepted once it meets the involution bound 1e-12 m
         // (the stopping test of Alg. 8 compares X_2 with the unconverged X_1; reading R6)
+        g_phase = PH_NODE_SIGN;
         int st = zolo_sign(h, X0, m, ell, 0, 2, 1e-15, bA, bB, &Y, nullptr, &fi, false, G0, nullptr, 1e-12 * m);
         if (st == PSSD_ERR_NOT_DEFINITE || st == PSSD_ERR_NO_CONVERGENCE || st == PSSD_ERR_NONFINITE) {
             release(h, mk);
             continue;
         }
         if (st) { release(h, outer); return st; }
+        g_phase = PH_NODE_SPLIT;
         {
             Timed t(h, K_HBM, 0, 8.0 * m);
             trace_partial(Y, ld, m, tmp, h->stream);
@@ -1466,6 +1512,7 @@ int sym_eig_node(pssd_handle h, const double *B, int m, double *W, double *w, in
         st = sym_eig_node(h, Bp, p, Wp, w, leaf, depth + 1, maxdepth, seed * 3 + 1);
         if (!st) st = sym_eig_node(h, Bm, m - p, Wm, w + p, leaf, depth + 1, maxdepth, seed * 3 + 2);
         if (st) { release(h, outer); return st; }
+        g_phase = PH_ASSEMBLE;
         join_leaves(h);
         {   // W = [U_+ W_+, U_- W_-]
             GemmArgs g; g.m = m; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Wp; g.ldb = p; g.C = W; g.ldc = ld;
@@ -1585,6 +1632,7 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
 {
     // tape: record the Zolotarev steps for the adjoint (FP64 / FP64e Zolotarev only); tape_store:
     // keep the shifted inverses of every step, else only the per-step iterates
+    PhaseScope phase(PH_FRONT);
     F.n = n;
     h->wait_limit = o.wait_cycles;
     if (info) info->method = o.method;
@@ -1653,21 +1701,25 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
     // a3: bounds (reading R5: |lambda(H)| in [lambda_min(M), lambda_max(M)])
     double alpha = o.alpha, beta = o.beta;
     if (!(alpha > 0.0) || !(beta > 0.0)) {
+        PhaseScope phase_b(PH_BOUNDS);
         Mark mk = mark(h);
         double *v = dalloc(h, n), *w = dalloc(h, n), *u = dalloc(h, n), *tmp = dalloc(h, 32 * (size_t)n + 8);
         double *M = F.M, *Li = F.Linv;
         cudaStream_t s = h->stream;
+        KryFused kM, kL;
+        kM.A = M; kM.lda = ld; kM.op = KRY_SYM;
+        kL.A = Li; kL.lda = ld; kL.op = KRY_TRI_PAIR;
         if (!(alpha > 0.0))
             alpha = 1.05 * lmax_estimate(h, n, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);
                 gemv(M, ld, 0, TRI_NONE, n, x, y, tmp, s);
-            }, 0xa1fa0001ull, v, w, tmp + 32 * (size_t)n);
+            }, 0xa1fa0001ull, v, w, tmp + 32 * (size_t)n, &kM);
         if (!(beta > 0.0))
             beta = 0.9 / lmax_estimate(h, n, [&](const double *x, double *y) {
                 Timed t(h, K_GEMV, 2.0 * n * (double)n, 8.0 * n * (double)n);  // two triangular halves
                 gemv(Li, ld, 0, TRI_LOWER, n, x, u, tmp, s);     // u = L^{-1} x
                 gemv(Li, ld, 1, TRI_UPPER, n, u, y, tmp, s);     // y = L^{-T} u
-            }, 0xbe7a0001ull, v, w, tmp + 32 * (size_t)n);
+            }, 0xbe7a0001ull, v, w, tmp + 32 * (size_t)n, &kL);
         release(h, mk);
     }
     if (!(alpha > 0.0) || !(beta > 0.0) || !std::isfinite(alpha) || !std::isfinite(beta)) return PSSD_ERR_NONFINITE;
@@ -1681,6 +1733,7 @@ int front(pssd_handle h, int n, const signed char *sigma, const double *H, int l
         gemm(h, g);
         mirror(h, F.K, ld, 0, n, 1);
     }
+    g_phase = PH_SIGN;   // restored by `phase` on return
     if (o.precision == PSSD_MIXED) {
         // FP32 Zolotarev steps, then FP64-accurate Newton-Schulz refinement
         F.Y = dalloc(h, nsz);
@@ -1994,6 +2047,7 @@ int pssd_split(pssd_handle h, int n, const signed char *sigma, const double *H, 
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
         const bool exact_be = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
         double *E = exact_be ? dalloc(h, (size_t)p * q + 1) : nullptr;
+        PhaseScope phase(PH_SPLIT);
         st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull);
         if (st) return st;
         // C_+ = chol(B_+), C_- = chol(-B_-)
@@ -2062,8 +2116,10 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
         double *Bp = dalloc(h, (size_t)p * p + 1), *Bm = dalloc(h, (size_t)q * q + 1);
         const bool exact_be = (o.flags & PSSD_FLAG_RESIDUALS) != 0;
         double *E = exact_be ? dalloc(h, (size_t)p * q + 1) : nullptr;
+        PhaseScope phase(PH_SPLIT);
         st = sym_split(h, F.K, F.Y, n, p, U, Bp, Bm, E, 0x51a7ull, true);
         if (st) return st;
+        g_phase = PH_OTHER;
         double *Wp = dalloc(h, (size_t)p * p + 1), *Wm = dalloc(h, (size_t)q * q + 1);
         double *w = dalloc(h, n);
         int maxdepth = 0;
@@ -2071,6 +2127,7 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
         if (!st && q > 0) st = sym_eig(h, Bm, q, Wm, w + p, leaf, 1, &maxdepth, 0x2002ull);
         if (st) return st;
         if (info) info->levels = maxdepth;
+        g_phase = PH_ASSEMBLE;
         double *Uf = dalloc(h, nsz);
         if (p > 0) {
             GemmArgs g; g.m = n; g.n = p; g.k = p; g.A = U; g.lda = ld; g.B = Wp; g.ldb = p; g.C = Uf; g.ldc = ld;
@@ -2082,8 +2139,10 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
             gemm(h, g);
         }
         if (!(o.flags & PSSD_FLAG_NO_REFINE)) {   // K ~ Uf diag(w) Uf^T, refined once
+            g_phase = PH_REFINE;
             st = sym_refine(h, F.K, ld, n, Uf, ld, w);
             if (st) return st;
+            g_phase = PH_ASSEMBLE;
         }
         double *Vt = dalloc(h, nsz);
         {   // V = L^{-T} Uf |Lambda|^{1/2}
@@ -2115,6 +2174,7 @@ int eig_core(pssd_handle h, int n, const signed char *sigma, const double *H, in
             gather_columns(Vt, ld, V, ldv, n, n, dperm, h->stream);
         }
         cuda_check(h, cudaStreamSynchronize(h->stream), "sync");   // host vectors above go out of scope
+        g_phase = PH_OTHER;
         if (info && p > 0 && q > 0)     // ||U_+^T K U_-||_F / ||K||_F
             info->split_backerr = split_backward_error(h, F.K, U, n, p, E);
         if (info)
@@ -2217,6 +2277,15 @@ long long pssd_launch_count(pssd_handle h) { return h ? g_launches.load() : -1; 
 
 // process-wide number of device allocations (cudaMalloc calls) the library has made
 long long pssd_device_alloc_count(void) { return g_device_allocs.load(); }
+
+// the launch count by phase (PSSD_PHASE_* = PH_*)
+int pssd_launch_count_phases(long long *counts, int n)
+{
+    static_assert(PSSD_PHASE_COUNT == PH_COUNT && PSSD_PHASE_SHIFT == PH_SHIFT && PSSD_PHASE_REFINE == PH_REFINE,
+                  "phase indices");
+    for (int i = 0; i < n && i < PH_COUNT && counts; ++i) counts[i] = g_phase_launches[i].load();
+    return PH_COUNT;
+}
 
 }  // extern "C"
 
@@ -3242,6 +3311,41 @@ extern "C" int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb,
         if (info) info->levels = maxdepth;
         Timed t(h, K_HBM, 0, 16.0 * msz);
         copy_matrix(Wc, m, W, ldw, m, m, h->stream);
+        return PSSD_OK;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// test hook: the Krylov loops behind the bounds, the shift search and the shift
+// screening, step by step or in one cluster launch, on the operators they use
+// ---------------------------------------------------------------------------
+extern "C" int pssd_test_krylov(pssd_handle h, int op, int m, const double *A, int lda, int steps, int power,
+                                unsigned long long seed, int fused, double *out, double *v0)
+{
+    if (!h) return -1;
+    if (op != PSSD_KRYLOV_SYM && op != PSSD_KRYLOV_TRI_PAIR) return -2;
+    if (m < 1 || m > PSSD_MAX_N || (fused && m > KRY_MAX_M)) return -3;
+    if (!A) return -4;
+    if (lda < m) return -5;
+    if (power < 0 || power > 1000 || (power == 0 && (steps < 1 || steps > m))) return -6;
+    if (!out) return -7;
+    return guarded(h, nullptr, [&]() -> int {
+        Mark mk = mark(h);
+        double *v = dalloc(h, m), *w = dalloc(h, m), *u = dalloc(h, m), *tmp = dalloc(h, 32 * (size_t)m + 8);
+        KryFused kf; kf.A = A; kf.lda = lda; kf.op = op == PSSD_KRYLOV_SYM ? KRY_SYM : KRY_TRI_PAIR;
+        auto apply = [&](const double *x, double *y) {
+            if (kf.op == KRY_SYM) {
+                gemv(A, lda, 0, TRI_NONE, m, x, y, tmp, h->stream);
+            } else {
+                gemv(A, lda, 0, TRI_LOWER, m, x, u, tmp, h->stream);
+                gemv(A, lda, 1, TRI_UPPER, m, u, y, tmp, h->stream);
+            }
+        };
+        if (power > 0) power_device(h, m, apply, v, w, out, power, fused ? &kf : nullptr);
+        else lanczos_device(h, m, apply, seed, steps, out, fused ? &kf : nullptr);
+        if (v0) fill_gaussian(v0, m, 1, m, power > 0 ? 0x5eedull : seed, h->stream);
+        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+        release(h, mk);
         return PSSD_OK;
     });
 }

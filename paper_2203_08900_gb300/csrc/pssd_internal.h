@@ -8,10 +8,33 @@
 
 namespace pssd {
 
+// Phases of a solve, for the launch counters below (the public indices are
+// PSSD_PHASE_* in pssd.h, in the same order)
+enum Phase {
+    PH_OTHER = 0, PH_FRONT, PH_BOUNDS, PH_SIGN, PH_SPLIT, PH_SHIFT, PH_NODE_SIGN, PH_NODE_SPLIT, PH_ASSEMBLE,
+    PH_LEAF, PH_REFINE, PH_COUNT
+};
+
 // process-wide count of kernels launched by the library (one increment per
-// launch statement, after the launch)
+// launch statement, after the launch), in total and by the phase the
+// launching thread is in
 extern std::atomic<long long> g_launches;
-inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern std::atomic<long long> g_phase_launches[PH_COUNT];
+extern thread_local int g_phase;
+inline void count_launch()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_phase_launches[g_phase].fetch_add(1, std::memory_order_relaxed);
+}
+
+// sets the calling thread's phase for its lifetime, then restores the previous one
+struct PhaseScope {
+    int saved;
+    explicit PhaseScope(int p) : saved(g_phase) { g_phase = p; }
+    ~PhaseScope() { g_phase = saved; }
+    PhaseScope(const PhaseScope &) = delete;
+    PhaseScope &operator=(const PhaseScope &) = delete;
+};
 
 // Allow `func` (a __global__ function) `bytes` of dynamic shared memory on the
 // current device: set once per (device, function), thread-safe.  False if the
@@ -133,6 +156,19 @@ void normalize_vec(double *y, double *x, int n, double *norm_out, cudaStream_t s
 void dot_vec(const double *x, const double *y, int n, double *out, cudaStream_t s);
 // w <- w - alpha[0] v - beta[0] vprev (device scalars; vprev and beta may be null)
 void lanczos_update(double *w, const double *v, const double *vprev, const double *alpha, const double *beta, int n,
+                    cudaStream_t s);
+
+// Krylov loops in one launch for operators of order m <= KRY_MAX_M (one thread-block
+// cluster; see kernels.cu).  Operators: KRY_SYM y = A x (A symmetric, full storage);
+// KRY_TRI_PAIR y = L^T (L x) (L lower triangular, entries above the diagonal not read).
+// The starting vector is the Gaussian vector fill_gaussian(v, m, 1, m, seed) makes.
+//   power == 0: `steps` Lanczos steps; out[j] = alpha_j (j < steps) and
+//               out[steps + 1 + j] = beta_j, the layout of the step-by-step loop.
+//   power  > 0: `power` normalised power steps, then out[0] = v^T A v.
+// Returns false (nothing launched) if m is outside [1, KRY_MAX_M].
+constexpr int KRY_MAX_M = 1024;
+enum KryOp { KRY_SYM = 0, KRY_TRI_PAIR = 1 };
+bool krylov_cluster(const double *A, long long lda, int op, int m, int steps, int power, uint64_t seed, double *out,
                     cudaStream_t s);
 void scale_columns(double *X, long long ldx, int m, int n, const double *d, int use_sqrt_abs,
                    cudaStream_t s);
