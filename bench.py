@@ -214,6 +214,16 @@ def run_gemm_probe(args):
     return 0
 
 
+def _seconds_by_k(ks, infos):
+    """Sum of the instances' own call times (each on its worker thread), by block order k."""
+    bins = [(16, 64), (64, 256), (256, 1025)]
+    out = {}
+    for lo, hi in bins:
+        sel = [i for i, k in enumerate(ks) if lo <= k < hi]
+        out["k%d-%d" % (lo, hi - 1)] = {"instances": len(sel), "seconds": sum(infos[i]["seconds"] for i in sel)}
+    return out
+
+
 def run_batch(args):
     """Batched workload: one step = pssd_eig_batched over `count` instances."""
     import torch
@@ -273,7 +283,8 @@ def run_batch(args):
             "config": {"workload": "batch of %d Casida matrices, k log-uniform [16,1024], d ~ U[0.5,50]"
                        % args.batch_count, "sum_n3": n3, "precision": args.precision},
             "max_rel_residual": res, "gpu_launches": h.launch_count() - l0,
-            "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()}, "clocks": ck}
+            "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()},
+            "host_seconds_by_k": _seconds_by_k(ks, infos), "clocks": ck}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -604,7 +615,7 @@ def main():
         ph0 = P.launch_count_phases()
         g0 = torch.cuda.Event(enable_timing=True); g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        Ds, Vs, _ = P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
+        Ds, Vs, binfo = P.eig_batched(Hs, handle=h, precision=P.PSSD_MIXED)
         g1.record(stream)
         torch.cuda.synchronize()
         tb = g0.elapsed_time(g1) / 1e3
@@ -615,6 +626,7 @@ def main():
                                  "precision": "mixed", "max_rel_residual": resb,
                                  "gpu_launches": h.launch_count() - lb0,
                                  "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()},
+                                 "host_seconds_by_k": _seconds_by_k(ks, binfo),
                                  "note": "pssd_eig_batched (host work queue over 16 worker streams)"}
         del Hs, Ds, Vs
     if rank == 0 and not args.no_cpu_baseline:

@@ -1073,6 +1073,48 @@ void copy_matrix(const double *X, long long ldx, double *Y, long long ldy, int m
     scale_copy<double, double>(X, ldx, Y, ldy, m, n, 1.0, s);
 }
 
+// Y[z] = X[z] for z < batch (m x n blocks, strides sX, sY): one launch for the batch
+template <class T>
+__global__ void copy_batched_kernel(const T *X, long long ldx, long long sX, T *Y, long long ldy, long long sY, int m,
+                                    int n)
+{
+    const int i = blockIdx.y;
+    const T *x = X + (long long)blockIdx.z * sX + (long long)i * ldx;
+    T *y = Y + (long long)blockIdx.z * sY + (long long)i * ldy;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) y[j] = x[j];
+}
+
+template <class T>
+void copy_batched(const T *X, long long ldx, long long sX, T *Y, long long ldy, long long sY, int m, int n, int batch,
+                  cudaStream_t s)
+{
+    if (m <= 0 || n <= 0 || batch <= 0) return;
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    copy_batched_kernel<T><<<dim3(gx, m, batch), 256, 0, s>>>(X, ldx, sX, Y, ldy, sY, m, n); count_launch();
+}
+template void copy_batched<double>(const double *, long long, long long, double *, long long, long long, int, int, int,
+                                   cudaStream_t);
+template void copy_batched<float>(const float *, long long, long long, float *, long long, long long, int, int, int,
+                                  cudaStream_t);
+
+// Z[i][j] <- (B[i][j] + Z[i][j]) / 2 for j < p, (B[i][j] - Z[i][j]) / 2 for j >= p (m x n):
+// with Z = Y B on entry, the columns (I + Y)/2 B_+ and (I - Y)/2 B_- of the two projectors
+__global__ void half_sum_diff_kernel(const double *B, long long ldb, double *Z, long long ldz, int m, int n, int p)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double b = B[(long long)i * ldb + j], z = Z[(long long)i * ldz + j];
+        Z[(long long)i * ldz + j] = 0.5 * (j < p ? b + z : b - z);
+    }
+}
+
+void half_sum_diff(const double *B, long long ldb, double *Z, long long ldz, int m, int n, int p, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return;
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    half_sum_diff_kernel<<<dim3(gx, m), 256, 0, s>>>(B, ldb, Z, ldz, m, n, p); count_launch();
+}
+
 template <class T>
 __global__ void add_diag_kernel(T *X, long long ldx, int n, double v)
 {

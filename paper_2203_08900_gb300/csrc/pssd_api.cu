@@ -398,8 +398,7 @@ void chol_rec(pssd_handle h, T *A, int off, int s, long long lda, long long sA, 
         g.C = tmp; g.ldc = hh; g.sC = sT;
         gemm(h, g);
         Timed t(h, K_HBM, 0, 2.0 * sizeof(T) * q * (double)hh * batch);
-        for (int z = 0; z < batch; ++z)
-            scale_copy<T, T>(tmp + (long long)z * sT, hh, A21 + (long long)z * sA, lda, q, hh, 1.0, h->stream);
+        copy_batched<T>(tmp, hh, sT, A21, lda, sA, q, hh, batch, h->stream);
     }
     {   // A22 -= L21 L21^T (lower)
         GemmArgs g; g.mode = gm_of<T>(); g.m = q; g.n = q; g.k = hh; g.batch = batch;
@@ -1011,16 +1010,14 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
         Timed t(h, K_HBM, 0, 8.0 * m * (double)m);
         fill_gaussian(Om, ld, m, m, seed, h->stream);
     }
-    if (p > 0) {   // Y_+ = (I + Y)/2 Omega_+
-        GemmArgs g; g.m = m; g.n = p; g.k = m; g.A = Y; g.lda = ld; g.B = Om; g.ldb = ld; g.Cin = Om; g.ldcin = ld;
-        g.C = Yb; g.ldc = ld; g.alpha = 0.5; g.beta = 0.5;
+    // [Y_+ Y_-] = [(I + Y)/2 Omega_+, (I - Y)/2 Omega_-]: one product Y Omega, then one pass
+    auto project = [&](const double *X) {
+        GemmArgs g; g.m = m; g.n = m; g.k = m; g.A = Y; g.lda = ld; g.B = X; g.ldb = ld; g.C = Yb; g.ldc = ld;
         gemm(h, g);
-    }
-    if (m - p > 0) {   // Y_- = (I - Y)/2 Omega_-
-        GemmArgs g; g.m = m; g.n = m - p; g.k = m; g.A = Y; g.lda = ld; g.B = Om + p; g.ldb = ld; g.Cin = Om + p;
-        g.ldcin = ld; g.C = Yb + p; g.ldc = ld; g.alpha = -0.5; g.beta = 0.5;
-        gemm(h, g);
-    }
+        Timed t(h, K_HBM, 0, 24.0 * m * (double)m);
+        half_sum_diff(X, ld, Yb, ld, m, m, p, h->stream);
+    };
+    project(Om);
     int st = PSSD_OK;
     if (p > 0 && p == m - p) {   // equal halves: both bases in one batched pass
         st = cholqr2(h, Yb, ld, m, p, U, ld, 2, p, p);
@@ -1029,16 +1026,7 @@ int sym_split(pssd_handle h, const double *B, const double *Y, int m, int p, dou
         if (!st && m - p > 0) st = cholqr2(h, Yb + p, ld, m, m - p, U + p, ld);
     }
     if (!st && refine) {
-        if (p > 0) {   // (I + Y)/2 U_+
-            GemmArgs g; g.m = m; g.n = p; g.k = m; g.A = Y; g.lda = ld; g.B = U; g.ldb = ld; g.Cin = U; g.ldcin = ld;
-            g.C = Yb; g.ldc = ld; g.alpha = 0.5; g.beta = 0.5;
-            gemm(h, g);
-        }
-        if (m - p > 0) {   // (I - Y)/2 U_-
-            GemmArgs g; g.m = m; g.n = m - p; g.k = m; g.A = Y; g.lda = ld; g.B = U + p; g.ldb = ld; g.Cin = U + p;
-            g.ldcin = ld; g.C = Yb + p; g.ldc = ld; g.alpha = -0.5; g.beta = 0.5;
-            gemm(h, g);
-        }
+        project(U);   // [(I + Y)/2 U_+, (I - Y)/2 U_-]
         if (p > 0 && p == m - p) {
             st = cholqr2(h, Yb, ld, m, p, U, ld, 2, p, p, 1);
         } else {

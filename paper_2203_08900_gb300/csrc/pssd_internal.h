@@ -140,6 +140,11 @@ void combine_lower(const T *Zinv, long long ldz, long long sZ, const double *a, 
 template <class TI, class TO>  // Y = alpha X (with conversion)
 void scale_copy(const TI *X, long long ldx, TO *Y, long long ldy, int m, int n, double alpha,
                 cudaStream_t s);
+template <class T>  // Y[z] = X[z], z < batch (m x n blocks; strides sX, sY), one launch
+void copy_batched(const T *X, long long ldx, long long sX, T *Y, long long ldy, long long sY, int m, int n, int batch,
+                  cudaStream_t s);
+// Z <- (B + Z)/2 in columns j < p, (B - Z)/2 in columns j >= p (m x n)
+void half_sum_diff(const double *B, long long ldb, double *Z, long long ldz, int m, int n, int p, cudaStream_t s);
 template <class T>
 void add_diag(T *X, long long ldx, int n, double v, cudaStream_t s);
 template <class T>  // partials[2*b] = sum (X-Y)^2, [2*b+1] = sum Y^2 (X may be null)
