@@ -257,8 +257,10 @@ int pssd_eig(pssd_handle h, int n, const signed char *sigma, const double *H, in
  * pointers; sigma may be NULL (every instance Casida-signed) or hold per-
  * instance host signatures (NULL entries allowed); infos NULL or `count` entries.
  * Instances run concurrently on up to PSSD_BATCH_WORKERS internal streams (one
- * workspace each, kept by the handle); the handle's stream is ordered before
- * and after the whole batch.  Returns the first failing instance's status.
+ * host thread and workspace each, kept by the handle); the environment variable
+ * PSSD_BATCH_WORKERS (an integer in [1, 64], read at each call) overrides that
+ * default.  The handle's stream is ordered before and after the whole batch.
+ * Returns the first failing instance's status.
  */
 #define PSSD_BATCH_WORKERS 16
 int pssd_eig_batched(pssd_handle h, int count, const int *n, const signed char *const *sigma,

@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cmath>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -3012,7 +3013,12 @@ extern "C" int pssd_eig_batched(pssd_handle h, int count, const int *n, const si
         if (v) return v;
         if (!V[i] || ldv[i] < n[i] || !D[i]) return -7;
     }
-    const int nw = std::min(count, PSSD_BATCH_WORKERS);
+    int nw_max = PSSD_BATCH_WORKERS;
+    if (const char *env = std::getenv("PSSD_BATCH_WORKERS")) {
+        const long v = std::strtol(env, nullptr, 10);
+        if (v >= 1 && v <= 64) nw_max = (int)v;
+    }
+    const int nw = std::min(count, nw_max);
     try {
         while ((int)h->workers.size() < nw) {
             auto *w = new pssd_handle_s();
