@@ -105,3 +105,18 @@ def test_option_ranges_are_argument_errors(P):
     assert L.pssd_split(h, 4, None, fake, 4, None, 4, out, 4, None, 2, out, 2, None, ctypes.byref(o),
                         ctypes.byref(info)) == -10
     assert L.pssd_destroy(h) == 0
+
+
+def test_phase_launch_counters(P):
+    """pssd_launch_count_phases: one counter per PSSD_PHASE_* index, named in the
+    binding in header order; without a GPU nothing has been launched."""
+    hdr = open(os.path.join(ROOT, "include", "pssd.h")).read()
+    idx = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"#define PSSD_PHASE_([A-Z_]+) (\d+)", hdr)}
+    count = idx.pop("count")
+    assert P.lib().pssd_launch_count_phases(None, 0) == count == len(P.PHASES)
+    assert sorted(idx.values()) == list(range(count))
+    for name, i in idx.items():
+        assert P.PHASES[i] == name
+    got = P.launch_count_phases()
+    assert list(got) == P.PHASES
+    assert all(v >= 0 for v in got.values())
