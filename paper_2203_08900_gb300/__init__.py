@@ -588,18 +588,19 @@ def test_sym_eig(B, handle=None, **kw):
     return w, W, info.as_dict()
 
 
-def test_krylov(A, op=0, steps=24, power=0, seed=1, fused=True, handle=None):
+def test_krylov(A, op=0, steps=24, power=0, seed=1, fused=True, want_v0=True, handle=None):
     """Test hook: the library's Krylov loops on a float64 CUDA matrix A (op 0: A x with A
     symmetric; op 1: A^T (A x) with A lower triangular), step by step or in one cluster
     launch.  Returns (out, v0): Lanczos alphas/betas (2 steps + 2 entries: alpha_j at j,
     beta_j at steps + 1 + j) or [v^T op(A) v] after `power` power steps, and the
-    starting vector before normalisation."""
+    starting vector before normalisation (None unless want_v0)."""
     m, lda = _check_H(A)
     h = _handle(handle)
     out = torch.zeros(2 * steps + 2 if power == 0 else 1, dtype=torch.float64, device=A.device)
-    v0 = torch.empty(m, dtype=torch.float64, device=A.device)
+    v0 = torch.empty(m, dtype=torch.float64, device=A.device) if want_v0 else None
     st = lib().pssd_test_krylov(h._h, op, m, ctypes.c_void_p(A.data_ptr()), lda, steps, power, seed,
-                                1 if fused else 0, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(v0.data_ptr()))
+                                1 if fused else 0, ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(v0.data_ptr() if v0 is not None else None))
     h._check(st)
     return out, v0
 

@@ -129,3 +129,29 @@ def test_fused_size_limit(P):
     assert e.value.status == -3
     out, _ = P.test_krylov(Ad, steps=4, fused=False)
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.parametrize("m", [256, 1024])
+def test_fused_is_one_launch_and_timed(P, m):
+    """The fused loop is one launch (the step-by-step loop: four per Lanczos step plus two
+    to start); both are timed with CUDA events after a warm-up and reported (each call also
+    holds the hook's host synchronisation)."""
+    Ad = torch.from_numpy(_sym(m, 600 + m)).cuda()
+    h = P._handle(None)
+    times, launches = {}, {}
+    for fused in (True, False):
+        P.test_krylov(Ad, steps=24, fused=fused, want_v0=False)
+        torch.cuda.synchronize()
+        l0 = h.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            P.test_krylov(Ad, steps=24, fused=fused, want_v0=False)
+        e1.record()
+        torch.cuda.synchronize()
+        launches[fused] = (h.launch_count() - l0) / 10
+        times[fused] = e0.elapsed_time(e1) / 10
+    print(f"\nLanczos 24 steps m={m}: fused {times[True] * 1e3:.0f} us ({launches[True]:.0f} launch), "
+          f"step by step {times[False] * 1e3:.0f} us ({launches[False]:.0f} launches)")
+    assert launches[True] == 1
+    assert launches[False] == 2 + 4 * 24
