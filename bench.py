@@ -584,7 +584,7 @@ def main():
                                           "note": "Sec. 6 Example 2 recipe on the GPU; the paper's Tab. ItRuntime "
                                                   "ran MATLAB on a laptop CPU (context, not a target)"}
         del Qe
-        # config 5: the step-reversal adjoint of <G, S> + sum of positive eigenvalues at n = 2048
+        # gradient workload: the step-reversal adjoint of <G, S> + sum of positive eigenvalues at n = 2048
         # (d ~ U[1,10], G symmetric N(0,1)), FP64: one warm-up, one timed backward (its forward included)
         ka = 1024
         Ha, _, _ = G.casida_torch(ka, ("uniform", 1.0, 10.0), seed=2048, device=dev)
@@ -603,7 +603,7 @@ def main():
                                  "note": "pssd_sign_vjp_rev: forward Zolotarev sign with its record + reversed steps, "
                                          "congruence and Cholesky; loss <G,S> + sum of positive eigenvalues"}
         del Ha, Ga, Hbar
-        # config 4: 512 Casida matrices, k log-uniform in [16, 1024], d ~ U[0.5, 50], mixed precision,
+        # batch workload: 512 Casida matrices, k log-uniform in [16, 1024], d ~ U[0.5, 50], mixed precision,
         # pssd_eig_batched: one warm-up, one timed call; max relative residual checked untimed
         ks = G.batch_sizes(512, 16, 1024, seed=0)
         Hs = [G.casida_torch(int(kk), ("uniform", 0.5, 50.0), seed=10000 + i, device=dev)[0].contiguous()
@@ -622,7 +622,7 @@ def main():
         with torch.no_grad():
             resb = max(float(torch.linalg.norm(Hx @ Vx - Vx * Dx) / torch.linalg.norm(Hx))
                        for Hx, Dx, Vx in zip(Hs, Ds, Vs))
-        line["batch_config4"] = {"s_per_step": tb, "instances_per_s": len(Hs) / tb, "instances": len(Hs),
+        line["batch_512_casida"] = {"s_per_step": tb, "instances_per_s": len(Hs) / tb, "instances": len(Hs),
                                  "precision": "mixed", "max_rel_residual": resb,
                                  "gpu_launches": h.launch_count() - lb0,
                                  "launches_by_phase": {k: v - ph0[k] for k, v in P.launch_count_phases().items()},

@@ -1958,7 +1958,7 @@ int sign_core(pssd_handle h, int n, const signed char *sigma, const double *H, i
     b.C = S; b.ldc = lds;
     gemm(h, b);
     if (o.precision == PSSD_MIXED) {
-        // north star (1): J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
+        // mixed precision: J-re-symmetrisation, then Newton-Schulz on S itself (polynomials of a
         // Sigma-symmetric S stay Sigma-symmetric), in FP64-accurate arithmetic
         {
             Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
@@ -2348,7 +2348,7 @@ extern "C" int pssd_sign_noalloc(pssd_handle h, int n, const signed char *sigma,
 }
 
 // ===========================================================================
-// Adjoint (north star (3)): cotangents of S = sign(H) and of the eigenvalues
+// Adjoint: cotangents of S = sign(H) and of the eigenvalues
 // pulled back to H.  With H = V Lambda V^{-1} (V from pssd_eig, V^{-1} =
 // Sigma_hat V^T Sigma by Eq. VSigmaOrth) the Frechet derivative of the sign
 // function is the Daleckii-Krein form
@@ -2988,7 +2988,7 @@ extern "C" int pssd_casida_eig(pssd_handle h, int k, const double *A, int lda, c
 
 
 // ===========================================================================
-// Batching (north star (2)): many independent Hamiltonians of uneven sizes.
+// Batching: many independent Hamiltonians of uneven sizes.
 // A host work queue hands instances, largest first, to a pool of workers;
 // each worker owns a handle with its own non-blocking stream and workspace and
 // runs the full pssd_eig pipeline of its instance there, so the kernels of up

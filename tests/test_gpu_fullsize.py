@@ -195,8 +195,8 @@ def test_config_n16384_same_q_exact_spectrum_fp64e(P):
 
 
 def _eig_checks(H, D, V, k):
-    """||HV - VD||_F / ||H||_F (the spec residual, one FP64 product of order n on the
-    GPU) and the Sigma-orthogonality ||(V^T Sigma V - Sigma_hat) X||_F / ||X||_F on 16
+    """||HV - VD||_F / ||H||_F (the target residual of the full diagonalisation, one FP64 product of
+    order n on the GPU) and the Sigma-orthogonality ||(V^T Sigma V - Sigma_hat) X||_F / ||X||_F on 16
     Gaussian probe columns."""
     n = 2 * k
     R = torch.addmm(V * D[None, :], H, V, beta=-1.0)          # H V - V D
