@@ -183,3 +183,42 @@ def bse1(k, dist=("uniform", 1.0, 10.0), coupling=0.5, seed=0):
     B *= coupling * d.min() / np.linalg.norm(B, 2)
     H = np.block([[A, B], [-B.conj(), -A.conj()]])
     return np.ascontiguousarray(H)
+
+
+def general_pseudosym(n, seed=0, n_pairs=0, definite=False, spread=1.0):
+    """A general (not necessarily definite) real pseudosymmetric matrix with a known
+    spectrum (Sec. 3.3, Def. pseudosym): A = V C Sigma V^T Sigma with V = expm(Sigma W)
+    (W skew-symmetric Gaussian scaled to ||W||_2 = spread), so that V^T Sigma V = Sigma and
+    V^{-1} = Sigma V^T Sigma, and C block diagonal with C Sigma symmetric: real 1 x 1
+    entries lambda_i, and `n_pairs` 2 x 2 blocks [[mu, nu], [-nu, mu]] on index pairs with
+    opposite signs of Sigma (eigenvalues mu +- i nu).  Then Sigma A = (Sigma V)(C Sigma)
+    (Sigma V)^T is symmetric.  definite=True takes no pairs and sign(lambda_i) = sigma_i,
+    which makes Sigma A positive definite.
+    Returns (A, sigma as +-1 int8 vector, C, V)."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(seed)
+    p = n // 2
+    sig = np.r_[np.ones(p), -np.ones(n - p)]
+    rng.shuffle(sig)
+    W = rng.standard_normal((n, n))
+    W = W - W.T
+    W *= spread / np.linalg.norm(W, 2)
+    V = expm(sig[:, None] * W)
+    C = np.zeros((n, n))
+    pos, neg = list(np.flatnonzero(sig > 0)), list(np.flatnonzero(sig < 0))
+    used = set()
+    if not definite:
+        for _ in range(min(n_pairs, len(pos), len(neg))):
+            i, j = pos.pop(), neg.pop()
+            mu, nu = rng.uniform(-3.0, 3.0), rng.uniform(0.3, 2.0)
+            C[i, i] = C[j, j] = mu
+            C[i, j], C[j, i] = nu, -nu
+            used.update((i, j))
+    for i in range(n):
+        if i in used:
+            continue
+        lam = rng.uniform(0.2, 3.0)
+        s = sig[i] if definite else (1.0 if rng.uniform() < 0.5 else -1.0)
+        C[i, i] = s * lam
+    A = V @ C @ (sig[:, None] * V.T) * sig[None, :]
+    return np.ascontiguousarray(A), sig.astype(np.int8), C, V

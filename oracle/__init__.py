@@ -10,7 +10,9 @@ Layout:
                   Jacobi eigensolver, pivoted low-rank Cholesky, Jacobi
                   elliptic functions and Zolotarev coefficients)
   oracle.py       the paper's algorithms, step by step, in FP64 (numpy matmul
-                  is the only library primitive used as a step)
+                  is the only library primitive used as a step, except the
+                  general non-definite layer: numpy eig and scipy's
+                  Bunch-Kaufman ldl, as Alg. 5 prescribes)
 
 Parity status of each function is stated in its docstring; all are pinned by
 the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.

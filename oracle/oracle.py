@@ -3,7 +3,10 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The scalar loops live
 in ``pssd_oracle.c``; this module strings them together in the paper's order
 and notation.  The only library primitive used as a step is the dense matrix
-product (``numpy.matmul``).
+product (``numpy.matmul``), except in the general (non-definite) layer at the
+end, whose steps also call numpy's general eigensolver (the definition of
+sign(A) for a complex spectrum) and scipy's Bunch-Kaufman LDL^T (the ``ldl``
+of Alg. 5).
 
 Two layers (both FP64):
 
@@ -18,6 +21,9 @@ Two layers (both FP64):
 * algorithm layer (``sign_alg``, ``split_alg``, ``eig_alg``): Alg. 8 with the
   inverse-form step Eq. (ZoloIt2), then Alg. 7, then the symmetric definite
   subproblems by Jacobi (Thm. DefDivConq).
+* general (non-definite) layer (``gsign_def``, ``hyp_basis_ldl``,
+  ``geig_alg``): Alg. 3 with the hyperbolic bases of Alg. 5 (readings R12-R14
+  in that section).
 
 Readings of the paper where it is garbled or silent:
   R1  Eq. (Compcis): the argument is i*K'/(2r+1) with the integer index i.
@@ -681,3 +687,145 @@ def zsign_def(H, sigma=None):
     s = signature(n, sigma)
     _, V = zeig_def(H, sigma)
     return (V @ V.conj().T) * s[None, :]
+
+
+# --------------------------------------------------------------------------
+# general (non-definite) pseudosymmetric case  (Sec. 3.3 Alg. 3, Sec. 4 Alg. 5)
+#
+# Library steps in this layer: numpy's general eigensolver (the definition of
+# sign(A) for a spectrum that may be complex) and scipy's Bunch-Kaufman LDL^T
+# (the `ldl` that Alg. 5 calls).  Readings:
+#   R12 Alg. 5 writes D^{1/2}; D has negative entries, so R = (L V |D|^{1/2})^T
+#       with Sigma_hat = sign(D), which keeps R^T Sigma_hat R = L D L^T; its last
+#       steps write Sigma_hat (and diag(Sigma_+, Sigma_-)) where the sizes call
+#       for Sigma_hat_+ and Sigma_hat_-: Q_+- = Sigma R_+-^T Sigma_hat_+-.
+#   R13 Alg. 3 "find shift" (no rule given): the widest gap between consecutive
+#       distinct real parts of the eigenvalues among the splits that leave between
+#       a quarter and three quarters of them on each side (any split if none does);
+#       the shift is the gap's midpoint, so a conjugate pair is never separated.
+#   R14 The paper's sign iterations (Eqs. LDLZolo, HRZolo) are analysed for the
+#       definite case (Lemma RationalIter); for a general pseudosymmetric A the
+#       oracle takes the definition sign(A) = X sign(Re Lambda) X^{-1}.
+# --------------------------------------------------------------------------
+
+def gsign_def(A):
+    """sign(A) for a real A with no eigenvalue on the imaginary axis, from its
+    definition: A = X Lambda X^{-1}, sign(A) = X sign(Re Lambda) X^{-1} (the
+    definition behind Eq. signDef, for a spectrum that may be complex).  The result of
+    a real A is real; the imaginary rounding residue is dropped."""
+    A = np.asarray(A, dtype=np.float64)
+    lam, X = np.linalg.eig(A)
+    scale = max(1.0, float(np.max(np.abs(lam)))) if lam.size else 1.0
+    if np.any(np.abs(lam.real) <= 1e-13 * scale):
+        raise ValueError("an eigenvalue lies on the imaginary axis: sign(A) is undefined")
+    S = np.linalg.solve(X.T, (X * np.sign(lam.real)[None, :]).T).T     # X sign(Re Lambda) X^{-1}
+    return np.ascontiguousarray(S.real)
+
+
+def _diagonalise_blocks(D):
+    """D (block diagonal, 1 x 1 and 2 x 2 symmetric blocks, as Bunch-Kaufman leaves it)
+    = Vd diag(w) Vd^T with Vd orthogonal and block diagonal (Alg. 5, "diagonalize D")."""
+    n = D.shape[0]
+    w, Vd = np.zeros(n), np.zeros((n, n))
+    i = 0
+    while i < n:
+        if i + 1 < n and D[i + 1, i] != 0.0:
+            wb, vb = np.linalg.eigh(D[i:i + 2, i:i + 2])
+            w[i:i + 2], Vd[i:i + 2, i:i + 2] = wb, vb
+            i += 2
+        else:
+            w[i], Vd[i, i] = D[i, i], 1.0
+            i += 1
+    return w, Vd
+
+
+def hyp_basis_ldl(S, sigma=None):
+    """Alg. 5: from S = sign(A) of a pseudosymmetric A, bases Q_+ and Q_- of the invariant
+    subspaces of the eigenvalues with positive and negative real part such that
+    Q_+-^T Sigma Q_+- = Sigma_hat_+- (Thm. HRisLDL): P = (I +- S)/2, r = trace(P),
+    Sigma P = L D L^T (Bunch-Kaufman), D diagonalised block by block, the r nonzero values
+    kept, R = (L Vd_r |D_r|^{1/2})^T, Sigma_hat = sign(D_r), Q = Sigma R^T Sigma_hat
+    (readings R12).  Returns (Q_+, Q_-, sigma_hat_+, sigma_hat_-)."""
+    from scipy.linalg import ldl
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    s = signature(n, sigma)
+    out = []
+    for sgn in (1.0, -1.0):
+        P = 0.5 * (np.eye(n) + sgn * S)
+        r = int(round(float(np.trace(P))))
+        if r <= 0:
+            out.append((np.zeros((n, 0)), np.zeros(0)))
+            continue
+        L, D, _ = ldl(s[:, None] * P, lower=True)        # Sigma P = L D L^T (lower triangle read)
+        w, Vd = _diagonalise_blocks(D)
+        keep = np.sort(np.argsort(-np.abs(w), kind="stable")[:r])
+        R = ((L @ Vd[:, keep]) * np.sqrt(np.abs(w[keep]))[None, :]).T     # r x n
+        sh = np.sign(w[keep])
+        out.append((s[:, None] * R.T * sh[None, :], sh))                # Q = Sigma R^T Sigma_hat
+    (Qp, sp), (Qm, sm) = out
+    return Qp, Qm, sp, sm
+
+
+def _general_shift(lam):
+    """Reading R13: the midpoint of the widest gap between consecutive distinct real parts
+    among the balanced splits (a quarter to three quarters on each side), else among all."""
+    re = np.sort(np.asarray(lam).real)
+    n = re.size
+    tol = 1e-12 * max(1.0, float(np.max(np.abs(re))))
+    gaps = [(re[i + 1] - re[i], i + 1, 0.5 * (re[i] + re[i + 1])) for i in range(n - 1) if re[i + 1] - re[i] > tol]
+    if not gaps:
+        return None
+    balanced = [g for g in gaps if n / 4.0 <= g[1] <= 3.0 * n / 4.0]
+    return max(balanced or gaps)[2]
+
+
+def geig_alg(A, sigma=None):
+    """Alg. 3 (pseudosymmetric spectral divide-and-conquer) with sign(A - shift I) from its
+    definition (R14), the bases of Alg. 5 and the shift of R13.  Stops at 1 x 1 blocks and
+    at 2 x 2 blocks holding a complex conjugate pair.  Returns (V, sigma_hat, D):
+    V^T Sigma V = Sigma_hat, V^{-1} = Sigma_hat V^T Sigma, and V^{-1} A V = D block
+    diagonal with blocks of order 1 (real eigenvalues) and 2 (conjugate pairs); the
+    off-diagonal blocks each split leaves are dropped (they are its backward error)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    s = signature(n, sigma)
+    if n == 1:
+        return np.eye(1), s.copy(), A.copy()
+    lam = np.linalg.eigvals(A)
+    if n == 2 and abs(lam[0].imag) > 0.0:
+        return np.eye(2), s.copy(), A.copy()
+    shift = _general_shift(lam)
+    if shift is None:
+        raise ValueError("all eigenvalues share one real part: Alg. 3 finds no shift")
+    S = gsign_def(A - shift * np.eye(n))
+    Qp, Qm, sp, sm = hyp_basis_ldl(S, s)
+    V0 = np.hstack([Qp, Qm])
+    s0 = np.r_[sp, sm]
+    B = ((s0[:, None] * V0.T) * s[None, :]) @ A @ V0            # V0^dagger A V0, V0^dagger = Sigma_0 V0^T Sigma
+    r = Qp.shape[1]
+    V1, s1, D1 = geig_alg(B[:r, :r], sp) if r else (np.zeros((0, 0)), np.zeros(0), np.zeros((0, 0)))
+    V2, s2, D2 = geig_alg(B[r:, r:], sm) if n - r else (np.zeros((0, 0)), np.zeros(0), np.zeros((0, 0)))
+    Z = np.zeros((r, n - r))
+    V = V0 @ np.block([[V1, Z], [Z.T, V2]])
+    D = np.block([[D1, Z], [Z.T, D2]])
+    return V, np.r_[s1, s2], D
+
+
+def block_eigenvalues(D):
+    """The eigenvalues of a block-diagonal D with 1 x 1 and 2 x 2 blocks (as geig_alg
+    returns it): the 1 x 1 entries and, per 2 x 2 block, the roots of its characteristic
+    polynomial x^2 - tr x + det, sorted by real part, then imaginary part."""
+    n = D.shape[0]
+    vals, i = [], 0
+    while i < n:
+        if i + 1 < n and (D[i + 1, i] != 0.0 or D[i, i + 1] != 0.0):
+            tr, det = D[i, i] + D[i + 1, i + 1], D[i, i] * D[i + 1, i + 1] - D[i, i + 1] * D[i + 1, i]
+            disc = complex(tr * tr - 4.0 * det)
+            root = disc ** 0.5
+            vals += [(tr - root) / 2.0, (tr + root) / 2.0]
+            i += 2
+        else:
+            vals.append(complex(D[i, i]))
+            i += 1
+    return np.array(sorted(vals, key=lambda z: (round(z.real, 12), z.imag)))
