@@ -423,6 +423,32 @@ int pssd_zsign(pssd_handle h, int n, const signed char *sigma, const double *H, 
 int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *V, int ldv,
               double *D, const pssd_opts *opts, pssd_info *info);
 
+/*
+ * sign(H) of a GENERAL pseudosymmetric H: Sigma H symmetric but not necessarily
+ * definite, so the spectrum may hold negative and positive real eigenvalues of
+ * either sign characteristic and complex conjugate pairs (Def. pseudosym; the
+ * setting of Alg. 3).  sign(H) = X sign(Re Lambda) X^{-1} needs no eigenvalue on
+ * the imaginary axis.  Method: the Newton iteration of Eq. NewtonSign, X <- (mu X +
+ * X^{-1}/mu)/2 with Frobenius-norm scaling mu = (||X^{-1}||_F/||X||_F)^{1/2} (dropped
+ * once the relative step is below 1e-2), run on the symmetric W = Sigma X: W^{-1} =
+ * (W^2)^{-1} W through the Cholesky factor of the positive definite W^2, so no
+ * pivoted indefinite factorisation is needed; stopped when the relative step is
+ * <= 2^-26.  The conditioning of W^2 is that of H squared: the method suits
+ * moderately conditioned H.
+ *   n, sigma, H, ldh, S, lds  as pssd_sign (S must not alias H)
+ *   opts   NULL = defaults; precision PSSD_FP64 or PSSD_FP64_EMULATED (PSSD_MIXED
+ *          returns -8); r, alpha, beta, method and max_restarts are not used
+ *   info   NULL or filled: iterations, stop_crit (first four steps), p = the number of
+ *          eigenvalues with positive real part (n + trace S)/2, s2_resid = ||S^2 - I||_F
+ *          (exact), jsym_resid = 0 (Sigma S is symmetric by construction)
+ * Status: PSSD_ERR_NOT_PSEUDOSYMMETRIC as pssd_sign; PSSD_ERR_NO_CONVERGENCE if an
+ * iterate is numerically singular (an eigenvalue on or next to the imaginary axis;
+ * info->fail_index = the failing Cholesky pivot of W^2) or 100 steps do not converge;
+ * PSSD_ERR_NONFINITE for NaN/Inf.
+ */
+int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
+               const pssd_opts *opts, pssd_info *info);
+
 /* Test hook: the Krylov loops the library runs for the bounds of Alg. 8 (largest
  * eigenvalue of M and of L^{-T} L^{-1}), the shift search of Alg. 2 (Lanczos
  * quadrature nodes) and the screening of a shift (power iteration on R^{-T} R^{-1}).

@@ -72,7 +72,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
            "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
            "pssd_test_sym_eig", "pssd_sign_vjp_rev", "pssd_zsign", "pssd_zeig", "pssd_launch_count_phases",
-           "pssd_test_krylov"]
+           "pssd_test_krylov", "pssd_gsign"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -108,6 +108,7 @@ def lib():
     L.pssd_sign_vjp_rev.argtypes = sig + [vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, ctypes.POINTER(Opts),
                                           ctypes.POINTER(Info)]
     L.pssd_zsign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_gsign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_zeig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     ll = ctypes.c_longlong
     L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
@@ -300,6 +301,21 @@ def sign(H, sigma=None, handle=None, **kw):
     o = _opts(**kw)
     st = lib().pssd_sign(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
                          S.stride(0), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    return S, info.as_dict()
+
+
+def gsign(H, sigma=None, handle=None, **kw):
+    """S = sign(H) of a general (not necessarily definite) pseudosymmetric H (float64
+    CUDA tensor; Sigma H symmetric): scaled Newton on Sigma X.  Returns (S, info dict)."""
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    S = torch.empty_like(H)
+    keep, sp = _sigma(n, sigma)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_gsign(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(S.data_ptr()),
+                          S.stride(0), ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return S, info.as_dict()
 

@@ -1115,6 +1115,28 @@ void half_sum_diff(const double *B, long long ldb, double *Z, long long ldz, int
     half_sum_diff_kernel<<<dim3(gx, m), 256, 0, s>>>(B, ldb, Z, ldz, m, n, p); count_launch();
 }
 
+// Y = a diag(sig)^rx X + b diag(sig) T diag(sig) (n x n; T may be null): the signature
+// scalings of the general sign iteration, one pass (Y may alias X or T: entry by entry)
+__global__ void sig_affine_kernel(const double *X, long long ldx, int rx, const double *T, long long ldt,
+                                  const double *sig, int n, double a, double b, double *Y, long long ldy)
+{
+    const int i = blockIdx.y;
+    const double si = sig[i], ai = rx ? a * si : a;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double v = ai * X[(long long)i * ldx + j];
+        if (T) v += b * si * sig[j] * T[(long long)i * ldt + j];
+        Y[(long long)i * ldy + j] = v;
+    }
+}
+
+void sig_affine(const double *X, long long ldx, int rx, const double *T, long long ldt, const double *sig, int n,
+                double a, double b, double *Y, long long ldy, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int gx = (n + 255) / 256; if (gx > 16) gx = 16;
+    sig_affine_kernel<<<dim3(gx, n), 256, 0, s>>>(X, ldx, rx, T, ldt, sig, n, a, b, Y, ldy); count_launch();
+}
+
 template <class T>
 __global__ void add_diag_kernel(T *X, long long ldx, int n, double v)
 {

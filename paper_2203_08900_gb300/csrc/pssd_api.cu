@@ -3310,6 +3310,137 @@ extern "C" int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb,
 }
 
 // ---------------------------------------------------------------------------
+// sign(H) of a general (not necessarily definite) pseudosymmetric H, Sigma H
+// symmetric but indefinite (Def. pseudosym; the case of Alg. 3): the Newton
+// iteration of Eq. NewtonSign with Frobenius-norm scaling, run on the symmetric
+// W = Sigma X.  With X = Sigma W, X^{-1} = W^{-1} Sigma, so Sigma X_{k+1} =
+// (mu W_k + Sigma W_k^{-1} Sigma / mu) / 2 stays symmetric; and W^{-1} =
+// (W^2)^{-1} W with W^2 symmetric positive definite for every nonsingular W, so a
+// step is one product W W, one Cholesky with inverse, two products and one pass --
+// no pivoted indefinite factorisation.  S = Sigma W at convergence.
+// ---------------------------------------------------------------------------
+extern "C" int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S,
+                          int lds, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!S || S == H) return -6;
+    if (lds < n) return -7;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o) || o.precision == PSSD_MIXED) return -8;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        PhaseScope phase(PH_SIGN);
+        h->wait_limit = o.wait_cycles;
+        h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+        h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
+        if (info) { info->method = PSSD_METHOD_NEWTON; info->precision = o.precision; }
+        const long long ld = n, nsz = (long long)n * n;
+        std::vector<double> hs(n);
+        for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+        double *sig = dalloc(h, n);
+        h2d(h, sig, hs.data(), sizeof(double) * n);
+        double *W = dalloc(h, nsz), *Wn = dalloc(h, nsz), *G = dalloc(h, nsz), *Ri = dalloc(h, nsz);
+        double *Gi = dalloc(h, nsz), *T = dalloc(h, nsz);
+        {   // W_0 = sym(Sigma H), and the symmetry defect of Sigma H
+            const int nb = sym_prepare_blocks(n);
+            Mark mk = mark(h);
+            double *pp = dalloc(h, 2 * (size_t)nb);
+            {
+                Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+                sym_prepare(H, ldh, sig, n, W, ld, pp, h->stream);
+            }
+            std::vector<double> hp(2 * (size_t)nb);
+            d2h_sync(h, hp.data(), pp, hp.size() * sizeof(double));
+            release(h, mk);
+            double d2 = 0, m2 = 0;
+            for (int i = 0; i < nb; ++i) { d2 += hp[2 * i]; m2 += hp[2 * i + 1]; }
+            if (!std::isfinite(d2) || !std::isfinite(m2)) return PSSD_ERR_NONFINITE;
+            if (!(m2 > 0.0)) return PSSD_ERR_NO_CONVERGENCE;        // H = 0: sign(H) undefined
+            if (std::sqrt(d2) > 1e-12 * std::sqrt(m2)) return PSSD_ERR_NOT_PSEUDOSYMMETRIC;
+        }
+        double *part = dalloc(h, 2 * (size_t)frob_blocks(n, n));
+        const double tol = std::sqrt(U64);
+        bool scaled = true, done = false;
+        for (int it = 0; it < 100 && !done; ++it) {
+            {   // W^2 (lower)
+                GemmArgs g; g.m = g.n = g.k = n; g.A = W; g.lda = ld; g.B = W; g.ldb = ld; g.C = G; g.ldc = ld;
+                g.lowerC = 1;
+                gemm(h, g);
+            }
+            int fi = -1;
+            if (chol_inv<double>(h, G, n, ld, 0, 1, Ri, 0, &fi)) {   // W_k numerically singular
+                if (info) info->fail_index = fi;
+                return PSSD_ERR_NO_CONVERGENCE;
+            }
+            {   // (W^2)^{-1} = R^{-T} R^{-1} (lower, mirrored)
+                GemmArgs l; l.m = l.n = l.k = n; l.A = Ri; l.lda = ld; l.ta = 1; l.triA = TRI_UPPER;
+                l.B = Ri; l.ldb = ld; l.triB = TRI_LOWER; l.C = Gi; l.ldc = ld; l.lowerC = 1;
+                gemm(h, l);
+                mirror<double>(h, Gi, ld, 0, n, 1);
+            }
+            {   // W^{-1} = (W^2)^{-1} W (symmetric: lower, mirrored)
+                GemmArgs f; f.m = f.n = f.k = n; f.A = Gi; f.lda = ld; f.B = W; f.ldb = ld; f.C = T; f.ldc = ld;
+                f.lowerC = 1;
+                gemm(h, f);
+                mirror<double>(h, T, ld, 0, n, 1);
+            }
+            double mu = 1.0;
+            if (scaled) {   // mu = (||X^{-1}||_F / ||X||_F)^{1/2} = (||W^{-1}||_F / ||W||_F)^{1/2}
+                double a2, w2, b2, t2;
+                frob_pair(h, nullptr, ld, W, ld, n, n, part, &a2, &w2);
+                frob_pair(h, nullptr, ld, T, ld, n, n, part, &b2, &t2);
+                mu = std::sqrt(std::sqrt(t2 / w2));
+                if (!std::isfinite(mu) || !(mu > 0.0)) return PSSD_ERR_NONFINITE;
+            }
+            {   // W_{k+1} = (mu W + Sigma W^{-1} Sigma / mu) / 2
+                Timed t(h, K_HBM, 0, 24.0 * n * (double)n);
+                sig_affine(W, ld, 0, T, ld, sig, n, 0.5 * mu, 0.5 / mu, Wn, ld, h->stream);
+            }
+            double d2, y2;
+            frob_pair(h, W, ld, Wn, ld, n, n, part, &d2, &y2);
+            if (!std::isfinite(d2) || !std::isfinite(y2)) return PSSD_ERR_NONFINITE;
+            if (!(y2 > 0.0)) return PSSD_ERR_NO_CONVERGENCE;   // the iterate vanished: eigenvalues +-i t
+            const double crit = std::sqrt(d2 / y2);
+            if (info) {
+                if (it < 4) info->stop_crit[it] = crit;
+                info->iterations = info->steps = it + 1;
+                info->passes = 1;
+            }
+            std::swap(W, Wn);
+            if (crit < 1e-2) scaled = false;   // near the limit: unscaled steps keep the quadratic rate
+            done = crit <= tol;
+        }
+        if (!done) return PSSD_ERR_NO_CONVERGENCE;
+        {   // S = Sigma W
+            Timed t(h, K_HBM, 0, 16.0 * n * (double)n);
+            sig_affine(W, ld, 1, nullptr, 0, sig, n, 1.0, 0.0, S, lds, h->stream);
+        }
+        {   // p = (n + trace S) / 2: the eigenvalues with positive real part
+            Timed t(h, K_HBM, 0, 8.0 * n);
+            trace_partial(S, lds, n, part, h->stream);
+        }
+        double tr;
+        d2h_sync(h, &tr, part, sizeof(double));
+        if (info) {
+            info->p = (int)std::lround(0.5 * (n + tr));
+            info->jsym_resid = 0.0;                  // Sigma S = W is symmetric by construction
+            GemmArgs g; g.m = g.n = g.k = n; g.A = S; g.lda = lds; g.B = S; g.ldb = lds; g.C = G; g.ldc = ld;
+            gemm(h, g);                                                   // S^2
+            {
+                Timed t(h, K_HBM, 0, 8.0 * n);
+                add_diag<double>(G, ld, n, -1.0, h->stream);
+            }
+            double d2, q2;
+            frob_pair(h, nullptr, ld, G, ld, n, n, part, &d2, &q2);
+            info->s2_resid = std::sqrt(q2);
+        }
+        return PSSD_OK;
+    });
+}
+
+// ---------------------------------------------------------------------------
 // test hook: the Krylov loops behind the bounds, the shift search and the shift
 // screening, step by step or in one cluster launch, on the operators they use
 // ---------------------------------------------------------------------------

@@ -145,6 +145,9 @@ void copy_batched(const T *X, long long ldx, long long sX, T *Y, long long ldy, 
                   cudaStream_t s);
 // Z <- (B + Z)/2 in columns j < p, (B - Z)/2 in columns j >= p (m x n)
 void half_sum_diff(const double *B, long long ldb, double *Z, long long ldz, int m, int n, int p, cudaStream_t s);
+// Y = a diag(sig)^rx X + b diag(sig) T diag(sig) (n x n; T may be null; Y may alias X or T)
+void sig_affine(const double *X, long long ldx, int rx, const double *T, long long ldt, const double *sig, int n,
+                double a, double b, double *Y, long long ldy, cudaStream_t s);
 template <class T>
 void add_diag(T *X, long long ldx, int n, double v, cudaStream_t s);
 template <class T>  // partials[2*b] = sum (X-Y)^2, [2*b+1] = sum Y^2 (X may be null)
