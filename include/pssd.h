@@ -449,6 +449,33 @@ int pssd_zeig(pssd_handle h, int n, const signed char *sigma, const double *H, i
 int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S, int lds,
                const pssd_opts *opts, pssd_info *info);
 
+/*
+ * Spectral division of a GENERAL pseudosymmetric H (the division step of Alg. 3):
+ * S = sign(H) as pssd_gsign; p = (n + trace S)/2 eigenvalues with positive real part;
+ * a Gaussian sketch of each projector (I +- S)/2 made orthonormal (U_+, U_-); the
+ * symmetric Sigma-Gram matrix U^T Sigma U of each basis diagonalised (= W Lambda W^T,
+ * symmetric divide-and-conquer of Alg. 2), Q_+- = U_+- W |Lambda|^{-1/2} and
+ * Sigma_hat_+- = sign(Lambda): the (Sigma, Sigma_hat)-orthogonal basis of Alg. 5 /
+ * Thm. HRisLDL (Q^T Sigma Q = Sigma_hat), obtained without a pivoted LDL^T.  Then
+ * Q^{-1} H Q = diag(A11, A22) with Q^{-1} = Sigma_hat Q^T Sigma, A11 = Sigma_hat_+
+ * Q_+^T Sigma H Q_+ (pseudosymmetric with respect to Sigma_hat_+), A22 likewise.
+ *   n, sigma, H, ldh   as pssd_sign
+ *   Q          device, n x n, ldq >= n: [Q_+ Q_-]; must not alias H
+ *   A11, A22   device, room for n x n each with leading dimension >= n (p is known
+ *              only after the sign): the p x p and (n-p) x (n-p) blocks are written
+ *              to their leading corners
+ *   sigma_hat  host, n entries: Sigma_hat_+ then Sigma_hat_- (+1 / -1)
+ *   p_out      host or NULL
+ *   opts       as pssd_gsign (PSSD_MIXED returns -14)
+ *   info       as pssd_gsign, plus split_backerr = ||Sigma_hat_+ Q_+^T Sigma H Q_-||_F /
+ *              ||H||_F, the coupling block the division drops (exact)
+ * Status: as pssd_gsign; PSSD_ERR_BASIS if a sketch loses rank or a Sigma-Gram
+ * matrix has an eigenvalue below 1e-10 of its largest (a basis close to Sigma-neutral).
+ */
+int pssd_gsplit(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *Q, int ldq,
+                double *A11, int lda11, double *A22, int lda22, signed char *sigma_hat, int *p_out,
+                const pssd_opts *opts, pssd_info *info);
+
 /* Test hook: the Krylov loops the library runs for the bounds of Alg. 8 (largest
  * eigenvalue of M and of L^{-T} L^{-1}), the shift search of Alg. 2 (Lanczos
  * quadrature nodes) and the screening of a shift (power iteration on R^{-T} R^{-1}).

@@ -72,7 +72,7 @@ EXPORTS = ["pssd_opts_init", "pssd_create", "pssd_destroy", "pssd_set_stream", "
            "pssd_test_gemm_f64", "pssd_workspace_bytes", "pssd_set_workspace", "pssd_workspace_peak",
            "pssd_device_alloc_count", "pssd_casida_sign", "pssd_casida_split", "pssd_casida_eig",
            "pssd_test_sym_eig", "pssd_sign_vjp_rev", "pssd_zsign", "pssd_zeig", "pssd_launch_count_phases",
-           "pssd_test_krylov", "pssd_gsign"]
+           "pssd_test_krylov", "pssd_gsign", "pssd_gsplit"]
 NOALLOC_MAX_N = 128
 MAX_N = 65535                 # PSSD_MAX_N: largest supported order
 
@@ -109,6 +109,8 @@ def lib():
                                           ctypes.POINTER(Info)]
     L.pssd_zsign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_gsign.argtypes = sig + [vp, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    L.pssd_gsplit.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     L.pssd_zeig.argtypes = sig + [vp, ctypes.c_int, vp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     ll = ctypes.c_longlong
     L.pssd_test_gemm_f32.argtypes = [vp] + [ctypes.c_int] * 10 + [ctypes.c_double, ctypes.c_double,
@@ -318,6 +320,30 @@ def gsign(H, sigma=None, handle=None, **kw):
                           S.stride(0), ctypes.byref(o), ctypes.byref(info))
     h._check(st)
     return S, info.as_dict()
+
+
+def gsplit(H, sigma=None, handle=None, **kw):
+    """Spectral division of a general pseudosymmetric H (float64 CUDA tensor).  Returns
+    (Q, A11, A22, sigma_hat (numpy int8), p, info): Q^T Sigma Q = diag(sigma_hat) and
+    Q^{-1} H Q = diag(A11, A22) with Q^{-1} = diag(sigma_hat) Q^T Sigma."""
+    import numpy as np
+    n, ldh = _check_H(H)
+    h = _handle(handle)
+    Q = torch.empty_like(H)
+    A11 = torch.empty_like(H)
+    A22 = torch.empty_like(H)
+    keep, sp = _sigma(n, sigma)
+    sh = np.zeros(n, dtype=np.int8)
+    p = ctypes.c_int(0)
+    info = Info()
+    o = _opts(**kw)
+    st = lib().pssd_gsplit(h._h, n, sp, ctypes.c_void_p(H.data_ptr()), ldh, ctypes.c_void_p(Q.data_ptr()),
+                           Q.stride(0), ctypes.c_void_p(A11.data_ptr()), A11.stride(0),
+                           ctypes.c_void_p(A22.data_ptr()), A22.stride(0), sh.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.byref(p), ctypes.byref(o), ctypes.byref(info))
+    h._check(st)
+    k = p.value
+    return Q, A11[:k, :k], A22[:n - k, :n - k], sh, k, info.as_dict()
 
 
 def sign_noalloc(H, S=None, sigma=None, handle=None, **kw):

@@ -3319,28 +3319,15 @@ extern "C" int pssd_test_sym_eig(pssd_handle h, int m, const double *B, int ldb,
 // step is one product W W, one Cholesky with inverse, two products and one pass --
 // no pivoted indefinite factorisation.  S = Sigma W at convergence.
 // ---------------------------------------------------------------------------
-extern "C" int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S,
-                          int lds, const pssd_opts *opts, pssd_info *info)
+namespace {
+// the general sign iteration on the device (see pssd_gsign): S = sign(H), sig the device
+// signature; the handle's engines and modes are set by the caller
+int gsign_core(pssd_handle h, int n, const double *sig, const double *H, int ldh, double *S, int lds,
+               pssd_info *info)
 {
-    if (!h) return -1;
-    int v = validate(n, sigma, H, ldh);
-    if (v) return v;
-    if (!S || S == H) return -6;
-    if (lds < n) return -7;
-    pssd_opts o = opts ? *opts : defaults();
-    if (opts_bad(o) || o.precision == PSSD_MIXED) return -8;
-    info_init(info);
-    return guarded(h, info, [&]() -> int {
-        PhaseScope phase(PH_SIGN);
-        h->wait_limit = o.wait_cycles;
-        h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
-        h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
-        if (info) { info->method = PSSD_METHOD_NEWTON; info->precision = o.precision; }
-        const long long ld = n, nsz = (long long)n * n;
-        std::vector<double> hs(n);
-        for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
-        double *sig = dalloc(h, n);
-        h2d(h, sig, hs.data(), sizeof(double) * n);
+    const long long ld = n, nsz = (long long)n * n;
+    Mark outer = mark(h);
+    const int st = [&]() -> int {
         double *W = dalloc(h, nsz), *Wn = dalloc(h, nsz), *G = dalloc(h, nsz), *Ri = dalloc(h, nsz);
         double *Gi = dalloc(h, nsz), *T = dalloc(h, nsz);
         {   // W_0 = sym(Sigma H), and the symmetry defect of Sigma H
@@ -3436,6 +3423,179 @@ extern "C" int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const 
             frob_pair(h, nullptr, ld, G, ld, n, n, part, &d2, &q2);
             info->s2_resid = std::sqrt(q2);
         }
+    return PSSD_OK;
+    }();
+    release(h, outer);
+    return st;
+}
+}  // namespace
+
+extern "C" int pssd_gsign(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *S,
+                          int lds, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!S || S == H) return -6;
+    if (lds < n) return -7;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o) || o.precision == PSSD_MIXED) return -8;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        PhaseScope phase(PH_SIGN);
+        h->wait_limit = o.wait_cycles;
+        h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+        h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
+        if (info) { info->method = PSSD_METHOD_NEWTON; info->precision = o.precision; }
+        std::vector<double> hs(n);
+        for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+        double *sig = dalloc(h, n);
+        h2d(h, sig, hs.data(), sizeof(double) * n);
+        return gsign_core(h, n, sig, H, ldh, S, lds, info);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Split of a general pseudosymmetric H (Alg. 3's division step): S from the general
+// sign iteration; a Gaussian sketch of each projector (I +- S)/2 made orthonormal
+// (CholeskyQR2, then the projector applied once more and one Cholesky QR pass);
+// the symmetric Sigma-Gram matrix G = U^T Sigma U of each basis diagonalised by the
+// symmetric recursion (G = W Lambda W^T), Q = U W |Lambda|^{-1/2}, Sigma_hat =
+// sign(Lambda), so Q^T Sigma Q = Sigma_hat: the (Sigma, Sigma_hat)-orthogonal basis
+// that Alg. 5 obtains from a pivoted LDL^T, reached without pivoting.  Then
+// A11 = Sigma_hat_+ Q_+^T Sigma H Q_+, A22 likewise (pseudosymmetric with respect
+// to Sigma_hat_+ and Sigma_hat_-).
+// ---------------------------------------------------------------------------
+extern "C" int pssd_gsplit(pssd_handle h, int n, const signed char *sigma, const double *H, int ldh, double *Q,
+                           int ldq, double *A11, int lda11, double *A22, int lda22, signed char *sigma_hat,
+                           int *p_out, const pssd_opts *opts, pssd_info *info)
+{
+    if (!h) return -1;
+    int v = validate(n, sigma, H, ldh);
+    if (v) return v;
+    if (!Q || Q == H) return -6;
+    if (ldq < n) return -7;
+    if (!A11) return -8;
+    if (lda11 < n) return -9;
+    if (!A22) return -10;
+    if (lda22 < n) return -11;
+    if (!sigma_hat) return -12;
+    pssd_opts o = opts ? *opts : defaults();
+    if (opts_bad(o) || o.precision == PSSD_MIXED) return -14;
+    info_init(info);
+    return guarded(h, info, [&]() -> int {
+        PhaseScope phase(PH_SIGN);
+        h->wait_limit = o.wait_cycles;
+        h->use_tc = (o.flags & PSSD_FLAG_NO_TENSOR_CORES) ? 0 : 1;
+        h->dmode = (o.precision == PSSD_FP64) ? GM_F64 : ((o.flags & PSSD_FLAG_EMU_SIMT) || !h->use_tc ? GM_DF : GM_OZ);
+        if (info) { info->method = PSSD_METHOD_NEWTON; info->precision = o.precision; }
+        const long long ld = n, nsz = (long long)n * n;
+        std::vector<double> hs(n);
+        for (int i = 0; i < n; ++i) hs[i] = sigma ? (double)sigma[i] : (i < n / 2 ? 1.0 : -1.0);
+        double *sig = dalloc(h, n);
+        h2d(h, sig, hs.data(), sizeof(double) * n);
+        double *S = dalloc(h, nsz);
+        int st = gsign_core(h, n, sig, H, ldh, S, ld, info);
+        if (st) return st;
+        g_phase = PH_SPLIT;
+        double *tmp = dalloc(h, 2 * (size_t)frob_blocks(n, n) + 8);
+        {
+            Timed t(h, K_HBM, 0, 8.0 * n);
+            trace_partial(S, ld, n, tmp, h->stream);
+        }
+        double tr;
+        d2h_sync(h, &tr, tmp, sizeof(double));
+        const int p = (int)std::lround(0.5 * (n + tr)), q = n - p;
+        if (p < 0 || q < 0) return PSSD_ERR_BASIS;
+        if (p_out) *p_out = p;
+        if (info) info->p = p;
+        // sketches of the two projectors, orthonormal bases U = [U_+ U_-]
+        double *Om = dalloc(h, nsz), *Yb = dalloc(h, nsz), *U = dalloc(h, nsz);
+        {
+            Timed t(h, K_HBM, 0, 8.0 * n * (double)n);
+            fill_gaussian(Om, ld, n, n, 0x9e5b17ull, h->stream);
+        }
+        auto project = [&](const double *X) {   // Yb = [(I + S)/2 X_+, (I - S)/2 X_-]
+            GemmArgs g; g.m = g.n = g.k = n; g.A = S; g.lda = ld; g.B = X; g.ldb = ld; g.C = Yb; g.ldc = ld;
+            gemm(h, g);
+            Timed t(h, K_HBM, 0, 24.0 * n * (double)n);
+            half_sum_diff(X, ld, Yb, ld, n, n, p, h->stream);
+        };
+        auto bases = [&](int passes) -> int {
+            int r = PSSD_OK;
+            if (p > 0) r = cholqr2(h, Yb, ld, n, p, U, ld, 1, 0, 0, passes);
+            if (!r && q > 0) r = cholqr2(h, Yb + p, ld, n, q, U + p, ld, 1, 0, 0, passes);
+            return r;
+        };
+        project(Om);
+        if (bases(2)) return PSSD_ERR_BASIS;
+        project(U);
+        if (bases(1)) return PSSD_ERR_BASIS;
+        // Sigma-Gram matrices and their eigendecompositions: Q = U W |Lambda|^{-1/2}
+        std::vector<double> shat(n);
+        auto hyperbolic = [&](const double *Uh, int r, double *Qh, double *sh) -> int {
+            Mark mk = mark(h);
+            double *Gm = dalloc(h, (size_t)r * r), *Wg = dalloc(h, (size_t)r * r), *wg = dalloc(h, r);
+            double *inv = dalloc(h, r);
+            GemmArgs g; g.m = g.n = r; g.k = n; g.A = Uh; g.lda = ld; g.ta = 1; g.kscale = sig; g.B = Uh;
+            g.ldb = ld; g.C = Gm; g.ldc = r; g.lowerC = 1;
+            gemm(h, g);                                                   // U^T Sigma U (lower)
+            mirror<double>(h, Gm, r, 0, r, 1);
+            int maxdepth = 0;
+            int e = sym_eig(h, Gm, r, Wg, wg, 64, 1, &maxdepth, 0x6e9a11ull + r);
+            if (!e) e = sym_refine(h, Gm, r, r, Wg, r, wg);
+            if (e) { release(h, mk); return e; }
+            std::vector<double> hw(r);
+            d2h_sync(h, hw.data(), wg, sizeof(double) * r);
+            double wmax = 0.0;
+            for (double x : hw) wmax = std::max(wmax, std::fabs(x));
+            std::vector<double> hinv(r);
+            for (int i = 0; i < r; ++i) {
+                if (!(std::fabs(hw[i]) > 1e-10 * wmax)) { release(h, mk); return PSSD_ERR_BASIS; }
+                sh[i] = hw[i] > 0.0 ? 1.0 : -1.0;
+                hinv[i] = 1.0 / std::fabs(hw[i]);
+            }
+            h2d(h, inv, hinv.data(), sizeof(double) * r);
+            GemmArgs b; b.m = n; b.n = r; b.k = r; b.A = Uh; b.lda = ld; b.B = Wg; b.ldb = r; b.C = Qh; b.ldc = ldq;
+            gemm(h, b);                                                   // U W
+            {
+                Timed t(h, K_HBM, 0, 16.0 * n * (double)r);
+                scale_columns(Qh, ldq, n, r, inv, 1, h->stream);          // . |Lambda|^{-1/2}
+            }
+            cuda_check(h, cudaStreamSynchronize(h->stream), "sync");      // hinv goes out of scope
+            release(h, mk);
+            return PSSD_OK;
+        };
+        if (p > 0 && (st = hyperbolic(U, p, Q, shat.data()))) return st;
+        if (q > 0 && (st = hyperbolic(U + p, q, Q + p, shat.data() + p))) return st;
+        for (int i = 0; i < n; ++i) sigma_hat[i] = (signed char)(shat[i] > 0.0 ? 1 : -1);
+        // blocks: A = Sigma_hat Q^T Sigma (H Q), diagonal blocks and (info) the coupling block
+        double *HQ = dalloc(h, nsz), *shd = dalloc(h, n);
+        h2d(h, shd, shat.data(), sizeof(double) * n);
+        {
+            GemmArgs g; g.m = g.n = g.k = n; g.A = H; g.lda = ldh; g.B = Q; g.ldb = ldq; g.C = HQ; g.ldc = ld;
+            gemm(h, g);
+        }
+        auto block = [&](int off, int r, double *Ab, int ldab) {
+            GemmArgs g; g.m = g.n = r; g.k = n; g.A = Q + off; g.lda = ldq; g.ta = 1; g.kscale = sig;
+            g.B = HQ + off; g.ldb = ld; g.C = Ab; g.ldc = ldab;
+            gemm(h, g);
+            Timed t(h, K_HBM, 0, 16.0 * r * (double)r);
+            sig_affine(Ab, ldab, 1, nullptr, 0, shd + off, r, 1.0, 0.0, Ab, ldab, h->stream);
+        };
+        if (p > 0) block(0, p, A11, lda11);
+        if (q > 0) block(p, q, A22, lda22);
+        if (info && p > 0 && q > 0) {   // ||Q_+^dagger H Q_-||_F / ||H||_F
+            double *E = dalloc(h, (size_t)p * q);
+            GemmArgs g; g.m = p; g.n = q; g.k = n; g.A = Q; g.lda = ldq; g.ta = 1; g.kscale = sig;
+            g.B = HQ + p; g.ldb = ld; g.C = E; g.ldc = q;
+            gemm(h, g);
+            double a2, e2, b2, h2;
+            frob_pair(h, nullptr, q, E, q, p, q, tmp, &a2, &e2);
+            frob_pair(h, nullptr, ldh, H, ldh, n, n, tmp, &b2, &h2);
+            info->split_backerr = std::sqrt(e2 / h2);
+        }
+        cuda_check(h, cudaStreamSynchronize(h->stream), "sync");          // shat goes out of scope
         return PSSD_OK;
     });
 }

@@ -109,3 +109,60 @@ def test_gsign_n2048_timed(P, precision):
     assert err <= 1e-14 * kap * kap
     assert info["s2_resid"] <= 1e-12 * n * np.linalg.norm(S_con, 2) ** 2
     assert info["p"] == int(np.sum(np.linalg.eigvals(C).real > 0))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64e"])
+@pytest.mark.parametrize("n,pairs,seed,spread", CASES)
+def test_gsplit_invariants(P, precision, n, pairs, seed, spread):
+    """The division of Alg. 3 through pssd_gsplit.  The basis is not unique; what is:
+    p, the inertia of Sigma_hat on each side (Sylvester's law; the oracle's Alg. 5 basis
+    gives it), the projector Q_+ Sigma_hat_+ Q_+^T Sigma = (I + S)/2, the spectra of the
+    blocks; and Q^T Sigma Q = Sigma_hat, Q^{-1} H Q = diag(A11, A22), Sigma_hat A11
+    symmetric hold for any valid basis."""
+    pr = {"fp64": P.PSSD_FP64, "fp64e": P.PSSD_FP64_EMULATED}[precision]
+    A, sg, C, V = G.general_pseudosym(n, seed=seed, n_pairs=pairs, spread=spread)
+    s = sg.astype(float)
+    Qd, A11, A22, sh, p, info = P.gsplit(_dev(A), sigma=sg, precision=pr)
+    Q, A11, A22 = Qd.cpu().numpy(), A11.cpu().numpy(), A22.cpu().numpy()
+    shf = sh.astype(float)
+    lam = np.linalg.eigvals(C)
+    assert p == int(np.sum(lam.real > 0))
+    assert set(np.unique(sh)) <= {-1, 1}
+    S_def = O.gsign_def(A)
+    _, _, sp_o, sm_o = O.hyp_basis_ldl(S_def, s)
+    assert np.sum(shf[:p] > 0) == np.sum(sp_o > 0) and np.sum(shf[p:] > 0) == np.sum(sm_o > 0)
+    kap, kq = np.linalg.cond(A), np.linalg.cond(Q)
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ (s[:, None] * Q) - np.diag(shf)) <= 1e-13 * n * kq * kq
+    Pp = 0.5 * (np.eye(n) + S_def)
+    Qp = Q[:, :p]
+    assert np.linalg.norm(Qp @ np.diag(shf[:p]) @ Qp.T * s[None, :] - Pp) <= 1e-14 * kap * kap * np.linalg.norm(Pp)
+    B = ((shf[:, None] * Q.T) * s[None, :]) @ A @ Q
+    assert np.linalg.norm(B[:p, :p] - A11) <= 1e-13 * kq * kq * nA
+    assert np.linalg.norm(B[p:, p:] - A22) <= 1e-13 * kq * kq * nA
+    assert np.linalg.norm(B[:p, p:]) <= 1e-14 * kap * kap * kq * kq * nA
+    if 0 < p < n:
+        assert info["split_backerr"] <= 1e-14 * kap * kap * kq * kq
+    for Ab, sb in ((A11, shf[:p]), (A22, shf[p:])):
+        if Ab.size:
+            SA = sb[:, None] * Ab
+            assert np.linalg.norm(SA - SA.T) <= 1e-13 * kq * kq * nA
+    scale = np.max(np.abs(lam))
+    if p:
+        ev, ref = np.sort_complex(np.linalg.eigvals(A11)), np.sort_complex(lam[lam.real > 0])
+        assert np.max(np.abs(ev - ref)) <= 1e-10 * kap * scale
+    if n - p:
+        ev, ref = np.sort_complex(np.linalg.eigvals(A22)), np.sort_complex(lam[lam.real < 0])
+        assert np.max(np.abs(ev - ref)) <= 1e-10 * kap * scale
+
+
+def test_gsplit_definite_signatures(P):
+    """Thm. DefDivConq through the general division: on a definite input Sigma_hat_+ = I,
+    Sigma_hat_- = -I, A11 symmetric positive definite, A22 symmetric negative definite."""
+    A, sg, _, _ = G.general_pseudosym(100, seed=41, definite=True)
+    Qd, A11, A22, sh, p, info = P.gsplit(_dev(A), sigma=sg)
+    assert np.all(sh[:p] == 1) and np.all(sh[p:] == -1)
+    A11, A22 = A11.cpu().numpy(), A22.cpu().numpy()
+    assert np.linalg.norm(A11 - A11.T) <= 1e-12 * np.linalg.norm(A11)
+    assert np.min(np.linalg.eigvalsh(0.5 * (A11 + A11.T))) > 0
+    assert np.max(np.linalg.eigvalsh(0.5 * (A22 + A22.T))) < 0
